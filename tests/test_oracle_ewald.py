@@ -1,0 +1,269 @@
+"""Pins of the exact-Ewald oracle (oracle/ewald_oracle.c) to things other than itself.
+
+Every check here compares the oracle with an independent fact fixed by the paper or by
+mathematics (Sec. 2 and Apps. A-B of Bagge & Tornberg 2022):
+  * xi-independence of the total u^R + u^F (+ k0, self)       -- Sec. 2.4, Eq. Dp-ewald-decomp
+  * App. A / App. B tensors vs quadrature of their defining integrals
+  * absolutely convergent 1P rotlet / stresslet image sums      -- Sec. 2 (convergence remark)
+  * the stresslet integral identity (0 inside, 8 pi q outside)  -- Eq. stresslet-identity
+  * special functions (K_nu identities, E_n) and printed limits -- Eqs. Knu-def, 1p-*-limit
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.special as sp
+
+from oracle import ewald as E
+
+KERNELS = ["stokeslet", "rotlet", "stresslet"]
+
+
+def _strengths(rng, kernel, n):
+    if kernel == "stresslet":
+        q = rng.standard_normal((n, 3))
+        nu = rng.standard_normal((n, 3))
+        nu /= np.linalg.norm(nu, axis=1, keepdims=True)
+        return np.hstack([q, nu])
+    return rng.standard_normal((n, 3))
+
+
+def _gf_numpy(kernel, xi, k):
+    """G^F(k; xi) for an array of wave vectors k (..., 3), Eqs. (stokeslet-fourier) -
+    (stresslet-fourier); used only as the integrand of the quadrature checks below."""
+    k = np.asarray(k, dtype=float)
+    k2 = np.sum(k * k, axis=-1)
+    gE = np.exp(-k2 / (4 * xi * xi))
+    gH = gE * (1 + k2 / (4 * xi * xi))
+    d = np.eye(3)
+    if kernel == "stokeslet":
+        K = -d * k2[..., None, None] + k[..., :, None] * k[..., None, :]
+        return (K * (-8 * np.pi / k2 ** 2 * gH)[..., None, None]).astype(complex)
+    if kernel == "rotlet":
+        eps = np.zeros((3, 3, 3))
+        eps[0, 1, 2] = eps[1, 2, 0] = eps[2, 0, 1] = 1
+        eps[0, 2, 1] = eps[2, 1, 0] = eps[1, 0, 2] = -1
+        K = -1j * np.einsum("jlm,...m->...jl", eps, k)
+        return K * (4 * np.pi / k2 * gE)[..., None, None]
+    K = (-1j * (np.einsum("jl,...m->...jlm", d, k) + np.einsum("mj,...l->...jlm", d, k)
+                + np.einsum("lm,...j->...jlm", d, k)) * k2[..., None, None, None]
+         + 2j * k[..., :, None, None] * k[..., None, :, None] * k[..., None, None, :])
+    return K * (-8 * np.pi / k2 ** 2 * gH)[..., None, None, None]
+
+
+# ----------------------------------------------------------------- special functions
+
+def test_En_matches_scipy():
+    for x in [1e-3, 0.2, 0.9, 1.0, 1.1, 3.0, 12.0, 40.0]:
+        assert abs(E.En(1, x) / sp.exp1(x) - 1) < 1e-14
+        assert abs(E.En(2, x) / sp.expn(2, x) - 1) < 1e-12
+    assert abs(E.En(0, 2.0) - math.exp(-2.0) / 2.0) < 1e-16
+
+
+@pytest.mark.parametrize("a,b", [(0.7, 1.3), (0.05, 4.0), (6.0, 0.3), (2.0, 20.0)])
+def test_Knu_bessel_identity(a, b):
+    # K_nu(a,b) + K_{-nu}(b,a) = 2 (a/b)^{nu/2} K_nu(2 sqrt(ab))   [App. B, Harris 2008]
+    for nu in (0, 1):
+        lhs = E.Knu(nu, a, b) + E.Knu(-nu, b, a)
+        rhs = 2 * (a / b) ** (nu / 2) * sp.kv(nu, 2 * math.sqrt(a * b))
+        assert abs(lhs / rhs - 1) < 1e-13
+
+
+@pytest.mark.parametrize("a,b", [(0.7, 1.3), (9.0, 0.2), (0.1, 2.0)])
+def test_Knu_recurrences(a, b):
+    # a K_{-1}(a,b) - b K_1(a,b) = e^{-a-b}     [App. B]
+    assert abs(a * E.Knu(-1, a, b) - b * E.Knu(1, a, b) - math.exp(-a - b)) < 1e-14 * math.exp(-a - b) * 50
+    # K_nu(a,0) = E_{nu+1}(a)                    [below Eq. 1p-rotlet-Q]
+    for nu in (-1, 0, 1, 2):
+        assert abs(E.Knu(nu, a, 0.0) / sp.expn(nu + 1, a) - 1) < 1e-13
+    # d/db K_nu = -K_{nu+1}: central difference
+    h = 1e-5 * max(b, 1)
+    for nu in (-1, 0, 1):
+        d = (E.Knu(nu, a, b + h) - E.Knu(nu, a, b - h)) / (2 * h)
+        assert abs(d + E.Knu(nu + 1, a, b)) < 1e-8 * abs(E.Knu(nu + 1, a, b))
+
+
+# ------------------------------------------------------------- App. A / B tensors
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_Q2p_matches_quadrature(kernel):
+    """App. A closed forms vs (1/2pi) int G^F(k1,k2,kappa3) e^{i kappa3 r3} d kappa3."""
+    xi = 3.0
+    K = 2 * xi * 7.5
+    xg, wg = np.polynomial.legendre.leggauss(600)
+    kap = K * xg
+    w = K * wg
+    for k1, k2, r3 in [(2 * np.pi, 0.0, 0.3), (2 * np.pi, 4 * np.pi, -0.2), (-2 * np.pi, 2 * np.pi, 0.45)]:
+        kv = np.stack([np.full_like(kap, k1), np.full_like(kap, k2), kap], axis=-1)
+        G = _gf_numpy(kernel, xi, kv)
+        ph = np.exp(1j * kap * r3) * w / (2 * np.pi)
+        q = np.tensordot(ph, G, axes=(0, 0))
+        c = E.Q2p(kernel, xi, k1, k2, r3)
+        assert np.abs(q - c).max() < 1e-12 * np.abs(q).max()
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_Q1p_matches_quadrature(kernel):
+    """App. B closed forms vs (1/(2pi)^2) iint G^F(k1,kap2,kap3) e^{i(kap2 r2+kap3 r3)}."""
+    xi = 2.0
+    K = 2 * xi * 7.0
+    xg, wg = np.polynomial.legendre.leggauss(220)
+    kap = K * xg
+    w = K * wg
+    K2, K3 = np.meshgrid(kap, kap, indexing="ij")
+    W = np.outer(w, w)
+    for k1, r2, r3 in [(2 * np.pi, 0.3, -0.2), (-4 * np.pi, 0.05, 0.4), (np.pi, 0.0, 0.0)]:
+        kv = np.stack([np.full_like(K2, k1), K2, K3], axis=-1)
+        G = _gf_numpy(kernel, xi, kv)
+        ph = np.exp(1j * (K2 * r2 + K3 * r3)) * W / (2 * np.pi) ** 2
+        q = np.tensordot(ph, G, axes=([0, 1], [0, 1]))
+        c = E.Q1p(kernel, xi, k1, r2, r3)
+        assert np.abs(q - c).max() < 1e-11 * np.abs(q).max()
+
+
+def test_zero_mode_limits_are_continuous():
+    # Eq. (1p-stokeslet-Q0-limit) and the zero limits of rotlet/stresslet
+    xi = 3.0
+    for kernel in KERNELS:
+        lim = E.Q1p0(kernel, xi, 0.0, 0.0)
+        near = E.Q1p0(kernel, xi, 1e-7, -0.7e-7)
+        assert np.abs(lim - near).max() < 200 * 1.22e-7  # approaches the limit like O(rho)
+    # Q^{2P,(0)} is smooth at r3 = 0 and odd/even as printed
+    for kernel in KERNELS:
+        a = E.Q2p0(kernel, xi, 0.2)
+        b = E.Q2p0(kernel, xi, -0.2)
+        if kernel == "stokeslet":
+            assert np.allclose(a, b, rtol=0, atol=1e-14)
+        else:
+            assert np.allclose(a, -b, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- whole-sum pins
+
+@pytest.mark.parametrize("D,L", [(3, [1, 1, 1]), (3, [1.0, 0.8, 1.3]), (2, [1, 1, 1]), (2, [1, 1, 0.5]),
+                                 (1, [1, 1, 1]), (1, [2, 1, 1])])
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_total_is_xi_independent(D, L, kernel):
+    """u = u^R + u^F (+k0 +self) does not depend on xi (Sec. 2.4)."""
+    rng = np.random.default_rng(7 + D)
+    n = 10
+    x = rng.random((n, 3)) * np.asarray(L)
+    f = _strengths(rng, kernel, n)
+    xi0 = E.default_xi(D, L)
+    u1 = E.potential(D, L, kernel, x, f, xi=xi0)
+    u2 = E.potential(D, L, kernel, x, f, xi=1.6 * xi0)
+    # explicit, distinct targets too
+    t = rng.random((4, 3)) * np.asarray(L)
+    v1 = E.potential(D, L, kernel, x, f, targets=t, xi=xi0)
+    v2 = E.potential(D, L, kernel, x, f, targets=t, xi=1.6 * xi0)
+    assert E.rms_rel(u1, u2) < 1e-12
+    assert E.rms_rel(v1, v2) < 1e-12
+
+
+def test_star_form_equals_explicit_coincident_targets():
+    rng = np.random.default_rng(3)
+    x = rng.random((8, 3))
+    for kernel in KERNELS:
+        f = _strengths(rng, kernel, 8)
+        a = E.potential(3, [1, 1, 1], kernel, x, f)
+        b = E.potential(3, [1, 1, 1], kernel, x, f, targets=x.copy())
+        assert np.abs(a - b).max() < 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("kernel", ["rotlet", "stresslet"])
+def test_1p_rotlet_stresslet_equal_image_sum(kernel):
+    """D = 1 rotlet and stresslet sums converge absolutely (Sec. 2): brute-force image sum
+    with Richardson extrapolation in the image count."""
+    rng = np.random.default_rng(11)
+    L = np.array([1.5, 1.0, 1.0])
+    n = 5
+    x = rng.random((n, 3)) * L
+    f = _strengths(rng, kernel, n)
+
+    def image_sum(P):
+        u = np.zeros((n, 3))
+        p = np.arange(-P, P + 1)
+        for m in range(n):
+            for j in range(n):
+                r = x[m] - x[j] + np.outer(p, [L[0], 0, 0])
+                if m == j:
+                    r = r[p != 0]
+                r2 = np.sum(r * r, axis=1)
+                rr = np.sqrt(r2)
+                if kernel == "rotlet":   # Omega_jl f_l = (f x r)_j / r^3
+                    u[m] += np.sum(np.cross(f[j], r) / (rr ** 3)[:, None], axis=0)
+                else:                    # T_jlm q_l nu_m = -6 r_j (r.q)(r.nu) / r^5
+                    q, nu = f[j, :3], f[j, 3:]
+                    u[m] += np.sum(-6 * r * ((r @ q) * (r @ nu) / rr ** 5)[:, None], axis=0)
+        return u
+
+    s1 = image_sum(4000)
+    s2 = image_sum(8000)
+    brute = (4 * s2 - s1) / 3
+    ref = E.potential(1, L, kernel, x, f)
+    assert E.rms_rel(ref, brute) < 1e-10
+
+
+def _sphere(center, a, nth=24, nph=48):
+    ct, wt = np.polynomial.legendre.leggauss(nth)
+    ph = 2 * np.pi * np.arange(nph) / nph
+    C, P = np.meshgrid(ct, ph, indexing="ij")
+    S = np.sqrt(1 - C ** 2)
+    nrm = np.stack([S * np.cos(P), S * np.sin(P), C], axis=-1).reshape(-1, 3)
+    w = (np.outer(wt, np.full(nph, 2 * np.pi / nph)) * a * a).reshape(-1)
+    return center + a * nrm, nrm, w
+
+
+@pytest.mark.parametrize("D", [0, 1, 2, 3])
+def test_stresslet_integral_identity(D):
+    """Eq. (stresslet-identity) for every D (Sec. 2.5).
+
+    With T_jlm = -6 r_j r_l r_m / r^5, r = x - y and nu the OUTWARD normal, the divergence
+    theorem gives 8 pi q0 at points enclosed by the surface and 0 outside (div_y T = 0 away
+    from y = x; the excised ball gives 6 * (4 pi / 3) delta_jl). The printed equation lists
+    the two regions the other way round, which is the inward-normal form."""
+    L = np.array([1.0, 1.0, 1.0])
+    c = np.array([0.5, 0.5, 0.5])
+    y, nrm, w = _sphere(c, 0.2)
+    q0 = np.array([0.3, -1.1, 0.7])
+    f = np.hstack([q0[None, :] * w[:, None], nrm])
+    inside = np.array([[0.5, 0.5, 0.5], [0.55, 0.45, 0.52]])
+    outside = np.array([[0.1, 0.1, 0.1], [0.9, 0.2, 0.6]])
+    ui = E.potential(D, L, "stresslet", y, f, targets=inside)
+    uo = E.potential(D, L, "stresslet", y, f, targets=outside)
+    assert np.abs(uo).max() < 1e-8
+    assert np.abs(ui - 8 * np.pi * q0).max() < 1e-8
+
+
+def test_free_space_kernels_special_values():
+    """Eq. (stokes-kernels) at r = (1,0,0): S = diag(2,1,1), Omega f = f x r, T = -6 e1e1e1."""
+    x = np.zeros((1, 3))
+    t = np.array([[1.0, 0.0, 0.0]])
+    us = E.potential(0, [1, 1, 1], "stokeslet", x, np.array([[1.0, 2.0, 3.0]]), targets=t)
+    assert np.allclose(us, [[2.0, 2.0, 3.0]], atol=1e-15)
+    ur = E.potential(0, [1, 1, 1], "rotlet", x, np.array([[1.0, 2.0, 3.0]]), targets=t)
+    assert np.allclose(ur, [np.cross([1.0, 2.0, 3.0], [1.0, 0, 0])], atol=1e-15)
+    ut = E.potential(0, [1, 1, 1], "stresslet", x, np.array([[2.0, 1.0, 0.0, 3.0, 0.0, 1.0]]), targets=t)
+    assert np.allclose(ut, [[-36.0, 0.0, 0.0]], atol=1e-14)
+
+
+def test_3p_self_term_and_magnitudes():
+    """Self term Eq. (3p-stokeslet-self-term); Fourier-part rms near the values printed for
+    N = 1000, L = 1, Q = 1, xi = 10 (Sec. 4.6: about 2, 20 and 7 for S, T, Omega)."""
+    rng = np.random.default_rng(5)
+    n = 1000
+    x = rng.random((n, 3))
+    for kernel, printed in [("stokeslet", 2.0), ("stresslet", 20.0), ("rotlet", 7.0)]:
+        f = rng.uniform(-1, 1, (n, 6 if kernel == "stresslet" else 3))
+        if kernel == "stresslet":
+            Q = np.sum((f[:, :3, None] * f[:, None, 3:]) ** 2)
+        else:
+            Q = np.sum(f ** 2)
+        f = f / math.sqrt(Q) if kernel != "stresslet" else np.hstack([f[:, :3] / Q ** 0.25, f[:, 3:] / Q ** 0.25])
+        p = E.parts(3, [1, 1, 1], kernel, x, f, xi=10.0)
+        rms = math.sqrt(np.mean(np.sum(p["fourier"] ** 2, axis=1)))
+        assert printed / 3 < rms < printed * 3
+        if kernel == "stokeslet":
+            assert np.allclose(p["self"], -4 * 10.0 / math.sqrt(math.pi) * f, atol=1e-15)
+        else:
+            assert np.abs(p["self"]).max() == 0.0
