@@ -1,0 +1,183 @@
+/*
+ * libse -- Spectral Ewald summation of the Stokes potentials (stokeslet, rotlet,
+ * stresslet) with periodicity in 3, 2, 1 or 0 directions, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Bagge & Tornberg, "Fast Ewald summation for Stokes flow with arbitrary
+ * periodicity" (J. Comput. Phys., arXiv 2210.01255). The potential
+ *     u^{DP}(x) = sum_n sum_{p in P_DP} G(x - x_n + p) . f(x_n)          (Sec. 2, Eq. periodic-potential)
+ * is split (Eq. Dp-ewald-decomp-self) into a real-space part summed over neighbours within
+ * r_c (Eq. real-space-potential-Dp), a Fourier-space part computed by the Spectral Ewald
+ * method (Sec. 3, Alg. 1: gridding, FFT, scaling by the modified kernel, IFFT, gathering)
+ * and the self / zero-mode / gauge corrections (Eqs. self-term, k0-stresslet-3p,
+ * 0p-stokeslet-extra-contribution, 1p-stokeslet-extra-contribution).
+ *
+ * Conventions
+ *   - mu = 1 and the kernels exactly as Eq. (stokes-kernels), no 1/(8 pi) factor.
+ *   - The first D coordinate directions are periodic (Eq. periodic-images); the primary
+ *     cell is [0,L1) x [0,L2) x [0,L3).
+ *   - Positions are double [N][3]. Periodic coordinates are wrapped into [0, L_i); a free
+ *     coordinate outside [0, L_i) is rejected with SE_ERR_RANGE.
+ *   - Strengths and potentials are double in an SE_FP64 plan and float in an SE_FP32 plan:
+ *       stokeslet, rotlet: strengths [n_rhs][N][3] = f
+ *       stresslet:         strengths [n_rhs][N][6] = (q, nu), source f_lm = q_l nu_m
+ *       potential u:       [n_rhs][N_t][3], overwritten.
+ *     With kernel_mask = STOKESLET|STRESSLET the strengths are [n_rhs][N][9] = (f, q, nu)
+ *     and u is the sum of both flows.
+ *   - targets == NULL selects the star form (targets = sources, the self interaction
+ *     omitted, Eq. periodic-potential-star). With explicit targets, a target that
+ *     coincides exactly with a source is treated the same way for that source.
+ *   - Zero-mode / gauge conventions: 3P stokeslet and rotlet zero mode = 0 and the 3P
+ *     stresslet carries Eq. (k0-stresslet-3p) evaluated with the wrapped coordinates;
+ *     the 1P stokeslet is reported with l_B = 1, l_H = e^{-1} (the extra contribution of
+ *     Eq. 1p-stokeslet-extra-contribution vanishes); the 0P stokeslet goes to zero at
+ *     infinity (Eq. 0p-stokeslet-extra-contribution subtracted); 2P needs no constant.
+ *
+ * Memory ownership: the caller owns every array passed in. The plan owns its grids,
+ * tables, FFT plans and scratch; it grows them on demand inside se_eval*.
+ * Execution: all device work of a plan is issued on the plan's stream (se_opts.stream),
+ * asynchronously; results are complete when that stream is synchronised. Errors of
+ * earlier asynchronous work surface at the next call or at se_sync. A plan is not
+ * thread-safe; no C++ exception crosses this interface.
+ */
+#ifndef SE_H
+#define SE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct se_plan_t* se_plan_h;
+
+typedef enum {
+  SE_OK = 0,
+  SE_ERR_ARG = -1,         /* invalid argument (NULL pointer, bad size, bad enum)          */
+  SE_ERR_RANGE = -2,       /* a free-direction coordinate outside [0, L_i), or NaN/Inf     */
+  SE_ERR_NOMEM = -3,       /* device or host allocation failed                             */
+  SE_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed                  */
+  SE_ERR_CUFFT = -5,       /* a cuFFT call failed                                          */
+  SE_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up                           */
+  SE_ERR_UNSUPPORTED = -7  /* a valid request this build does not implement               */
+} se_status;
+
+enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4 };
+enum { SE_WIN_GAUSSIAN = 0, SE_WIN_KB = 1, SE_WIN_PKB = 2 };
+enum { SE_FP64 = 0, SE_FP32 = 1 };
+/* parts of the decomposition returned by se_eval_parts (bit mask) */
+enum { SE_PART_REAL = 1, SE_PART_FOURIER = 2, SE_PART_CORR = 4, SE_PART_ALL = 7 };
+
+typedef struct {
+  int prec;          /* SE_FP64 (default) or SE_FP32                                         */
+  int f_M;           /* grid sizes rounded to multiples of f_M by the rules of Sec. 4 (4)  */
+  double lambda;     /* box padding factor of Eq. (extended-grid-size); 0 = Table 4       */
+  int Mext[3];       /* extended grid size M'_i in free directions; 0 = Eq. extended-grid-size */
+  double s0;         /* upsampling factor of the k^P = 0 class, Eq. (upsampling-factor-s0); 0 = rule */
+  double s_star;     /* upsampling factor of K_*, Eq. (upsampling-factor-sstar); 0 = rule */
+  int kbar_star;     /* threshold kbar_* of Eq. (estimate-kbarstar); -1 = rule            */
+  double tol_abs;    /* absolute tolerance used by the s_*, kbar_* rules (0 = 1e-10)     */
+  double Q;          /* source quantity Q of Eqs. (vector/tensor-source-quantity) for the rules (0 = 1) */
+  int kernel_mask;   /* kernels the plan will be used with (for the free-direction rules); 0 = all */
+  void* stream;      /* cudaStream_t to issue work on; NULL = the legacy default stream   */
+  int flags;         /* reserved, 0                                                         */
+} se_opts;
+
+/* Fill *opts with the defaults above. */
+se_status se_opts_default(se_opts* opts);
+
+/*
+ * Create a plan (Alg. 1 input; Sec. 3.2 discrete formulation).
+ *   periodicity  D in {0,1,2,3}: directions 0..D-1 periodic.
+ *   box          L_i > 0.
+ *   xi           Ewald decomposition parameter (> 0).
+ *   rc           real-space cut-off radius (> 0).
+ *   M            grid subintervals along each box side; the grid spacing is h = L_0/M_0 and
+ *                must be the same in every direction (|L_i/M_i - h| <= 1e-12 h) for the
+ *                periodic directions; for free directions M_i only sets h when D = 0
+ *                (h = L_0/M_0) and the extended size follows Eq. (extended-grid-size).
+ *                Periodic M_i must be even.
+ *   P            window support in grid points (even, 2..32), Sec. 3.3.
+ *   window       SE_WIN_GAUSSIAN (Eq. TG-window), SE_WIN_KB (Eq. KB-window) or SE_WIN_PKB.
+ *   opts         NULL for defaults.
+ * Returns SE_OK and a plan in *out, or an error and *out = NULL.
+ * Device memory for the plan's tables is allocated here (0P: also the kernel
+ * precomputation of Sec. 3.5, which launches GPU work on the plan's stream).
+ */
+se_status se_plan_create(se_plan_h* out, int periodicity, const double box[3], double xi,
+                         double rc, const int M[3], int P, int window, const se_opts* opts);
+
+/*
+ * Parameter selection, Sec. 4.6 (steps 1-7), with the relative tolerance converted to an
+ * absolute one by tau_abs = tol_rel * U(L,Q,xi) (Sec. 4.2).
+ *   kernel_mask  kernels to be evaluated (the strictest parameters over the mask win).
+ *   Q            source quantity (Eq. vector-source-quantity / tensor-source-quantity).
+ *   N            number of sources (used only when *xi <= 0: xi is then chosen from the
+ *                average number of neighbours of Table 5, uniform system).
+ *   tol_rel      relative rms tolerance of the Fourier-space part.
+ *   io_opts      in: f_M (0 = 4), lambda; out: Mext, s0, s_star, kbar_star, tol_abs filled in.
+ *   xi           in/out: the decomposition parameter (<= 0: chosen here).
+ *   rc, M, P     out: cut-off radius, grid sizes along the box sides, window support.
+ * The window is the PKB window (Sec. 3.3).
+ */
+se_status se_autotune(int periodicity, const double box[3], int kernel_mask, double Q,
+                      long long N, double tol_rel, se_opts* io_opts, double* xi, double* rc,
+                      int M[3], int* P);
+
+/*
+ * Evaluate the potential (Eqs. Dp-ewald-decomp / Dp-ewald-decomp-self).
+ *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET or SE_STOKESLET|SE_STRESSLET.
+ *   n_src, src   device double [n_src][3].
+ *   strengths    device [n_rhs][n_src][c], c = 3 (S, Omega), 6 (T) or 9 (S|T); float in an
+ *                SE_FP32 plan, double in an SE_FP64 plan.
+ *   n_rhs        number of right-hand sides (strength vectors at the same points), >= 1.
+ *   n_tgt, tgt   device double [n_tgt][3], or tgt = NULL for the star form (n_tgt ignored).
+ *   u            device [n_rhs][N_t][3] of the plan's precision, overwritten.
+ * Asynchronous on the plan's stream.
+ */
+se_status se_eval(se_plan_h plan, int kernel_mask, long long n_src, const double* src,
+                  const void* strengths, int n_rhs, long long n_tgt, const double* tgt, void* u);
+
+/* As se_eval, returning only the parts selected by parts_mask (SE_PART_*): the real-space
+ * sum, the Fourier-space part u_h^{DP,F} (Alg. 1) and the corrections (self term, 3P
+ * stresslet zero mode, 0P/1P stokeslet gauge constants). */
+se_status se_eval_parts(se_plan_h plan, int kernel_mask, int parts_mask, long long n_src,
+                        const double* src, const void* strengths, int n_rhs, long long n_tgt,
+                        const double* tgt, void* u);
+
+/* As se_eval with HOST arrays (same layouts): copies in, evaluates and copies the result
+ * back through plan-owned pinned staging buffers; returns when u is filled. */
+se_status se_eval_host(se_plan_h plan, int kernel_mask, long long n_src, const double* src,
+                       const void* strengths, int n_rhs, long long n_tgt, const double* tgt,
+                       void* u);
+
+/* Read back plan information: h, the grid sizes actually used (n[3]: FFT grid per
+ * direction, m[3]: spread-grid extent per direction), R (truncation radius, 0 for 3P),
+ * s0, s_star, kbar_star, the number of kernels launched by the last evaluation and its
+ * per-stage device times in ms (times[0..7]: bin, spread, fft, scale, ifft, gather, real,
+ * corr; -1 when timing is off). Reading the times waits for the last evaluation. */
+typedef struct {
+  double h, R, s0, s_star, dL[3];
+  int n[3], m[3], kbar_star, P;
+  float times_ms[8];
+  int launches;        /* kernels libse launched in the last evaluation (cuFFT's not counted) */
+} se_info;
+se_status se_get_info(se_plan_h plan, se_info* info);
+
+/* Copy the plan's spread grid (after the last evaluation, before the FFT) to host memory:
+ * component-major [C][m0][m1][m2] in the plan's precision; bytes must be >= the grid size.
+ * Used to check the gridding step (Eq. SE-gridding-disc) in isolation. */
+se_status se_debug_grid(se_plan_h plan, void* host_dst, unsigned long long bytes);
+
+/* Enable per-stage CUDA-event timing of subsequent evaluations (0 = off). */
+se_status se_set_timing(se_plan_h plan, int on);
+
+/* Wait for the plan's stream and report any asynchronous device error. */
+se_status se_sync(se_plan_h plan);
+
+/* Release the plan and everything it owns. NULL is accepted. */
+void se_destroy(se_plan_h plan);
+
+/* Human-readable name of a status code (static storage). */
+const char* se_status_str(se_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1306 @@
+// libse device code: point binning, window weights, gridding (spread), k-space scaling,
+// gathering, real-space sum and corrections, and the se_eval orchestration (Alg. 1 plus
+// the real-space and correction terms of Eq. Dp-ewald-decomp-self).
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "se_internal.h"
+
+namespace se {
+
+// ====================================================================== small helpers
+
+se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out) {
+  DevBuf& b = (*p->bufs)[name];
+  if (bytes == 0) bytes = 16;
+  if (b.bytes < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8;  // a little headroom for growth
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return SE_ERR_NOMEM;
+    }
+    b.bytes = want;
+  }
+  *out = b.p;
+  return SE_OK;
+}
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { typedef float4 type; };
+template <> struct Vec4<double> { typedef double4 type; };
+
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// floor division for possibly negative a, b > 0
+__host__ __device__ inline int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+static int grid1d(long long n, int block) { return (int)std::max<long long>(1, (n + block - 1) / block); }
+
+// ============================================================ point binning (counting sort)
+
+// Wrap a coordinate of a periodic direction into [0, L); flag a free coordinate outside
+// [0, L) or a non-finite one.
+__device__ inline double wrap_coord(double x, double L, int periodic, int* status) {
+  if (!isfinite(x)) {
+    atomicOr(status, 1);
+    return 0.0;
+  }
+  if (periodic) {
+    double w = x - floor(x / L) * L;
+    if (w >= L) w -= L;
+    if (w < 0) w = 0;
+    return w;
+  }
+  if (x < 0.0 || x >= L) atomicOr(status, 1);
+  return fmin(fmax(x, 0.0), nextafter(L, 0.0));
+}
+
+// key of the spread tile of each point; rank within the tile by atomic counting
+__global__ void k_tile_keys(GridGeom g, const double* __restrict__ x, int n, int* __restrict__ key,
+                            int* __restrict__ rank, int* __restrict__ count, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    double w = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
+    double u = (w - g.origin[d]) * g.inv_h;
+    int cc = (int)floor(u);
+    if (g.periodic[d]) {
+      if (cc >= g.m[d]) cc -= g.m[d];
+    }
+    cc = min(max(cc, 0), g.m[d] - 1);
+    c[d] = cc / TS;
+  }
+  int k = (c[0] * g.ntile[1] + c[1]) * g.ntile[2] + c[2];
+  key[i] = k;
+  rank[i] = atomicAdd(&count[k], 1);
+}
+
+// key of the real-space cell of each point (cells of side >= rc / S)
+struct CellGeom {
+  int nc[3];
+  int range[3];
+  int periodic[3];
+  double L[3];
+  double inv_cs[3];
+};
+
+__global__ void k_cell_keys(CellGeom g, const double* __restrict__ x, int n, int* __restrict__ key,
+                            int* __restrict__ rank, int* __restrict__ count, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    double w = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
+    int cc = (int)floor(w * g.inv_cs[d]);
+    c[d] = min(max(cc, 0), g.nc[d] - 1);
+  }
+  int k = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+  key[i] = k;
+  rank[i] = atomicAdd(&count[k], 1);
+}
+
+// exclusive scan of count[0..nk) into start[0..nk], one CTA (nk is at most a few 1e5)
+__global__ void k_scan(const int* __restrict__ count, int* __restrict__ start, int nk) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x, nt = blockDim.x;
+  const int per = (nk + nt - 1) / nt;
+  const int b = t * per, e = min(nk, b + per);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += count[i];
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < nt; off <<= 1) {
+    int v = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  int run = t ? part[t - 1] : 0;
+  for (int i = b; i < e; ++i) {
+    start[i] = run;
+    run += count[i];
+  }
+  if (t == nt - 1) start[nk] = part[nt - 1];
+}
+
+__global__ void k_scatter_perm(const int* __restrict__ key, const int* __restrict__ rank,
+                               const int* __restrict__ start, int n, int* __restrict__ perm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  perm[start[key[i]] + rank[i]] = i;
+}
+
+// counting sort by key; returns perm (sorted -> original) and start[nk+1]
+static se_status counting_sort(se_plan_t* p, const char* tag, int n, int nk,
+                               void (*keyfun)(se_plan_t*, const double*, int, int*, int*, int*, const void*),
+                               const double* x, const void* geom, int** perm_out, int** start_out) {
+  std::string t(tag);
+  void *key, *rank, *count, *start, *perm;
+  SE_TRY(buf(p, (t + ".key").c_str(), sizeof(int) * (size_t)n, &key));
+  SE_TRY(buf(p, (t + ".rank").c_str(), sizeof(int) * (size_t)n, &rank));
+  SE_TRY(buf(p, (t + ".count").c_str(), sizeof(int) * (size_t)nk, &count));
+  SE_TRY(buf(p, (t + ".start").c_str(), sizeof(int) * (size_t)(nk + 1), &start));
+  SE_TRY(buf(p, (t + ".perm").c_str(), sizeof(int) * (size_t)n, &perm));
+  SE_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)nk, p->stream));
+  if (n > 0) keyfun(p, x, n, (int*)key, (int*)rank, (int*)count, geom);
+  ++p->launches;
+  k_scan<<<1, 1024, 0, p->stream>>>((int*)count, (int*)start, nk);
+  if (n > 0) {
+    ++p->launches;
+    k_scatter_perm<<<grid1d(n, 256), 256, 0, p->stream>>>((int*)key, (int*)rank, (int*)start, n,
+                                                           (int*)perm);
+  }
+  SE_CUDA(cudaGetLastError());
+  *perm_out = (int*)perm;
+  *start_out = (int*)start;
+  return SE_OK;
+}
+
+static void tile_keyfun(se_plan_t* p, const double* x, int n, int* key, int* rank, int* count,
+                        const void* geom) {
+  ++p->launches;
+  k_tile_keys<<<grid1d(n, 256), 256, 0, p->stream>>>(*(const GridGeom*)geom, x, n, key, rank, count,
+                                                     p->d_status);
+}
+static void cell_keyfun(se_plan_t* p, const double* x, int n, int* key, int* rank, int* count,
+                        const void* geom) {
+  ++p->launches;
+  k_cell_keys<<<grid1d(n, 256), 256, 0, p->stream>>>(*(const CellGeom*)geom, x, n, key, rank, count,
+                                                     p->d_status);
+}
+
+// ================================================================ window weights (Sec. 3.3)
+
+template <typename T>
+struct WinArgs {
+  int kind, P, nu;
+  T alpha, beta, inv_i0beta;
+  const T* pkb;  // [P][nu+1] Chebyshev coefficients
+};
+
+template <typename T>
+__device__ inline T dev_i0(T x) {
+  T q = x * x * T(0.25), term = T(1), sum = T(1);
+  for (int k = 1; k < 400; ++k) {
+    term *= q / (T(k) * T(k));
+    sum += term;
+    if (term < T(1e-17) * sum) break;
+  }
+  return sum;
+}
+
+// value of the window at tap q of a point whose fractional grid offset is delta in [0,1):
+// the offset from the point to the tap is (q - P/2 + 1 - delta) h
+template <typename T>
+__device__ inline T win_tap(const WinArgs<T>& w, int q, T delta) {
+  if (w.kind == SE_WIN_PKB) {
+    // subinterval q, local variable s = 1 - 2 delta in (-1, 1]; Clenshaw recurrence
+    const T s = T(1) - T(2) * delta;
+    const T* c = w.pkb + q * (w.nu + 1);
+    T b1 = 0, b2 = 0;
+    for (int j = w.nu; j >= 1; --j) {
+      T b0 = c[j] + T(2) * s * b1 - b2;
+      b2 = b1;
+      b1 = b0;
+    }
+    return c[0] + s * b1 - b2;
+  }
+  const T t = (T(q - w.P / 2 + 1) - delta) / T(w.P / 2);  // offset in units of a_w
+  if (w.kind == SE_WIN_GAUSSIAN) return exp(-w.alpha * t * t);
+  T a = T(1) - t * t;
+  if (a < 0) return T(0);
+  return dev_i0(w.beta * sqrt(a)) * w.inv_i0beta;
+}
+
+// base tap index (unwrapped) and window values for each point, in sorted order
+template <typename T>
+__global__ void k_weights(GridGeom g, WinArgs<T> w, const double* __restrict__ x,
+                          const int* __restrict__ perm, int n, int* __restrict__ base,
+                          T* __restrict__ wts, int* status) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int i = perm ? perm[s] : s;
+  const int P = g.P;
+  for (int d = 0; d < 3; ++d) {
+    double xw = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
+    double u = (xw - g.origin[d]) * g.inv_h;
+    double fl = floor(u);
+    int c = (int)fl;
+    T delta = (T)(u - fl);
+    if (g.periodic[d] && c >= g.m[d]) c -= g.m[d];
+    base[3 * s + d] = c - P / 2 + 1;
+    T* wd = wts + ((size_t)s * 3 + d) * P;
+    for (int q = 0; q < P; ++q) wd[q] = win_tap(w, q, delta);
+  }
+}
+
+// spread components in sorted order: S, Omega: f per RHS; T: the 6 symmetric components
+// (q_l nu_m + q_m nu_l)/2 in the order 11,22,33,12,13,23 (the stresslet operator is fully
+// symmetric, Eq. stokes-kernels, so only the symmetric part of f_lm contributes)
+template <typename T>
+__global__ void k_sort_strengths(int kernel, const T* __restrict__ f, const int* __restrict__ perm,
+                                 int n, int n_rhs, T* __restrict__ sf) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int i = perm[s];
+  if (kernel == SE_STRESSLET) {
+    const int C = 6 * n_rhs;
+    for (int r = 0; r < n_rhs; ++r) {
+      const T* q = f + ((size_t)r * n + i) * 6;
+      const T* nu = q + 3;
+      T* o = sf + (size_t)s * C + 6 * r;
+      o[0] = q[0] * nu[0];
+      o[1] = q[1] * nu[1];
+      o[2] = q[2] * nu[2];
+      o[3] = T(0.5) * (q[0] * nu[1] + q[1] * nu[0]);
+      o[4] = T(0.5) * (q[0] * nu[2] + q[2] * nu[0]);
+      o[5] = T(0.5) * (q[1] * nu[2] + q[2] * nu[1]);
+    }
+  } else {
+    const int C = 3 * n_rhs;
+    for (int r = 0; r < n_rhs; ++r)
+      for (int l = 0; l < 3; ++l) sf[(size_t)s * C + 3 * r + l] = f[((size_t)r * n + i) * 3 + l];
+  }
+}
+
+// ========================================================= gridding, Eq. (SE-gridding-disc)
+//
+// Output-driven: one CTA per TS^3 tile of the grid; each thread owns two grid points along
+// direction 0 and accumulates all components in registers over the points of the tiles
+// whose windows reach the tile. No atomics; each grid value is written once.
+
+constexpr int SP_CHUNK = 64;
+
+template <typename T, int CMAX>
+__global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restrict__ tile_start,
+                                                const int* __restrict__ base, const T* __restrict__ wts,
+                                                const T* __restrict__ sf, int C, T* __restrict__ grid) {
+  __shared__ T s_w[SP_CHUNK][3 * TS];
+  __shared__ T s_f[SP_CHUNK][CMAX];
+  const int P = g.P;
+  const int tid = threadIdx.x;
+  const int lz = tid & 7, ly = (tid >> 3) & 7, lx0 = (tid >> 6) * 2;
+  const int t0 = blockIdx.x, t1 = blockIdx.y, t2 = blockIdx.z;
+  const int o[3] = {t0 * TS, t1 * TS, t2 * TS};
+  T acc0[CMAX], acc1[CMAX];
+#pragma unroll
+  for (int c = 0; c < CMAX; ++c) acc0[c] = acc1[c] = T(0);
+
+  // range of source tiles whose points can reach this tile: cell c reaches [o, o+TS) iff
+  // c in [o - P/2, o + TS - 2 + P/2]; one extra tile on each side of a periodic direction
+  // whose extent is not a multiple of TS (the wrapped tile is partial)
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = fdiv(o[d] - P / 2, TS);
+    hi[d] = fdiv(o[d] + TS - 2 + P / 2, TS);
+    if (g.periodic[d] && (g.m[d] % TS)) {
+      lo[d] -= 1;
+      hi[d] += 1;
+    }
+  }
+  for (int b0 = lo[0]; b0 <= hi[0]; ++b0) {
+    int w0 = b0, sh0 = 0;
+    if (g.periodic[0]) {
+      int im = fdiv(b0, g.ntile[0]);
+      w0 = b0 - im * g.ntile[0];
+      sh0 = im * g.m[0];
+    } else if (b0 < 0 || b0 >= g.ntile[0]) continue;
+    for (int b1 = lo[1]; b1 <= hi[1]; ++b1) {
+      int w1 = b1, sh1 = 0;
+      if (g.periodic[1]) {
+        int im = fdiv(b1, g.ntile[1]);
+        w1 = b1 - im * g.ntile[1];
+        sh1 = im * g.m[1];
+      } else if (b1 < 0 || b1 >= g.ntile[1]) continue;
+      for (int b2 = lo[2]; b2 <= hi[2]; ++b2) {
+        int w2 = b2, sh2 = 0;
+        if (g.periodic[2]) {
+          int im = fdiv(b2, g.ntile[2]);
+          w2 = b2 - im * g.ntile[2];
+          sh2 = im * g.m[2];
+        } else if (b2 < 0 || b2 >= g.ntile[2]) continue;
+        const int bin = (w0 * g.ntile[1] + w1) * g.ntile[2] + w2;
+        const int beg = tile_start[bin], end = tile_start[bin + 1];
+        const int rel0 = sh0 - o[0], rel1 = sh1 - o[1], rel2 = sh2 - o[2];
+        for (int p0 = beg; p0 < end; p0 += SP_CHUNK) {
+          const int cnt = min(SP_CHUNK, end - p0);
+          __syncthreads();
+          for (int idx = tid; idx < cnt * 3 * TS; idx += blockDim.x) {
+            const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
+            const int d = r / TS, l = r - d * TS;
+            const int rel = d == 0 ? rel0 : (d == 1 ? rel1 : rel2);
+            const int q = l - (base[3 * (p0 + pp) + d] + rel);
+            s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)(p0 + pp) * 3 + d) * P + q] : T(0);
+          }
+          for (int idx = tid; idx < cnt * C; idx += blockDim.x) {
+            const int pp = idx / C, c = idx - pp * C;
+            s_f[pp][c] = sf[(size_t)(p0 + pp) * C + c];
+          }
+          __syncthreads();
+          for (int pp = 0; pp < cnt; ++pp) {
+            const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
+            if (wyz != T(0)) {
+              const T wa = s_w[pp][lx0] * wyz, wb = s_w[pp][lx0 + 1] * wyz;
+#pragma unroll
+              for (int c = 0; c < CMAX; ++c) {
+                if (c < C) {
+                  const T fv = s_f[pp][c];
+                  acc0[c] += wa * fv;
+                  acc1[c] += wb * fv;
+                }
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const int y = o[1] + ly, z = o[2] + lz;
+  if (y < g.m[1] && z < g.m[2]) {
+    for (int xi = 0; xi < 2; ++xi) {
+      const int xx = o[0] + lx0 + xi;
+      if (xx >= g.m[0]) continue;
+      const size_t off = ((size_t)xx * g.n[1] + y) * g.n[2] + z;
+#pragma unroll
+      for (int c = 0; c < CMAX; ++c)
+        if (c < C) grid[c * G + off] = xi ? acc1[c] : acc0[c];
+    }
+  }
+}
+
+// ============================================== scaling step, Eq. (SE-scaling-disc), D = 3
+//
+// In place on the half spectrum [C][n0][n1][n2/2+1]. Per mode: the scalar
+// A^(k) (1 + k^2/4xi^2 for the Hasimoto screening) * g0[i0] g1[i1] g2[i2] with the
+// separable tables g_d = exp(-k_d^2/4xi^2) / w^_0(k_d)^2, times the operator symbol
+// K^(k) of Eqs. (diffop-rel-fourier-1..3). Zero mode and Nyquist planes set to zero.
+
+template <typename T>
+struct ScaleArgs {
+  int n0, n1, n2, h2;
+  T kf0, kf1, kf2;  // 2 pi / L_d
+  T inv4xi2;
+  const T* g0;
+  const T* g1;
+  const T* g2;
+};
+
+template <typename T>
+__global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__ spec) {
+  const size_t H = (size_t)a.n0 * a.n1 * a.h2;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= H) return;
+  const int i2 = (int)(idx % a.h2);
+  const int i1 = (int)((idx / a.h2) % a.n1);
+  const int i0 = (int)(idx / ((size_t)a.h2 * a.n1));
+  const int kb0 = i0 < a.n0 / 2 ? i0 : i0 - a.n0;
+  const int kb1 = i1 < a.n1 / 2 ? i1 : i1 - a.n1;
+  const int kb2 = i2;
+  const bool zero = (i0 == a.n0 / 2) || (i1 == a.n1 / 2) || (i2 == a.n2 / 2) ||
+                    (i0 == 0 && i1 == 0 && i2 == 0);
+  const T k0 = a.kf0 * kb0, k1 = a.kf1 * kb1, k2 = a.kf2 * kb2;
+  const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+  T s = T(0);
+  if (!zero) {
+    const T g = a.g0[i0] * a.g1[i1] * a.g2[i2];
+    if (kernel == SE_ROTLET)
+      s = T(4.0 * M_PI) / kk * g;  // H^ = 4 pi / k^2, Ewald screening
+    else
+      s = T(-8.0 * M_PI) / (kk * kk) * (T(1) + kk * a.inv4xi2) * g;  // B^ = -8 pi / k^4, Hasimoto
+  }
+  // complex values as interleaved (re, im) pairs
+  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  for (int r = 0; r < n_rhs; ++r) {
+    T re[6], im[6];
+    for (int c = 0; c < cin; ++c) {
+      const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
+      re[c] = spec[o];
+      im[c] = spec[o + 1];
+    }
+    T ore[3], oim[3];
+    if (kernel == SE_STOKESLET) {
+      // (-delta k^2 + k k) F
+      const T kfr = k0 * re[0] + k1 * re[1] + k2 * re[2];
+      const T kfi = k0 * im[0] + k1 * im[1] + k2 * im[2];
+      const T kv[3] = {k0, k1, k2};
+      for (int j = 0; j < 3; ++j) {
+        ore[j] = s * (-kk * re[j] + kv[j] * kfr);
+        oim[j] = s * (-kk * im[j] + kv[j] * kfi);
+      }
+    } else if (kernel == SE_ROTLET) {
+      // -i eps_jlm k_m F_l = -i (F x k)_j
+      const T cr[3] = {re[1] * k2 - re[2] * k1, re[2] * k0 - re[0] * k2, re[0] * k1 - re[1] * k0};
+      const T ci[3] = {im[1] * k2 - im[2] * k1, im[2] * k0 - im[0] * k2, im[0] * k1 - im[1] * k0};
+      for (int j = 0; j < 3; ++j) {
+        ore[j] = s * ci[j];   // -i (a + ib) = b - ia
+        oim[j] = -s * cr[j];
+      }
+    } else {
+      // K^T_jlm F_lm = -i k^2 (2 (F k)_j + k_j tr F) + 2 i k_j (k F k), F symmetric
+      // components 0..5 = 11,22,33,12,13,23
+      const T kv[3] = {k0, k1, k2};
+      T Fkr[3], Fki[3];
+      Fkr[0] = re[0] * k0 + re[3] * k1 + re[4] * k2;
+      Fkr[1] = re[3] * k0 + re[1] * k1 + re[5] * k2;
+      Fkr[2] = re[4] * k0 + re[5] * k1 + re[2] * k2;
+      Fki[0] = im[0] * k0 + im[3] * k1 + im[4] * k2;
+      Fki[1] = im[3] * k0 + im[1] * k1 + im[5] * k2;
+      Fki[2] = im[4] * k0 + im[5] * k1 + im[2] * k2;
+      const T trr = re[0] + re[1] + re[2], tri = im[0] + im[1] + im[2];
+      const T kFkr = k0 * Fkr[0] + k1 * Fkr[1] + k2 * Fkr[2];
+      const T kFki = k0 * Fki[0] + k1 * Fki[1] + k2 * Fki[2];
+      for (int j = 0; j < 3; ++j) {
+        // value v = -k^2 (2 Fk_j + k_j tr) + 2 k_j kFk ; multiplied by i
+        const T vr = -kk * (T(2) * Fkr[j] + kv[j] * trr) + T(2) * kv[j] * kFkr;
+        const T vi = -kk * (T(2) * Fki[j] + kv[j] * tri) + T(2) * kv[j] * kFki;
+        ore[j] = -s * vi;
+        oim[j] = s * vr;
+      }
+    }
+    for (int j = 0; j < 3; ++j) {
+      const size_t o = (((size_t)(3 * r + j)) * H + idx) * 2;
+      spec[o] = ore[j];
+      spec[o + 1] = oim[j];
+    }
+  }
+}
+
+// ====================================================== gathering, Eq. (SE-gathering-disc)
+//
+// One warp per target: lanes cover the P x P (direction 1, 2) taps, each lane runs over the
+// P taps of direction 0; warp-shuffle reduction; u = h^3 * sum.
+
+template <typename T, int NCMAX>
+__global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restrict__ perm,
+                                                const int* __restrict__ base, const T* __restrict__ wts,
+                                                const T* __restrict__ F, int nt, int NC, T scale,
+                                                T* __restrict__ u) {
+  __shared__ T s_w[8][3 * MAX_P];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * 8 + warp;
+  if (s >= nt) return;
+  const int P = g.P;
+  for (int i = lane; i < 3 * P; i += 32) s_w[warp][i] = wts[(size_t)s * 3 * P + i];
+  const int b0 = base[3 * s], b1 = base[3 * s + 1], b2 = base[3 * s + 2];
+  __syncwarp();
+  T acc[NCMAX];
+#pragma unroll
+  for (int c = 0; c < NCMAX; ++c) acc[c] = T(0);
+  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const T* w0 = s_w[warp];
+  const T* w1 = s_w[warp] + P;
+  const T* w2 = s_w[warp] + 2 * P;
+  for (int l = lane; l < P * P; l += 32) {
+    const int b = l / P, c = l - b * P;
+    int y = b1 + b, z = b2 + c;
+    if (g.periodic[1]) { if (y < 0) y += g.m[1]; else if (y >= g.m[1]) y -= g.m[1]; }
+    if (g.periodic[2]) { if (z < 0) z += g.m[2]; else if (z >= g.m[2]) z -= g.m[2]; }
+    const T wyz = w1[b] * w2[c];
+    for (int a = 0; a < P; ++a) {
+      int xx = b0 + a;
+      if (g.periodic[0]) { if (xx < 0) xx += g.m[0]; else if (xx >= g.m[0]) xx -= g.m[0]; }
+      const size_t off = ((size_t)xx * g.n[1] + y) * g.n[2] + z;
+      const T wv = w0[a] * wyz;
+#pragma unroll
+      for (int k = 0; k < NCMAX; ++k)
+        if (k < NC) acc[k] += wv * F[k * G + off];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NCMAX; ++k) {
+    if (k < NC) {
+      T v = acc[k];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      acc[k] = v;
+    }
+  }
+  if (lane == 0) {
+    const int i = perm ? perm[s] : s;
+    for (int k = 0; k < NC; ++k) {
+      const int r = k / 3, j = k - 3 * r;
+      u[((size_t)r * nt + i) * 3 + j] = scale * acc[k];
+    }
+  }
+}
+
+// ====================================== real-space sum, Eq. (real-space-potential-Dp)
+//
+// Cell list of cells with side >= rc / S (S = range); one thread per target looping over
+// the (2S+1)^3 neighbour cells with periodic images in the periodic directions. A pair at
+// exactly zero separation is the omitted self interaction of the star sum: it contributes
+// the self term -G^F(0) . f (Eq. self-term) instead, so the star form and explicit
+// coincident targets agree.
+
+template <typename T>
+struct RealArgs {
+  CellGeom cg;
+  T xi, rc2;
+  int kernel, n_rhs, nsrc, ntgt;
+  const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
+  const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
+  const T* fs;                       // sorted strengths [ns][c * n_rhs]
+  const int* cstart;                 // cell starts [ncell+1]
+  const typename Vec4<T>::type* xt;  // sorted targets
+  const typename Vec4<T>::type* xtl; // low parts of the sorted targets (FP32 only)
+  const int* tperm;                  // sorted target -> original index
+  const int* tcell;                  // cell of each sorted target ([3] ints)
+  T* u;
+};
+
+template <typename T>
+__device__ inline T dev_erfc(T x);
+template <> __device__ inline float dev_erfc<float>(float x) { return erfcf(x); }
+template <> __device__ inline double dev_erfc<double>(double x) { return erfc(x); }
+
+template <typename T, int RMAX>
+__global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.ntgt) return;
+  typedef typename Vec4<T>::type V4;
+  const V4 xt = a.xt[s];
+  V4 xtl;
+  xtl.x = xtl.y = xtl.z = xtl.w = T(0);
+  if (sizeof(T) == 4) xtl = a.xtl[s];
+  const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
+  const int nc = a.kernel == SE_STRESSLET ? 6 : 3;
+  const int C = nc * a.n_rhs;
+  T acc[3 * RMAX];
+#pragma unroll
+  for (int k = 0; k < 3 * RMAX; ++k) acc[k] = T(0);
+  const T xi = a.xi;
+  const T xi2 = xi * xi;
+  const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
+  const CellGeom& g = a.cg;
+  for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
+    int ux = cx + dx;
+    double shx_d = 0;
+    if (g.periodic[0]) {
+      int im = fdiv(ux, g.nc[0]);
+      ux -= im * g.nc[0];
+      shx_d = im * g.L[0];
+    } else if (ux < 0 || ux >= g.nc[0]) continue;
+    const T shx = (T)shx_d;
+    for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
+      int uy = cy + dy;
+      double shy_d = 0;
+      if (g.periodic[1]) {
+        int im = fdiv(uy, g.nc[1]);
+        uy -= im * g.nc[1];
+        shy_d = im * g.L[1];
+      } else if (uy < 0 || uy >= g.nc[1]) continue;
+      const T shy = (T)shy_d;
+      for (int dz = -g.range[2]; dz <= g.range[2]; ++dz) {
+        int uz = cz + dz;
+        double shz_d = 0;
+        if (g.periodic[2]) {
+          int im = fdiv(uz, g.nc[2]);
+          uz -= im * g.nc[2];
+          shz_d = im * g.L[2];
+        } else if (uz < 0 || uz >= g.nc[2]) continue;
+        const T shz = (T)shz_d;
+        const int cell = (ux * g.nc[1] + uy) * g.nc[2] + uz;
+        const int beg = a.cstart[cell], end = a.cstart[cell + 1];
+        // image shift in hi + lo parts (exact in FP64; FP32 keeps the rounding of p L)
+        const T shxl = (T)(shx_d - (double)shx), shyl = (T)(shy_d - (double)shy), shzl = (T)(shz_d - (double)shz);
+        for (int j = beg; j < end; ++j) {
+          const V4 xs = a.xs[j];
+          T r0, r1, r2;
+          if (sizeof(T) == 4) {
+            // r = x_target - (x_source + p): every coordinate as hi + lo floats; the sum
+            // x_source_hi + shift is split exactly (Fast2Sum, |shift| >= |x_source|), so the
+            // separation is accurate to the rounding of the final difference
+            const V4 xl = a.xsl[j];
+            const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
+            const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
+            r0 = (xt.x - ax) + ((xtl.x - xl.x) - (shxl + ex));
+            r1 = (xt.y - ay) + ((xtl.y - xl.y) - (shyl + ey));
+            r2 = (xt.z - az) + ((xtl.z - xl.z) - (shzl + ez));
+          } else {
+            r0 = xt.x - (xs.x + shx);
+            r1 = xt.y - (xs.y + shy);
+            r2 = xt.z - (xs.z + shz);
+          }
+          const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
+          if (rr2 >= a.rc2) continue;
+          const T* f = a.fs + (size_t)j * C;
+          if (rr2 == T(0)) {
+            if (a.kernel == SE_STOKESLET) {
+              const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi)
+              for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
+                for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[3 * r + q];
+            }
+            continue;
+          }
+          const T rn = sqrt(rr2);
+          const T inv2 = T(1) / rr2;
+          const T e = exp(-xi2 * rr2);
+          const T ec = dev_erfc(xi * rn) / rn;
+          if (a.kernel == SE_STOKESLET) {
+            // (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e / sqrt pi
+            const T c1 = ec + c2pi * e;
+            const T c0 = c1 - T(2) * c2pi * e;
+            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
+              const T* fr = f + 3 * r;
+              const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1 * inv2;
+              acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
+              acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
+              acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
+            }
+          } else if (a.kernel == SE_ROTLET) {
+            // eps_jlm r_m / r^2 (erfc/r + 2 xi e / sqrt pi) f_l = (f x r)_j c
+            const T c1 = (ec + c2pi * e) * inv2;
+            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
+              const T* fr = f + 3 * r;
+              acc[3 * r + 0] += c1 * (fr[1] * r2 - fr[2] * r1);
+              acc[3 * r + 1] += c1 * (fr[2] * r0 - fr[0] * r2);
+              acc[3 * r + 2] += c1 * (fr[0] * r1 - fr[1] * r0);
+            }
+          } else {
+            // -2 r_j r_l r_m / r^4 (3 erfc/r + (3 + 2 xi^2 r^2) 2 xi e/sqrt pi)
+            //   + (delta_jl r_m + delta_mj r_l + delta_lm r_j) 4 xi^3 e / sqrt pi
+            const T A = T(3) * ec + (T(3) + T(2) * xi2 * rr2) * c2pi * e;
+            const T B = T(2) * xi2 * c2pi * e;
+            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
+              const T* q = f + 6 * r;
+              const T* nu = q + 3;
+              const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
+              const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
+              const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
+              const T c3 = -T(2) * rq * rnu * inv2 * inv2 * A + qn * B;
+              acc[3 * r + 0] += c3 * r0 + B * (q[0] * rnu + nu[0] * rq);
+              acc[3 * r + 1] += c3 * r1 + B * (q[1] * rnu + nu[1] * rq);
+              acc[3 * r + 2] += c3 * r2 + B * (q[2] * rnu + nu[2] * rq);
+            }
+          }
+        }
+      }
+    }
+  }
+  const int i = a.tperm[s];
+  for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
+    for (int q = 0; q < 3; ++q) a.u[((size_t)r * a.ntgt + i) * 3 + q] += acc[3 * r + q];
+}
+
+// sorted positions (wrapped, plan precision, padded to 4) and cell coordinates
+template <typename T>
+__global__ void k_sort_positions(CellGeom g, const double* __restrict__ x, const int* __restrict__ perm,
+                                 int n, typename Vec4<T>::type* __restrict__ xs,
+                                 typename Vec4<T>::type* __restrict__ xsl, int* __restrict__ cell3,
+                                 int* status) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int i = perm[s];
+  double w[3];
+  for (int d = 0; d < 3; ++d) w[d] = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
+  typename Vec4<T>::type v, lo;
+  v.x = (T)w[0];
+  v.y = (T)w[1];
+  v.z = (T)w[2];
+  v.w = T(0);
+  xs[s] = v;
+  lo.x = (T)(w[0] - (double)v.x);
+  lo.y = (T)(w[1] - (double)v.y);
+  lo.z = (T)(w[2] - (double)v.z);
+  lo.w = T(0);
+  if (xsl) xsl[s] = lo;
+  if (cell3) {
+    for (int d = 0; d < 3; ++d) {
+      int cc = (int)floor(w[d] * g.inv_cs[d]);
+      cell3[3 * s + d] = min(max(cc, 0), g.nc[d] - 1);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_sort_rs_strengths(int kernel, const T* __restrict__ f, const int* __restrict__ perm,
+                                    int n, int n_rhs, T* __restrict__ fs) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  int i = perm[s];
+  const int nc = kernel == SE_STRESSLET ? 6 : 3;
+  for (int r = 0; r < n_rhs; ++r)
+    for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = f[((size_t)r * n + i) * nc + c];
+}
+
+// ================================================================ corrections
+//
+// 3P stresslet zero mode, Eq. (k0-stresslet-3p):
+//   u(x) += -8 pi / |B| ( x sum_n (q_n . nu_n) - sum_n x_n (q_n . nu_n) )
+// with the wrapped coordinates. Sums in FP64.
+
+template <typename T>
+__global__ void k_k0_sums(GridGeom g, const double* __restrict__ x, const T* __restrict__ f, int n,
+                          int n_rhs, double* __restrict__ sums, int* status) {
+  // sums[r*4 + 0] = sum qn, sums[r*4 + 1..3] = sum x_n qn
+  __shared__ double red[4][256];
+  for (int r = 0; r < n_rhs; ++r) {
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      const T* q = f + ((size_t)r * n + i) * 6;
+      double qn = (double)q[0] * q[3] + (double)q[1] * q[4] + (double)q[2] * q[5];
+      a0 += qn;
+      a1 += wrap_coord(x[3 * i], g.L[0], 1, status) * qn;
+      a2 += wrap_coord(x[3 * i + 1], g.L[1], 1, status) * qn;
+      a3 += wrap_coord(x[3 * i + 2], g.L[2], 1, status) * qn;
+    }
+    red[0][threadIdx.x] = a0;
+    red[1][threadIdx.x] = a1;
+    red[2][threadIdx.x] = a2;
+    red[3][threadIdx.x] = a3;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+      if (threadIdx.x < off)
+        for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int k = 0; k < 4; ++k) atomicAdd(&sums[r * 4 + k], red[k][0]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_k0_apply(GridGeom g, const double* __restrict__ t, int nt, int n_rhs,
+                           const double* __restrict__ sums, double coef, T* __restrict__ u, int* status) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  double w[3];
+  for (int d = 0; d < 3; ++d) w[d] = wrap_coord(t[3 * i + d], g.L[d], 1, status);
+  for (int r = 0; r < n_rhs; ++r)
+    for (int j = 0; j < 3; ++j)
+      u[((size_t)r * nt + i) * 3 + j] += (T)(coef * (w[j] * sums[r * 4] - sums[r * 4 + 1 + j]));
+}
+
+}  // namespace se
+
+using namespace se;
+
+// ======================================================================= plan creation
+
+static void free_plan(se_plan_t* p) {
+  if (!p) return;
+  if (p->bufs) {
+    for (auto& kv : *p->bufs)
+      if (kv.second.p) cudaFree(kv.second.p);
+    delete p->bufs;
+  }
+  if (p->fwd) {
+    for (auto& kv : *p->fwd) cufftDestroy(kv.second);
+    delete p->fwd;
+  }
+  if (p->inv) {
+    for (auto& kv : *p->inv) cufftDestroy(kv.second);
+    delete p->inv;
+  }
+  if (p->pkb_coef.p) cudaFree(p->pkb_coef.p);
+  for (int d = 0; d < 3; ++d)
+    if (p->gtab[d].p) cudaFree(p->gtab[d].p);
+  if (p->d_status) cudaFree(p->d_status);
+  if (p->pin) cudaFreeHost(p->pin);
+  for (int i = 0; i < 10; ++i)
+    if (p->timers.ev[i]) cudaEventDestroy(p->timers.ev[i]);
+  delete p;
+}
+
+template <typename T>
+static se_status upload(const std::vector<double>& v, DevBuf* b) {
+  std::vector<T> h(v.begin(), v.end());
+  size_t bytes = sizeof(T) * std::max<size_t>(1, h.size());
+  if (cudaMalloc(&b->p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SE_ERR_NOMEM;
+  }
+  b->bytes = bytes;
+  if (!h.empty()) SE_CUDA(cudaMemcpy(b->p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return SE_OK;
+}
+
+static se_status build_tables(se_plan_t* p) {
+  // per-direction scaling tables g_d[i] = exp(-k^2 / 4 xi^2) / w^_0(k)^2 / n_d in FFT order (D = 3)
+  for (int d = 0; d < 3; ++d) {
+    const int n = p->geom.n[d];
+    std::vector<double> g(n);
+    for (int i = 0; i < n; ++i) {
+      int kb = i < n / 2 ? i : i - n;
+      double k = 2.0 * M_PI * kb / (p->geom.h * n);
+      double wh = window_hat(p->win, k);
+      // the 1/n of the inverse DFT (cuFFT transforms are unnormalised) is folded in here
+      g[i] = std::exp(-k * k / (4.0 * p->xi * p->xi)) / (wh * wh) / n;
+    }
+    SE_TRY(p->prec == SE_FP32 ? upload<float>(g, &p->gtab[d]) : upload<double>(g, &p->gtab[d]));
+  }
+  if (p->window == SE_WIN_PKB) {
+    SE_TRY(p->prec == SE_FP32 ? upload<float>(p->win.pkb, &p->pkb_coef)
+                              : upload<double>(p->win.pkb, &p->pkb_coef));
+  }
+  return SE_OK;
+}
+
+extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], double xi, double rc,
+                                    const int M[3], int P, int window, const se_opts* opts) {
+  if (!out) return SE_ERR_ARG;
+  *out = nullptr;
+  if (!box || !M || D < 0 || D > 3) return SE_ERR_ARG;
+  if (!(xi > 0) || !(rc > 0) || !std::isfinite(xi) || !std::isfinite(rc)) return SE_ERR_ARG;
+  if (P < 2 || P > MAX_P || (P & 1)) return SE_ERR_ARG;
+  if (window < SE_WIN_GAUSSIAN || window > SE_WIN_PKB) return SE_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0) || !std::isfinite(box[d])) return SE_ERR_ARG;
+  if (M[0] < 2) return SE_ERR_ARG;
+  if (D != 3) return SE_ERR_UNSUPPORTED;  // reduced periodicity: see se_plan_create_free
+  se_opts o;
+  se_opts_default(&o);
+  if (opts) o = *opts;
+  if (o.prec != SE_FP64 && o.prec != SE_FP32) return SE_ERR_ARG;
+
+  se_plan_t* p = new (std::nothrow) se_plan_t();
+  if (!p) return SE_ERR_NOMEM;
+  p->bufs = new std::map<std::string, DevBuf>();
+  p->fwd = new std::map<int, cufftHandle>();
+  p->inv = new std::map<int, cufftHandle>();
+  p->D = D;
+  for (int d = 0; d < 3; ++d) p->L[d] = box[d];
+  p->xi = xi;
+  p->rc = rc;
+  p->P = P;
+  p->window = window;
+  p->opts = o;
+  p->prec = o.prec;
+  p->stream = (cudaStream_t)o.stream;
+  cudaGetDevice(&p->device);
+
+  const double h = box[0] / M[0];
+  GridGeom& g = p->geom;
+  g.h = h;
+  g.inv_h = 1.0 / h;
+  g.P = P;
+  for (int d = 0; d < 3; ++d) {
+    g.L[d] = box[d];
+    g.periodic[d] = d < D;
+    g.origin[d] = 0.0;
+    double md = box[d] / h;
+    int mi = (int)std::llround(md);
+    if (std::fabs(md - mi) > 1e-9 * md || mi < 2 || (mi & 1) || mi < P) {
+      free_plan(p);
+      return SE_ERR_ARG;
+    }
+    g.m[d] = mi;
+    g.n[d] = mi;
+    g.ntile[d] = cdiv(mi, TS);
+  }
+  window_setup(&p->win, window, P, h);
+  if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    free_plan(p);
+    return SE_ERR_NOMEM;
+  }
+  cudaMemset(p->d_status, 0, sizeof(int));
+  se_status st = build_tables(p);
+  if (st != SE_OK) {
+    free_plan(p);
+    return st;
+  }
+  for (int i = 0; i < 10; ++i) cudaEventCreate(&p->timers.ev[i]);
+  *out = p;
+  return SE_OK;
+}
+
+extern "C" void se_destroy(se_plan_h p) { free_plan(p); }
+
+extern "C" se_status se_set_timing(se_plan_h p, int on) {
+  if (!p) return SE_ERR_ARG;
+  p->timers.on = on != 0;
+  return SE_OK;
+}
+
+extern "C" se_status se_get_info(se_plan_h p, se_info* info) {
+  if (!p || !info) return SE_ERR_ARG;
+  std::memset(info, 0, sizeof(*info));
+  info->h = p->geom.h;
+  info->R = p->R;
+  info->s0 = p->s0;
+  info->s_star = p->s_star;
+  info->kbar_star = p->kbar_star;
+  info->P = p->P;
+  for (int d = 0; d < 3; ++d) {
+    info->n[d] = p->geom.n[d];
+    info->m[d] = p->geom.m[d];
+    info->dL[d] = p->dL[d];
+  }
+  if (p->timed_pending) {
+    SE_CUDA(cudaEventSynchronize(p->timers.ev[8]));
+    for (int i = 0; i < 8; ++i) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, p->timers.ev[i], p->timers.ev[i + 1]);
+      p->times_ms[i] = ms;
+    }
+    p->timed_pending = false;
+  }
+  for (int i = 0; i < 8; ++i) info->times_ms[i] = p->times_ms[i];
+  info->launches = p->launches;
+  return SE_OK;
+}
+
+extern "C" se_status se_sync(se_plan_h p) {
+  if (!p) return SE_ERR_ARG;
+  SE_CUDA(cudaStreamSynchronize(p->stream));
+  int st = 0;
+  SE_CUDA(cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    cudaMemset(p->d_status, 0, sizeof(int));
+    return (st & 2) ? SE_ERR_TIMEOUT : SE_ERR_RANGE;
+  }
+  return SE_OK;
+}
+
+extern "C" se_status se_debug_grid(se_plan_h p, void* dst, unsigned long long bytes) {
+  if (!p || !dst) return SE_ERR_ARG;
+  auto it = p->bufs->find("grid");
+  if (it == p->bufs->end() || p->last_grid_comps == 0) return SE_ERR_ARG;
+  size_t es = p->prec == SE_FP32 ? 4 : 8;
+  size_t need = es * (size_t)p->last_grid_comps * p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
+  if (bytes < need) return SE_ERR_ARG;
+  SE_CUDA(cudaStreamSynchronize(p->stream));
+  SE_CUDA(cudaMemcpy(dst, it->second.p, need, cudaMemcpyDeviceToHost));
+  return SE_OK;
+}
+
+// ======================================================================== evaluation
+
+namespace {
+
+struct Stage {
+  se_plan_t* p;
+  int idx = 0;
+  void mark() {
+    if (p->timers.on) cudaEventRecord(p->timers.ev[idx], p->stream);
+    ++idx;
+  }
+};
+
+se_status get_fft(se_plan_t* p, bool forward, int batch, cufftHandle* out) {
+  auto& mp = forward ? *p->fwd : *p->inv;
+  auto it = mp.find(batch);
+  if (it != mp.end()) {
+    *out = it->second;
+    return SE_OK;
+  }
+  cufftHandle h;
+  int n[3] = {p->geom.n[0], p->geom.n[1], p->geom.n[2]};
+  long long G = (long long)n[0] * n[1] * n[2];
+  long long H = (long long)n[0] * n[1] * (n[2] / 2 + 1);
+  cufftType t;
+  if (p->prec == SE_FP32) t = forward ? CUFFT_R2C : CUFFT_C2R;
+  else t = forward ? CUFFT_D2Z : CUFFT_Z2D;
+  SE_CUFFT(cufftPlanMany(&h, 3, n, nullptr, 1, forward ? (int)G : (int)H, nullptr, 1,
+                         forward ? (int)H : (int)G, t, batch));
+  SE_CUFFT(cufftSetStream(h, p->stream));
+  mp[batch] = h;
+  *out = h;
+  return SE_OK;
+}
+
+template <typename T>
+se_status fft_exec(cufftHandle h, bool forward, T* real, T* cplx);
+template <>
+se_status fft_exec<float>(cufftHandle h, bool forward, float* real, float* cplx) {
+  if (forward) SE_CUFFT(cufftExecR2C(h, real, (cufftComplex*)cplx));
+  else SE_CUFFT(cufftExecC2R(h, (cufftComplex*)cplx, real));
+  return SE_OK;
+}
+template <>
+se_status fft_exec<double>(cufftHandle h, bool forward, double* real, double* cplx) {
+  if (forward) SE_CUFFT(cufftExecD2Z(h, real, (cufftDoubleComplex*)cplx));
+  else SE_CUFFT(cufftExecZ2D(h, (cufftDoubleComplex*)cplx, real));
+  return SE_OK;
+}
+
+template <typename T, int CMAX>
+void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C,
+                   T* grid) {
+  dim3 grd(p->geom.ntile[0], p->geom.ntile[1], p->geom.ntile[2]);
+  ++p->launches;
+  k_spread<T, CMAX><<<grd, 256, 0, p->stream>>>(p->geom, tile_start, base, w, sf, C, grid);
+}
+
+template <typename T, int NC>
+void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, const T* F, int nt, int NCr,
+                   T scale, T* u) {
+  ++p->launches;
+  k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u);
+}
+
+template <typename T, int R>
+void real_launch(se_plan_t* p, const RealArgs<T>& a) {
+  ++p->launches;
+  k_real<T, R><<<grid1d(a.ntgt, 128), 128, 0, p->stream>>>(a);
+}
+
+template <typename T>
+se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const double* src,
+                    const T* strengths, int n_rhs, long long n_tgt, const double* tgt, T* u) {
+  const bool star = (tgt == nullptr);
+  const int N = (int)n_src;
+  const int NT = star ? N : (int)n_tgt;
+  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const int C = cin * n_rhs;    // spread components
+  const int NC = 3 * n_rhs;     // output components
+  if (C > MAX_COMP || n_rhs > 16) return SE_ERR_UNSUPPORTED;
+  const GridGeom& g = p->geom;
+  cudaStream_t st = p->stream;
+  Stage stage{p};
+  for (int i = 0; i < 8; ++i) p->times_ms[i] = -1;
+  p->launches = 0;
+  stage.mark();  // 0
+
+  if (!(parts & SE_PART_FOURIER)) SE_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * (size_t)NC * NT, st));
+
+  // ---------------- Fourier-space part (Alg. 1)
+  if (parts & SE_PART_FOURIER) {
+    const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
+    int *perm, *tstart;
+    SE_TRY(counting_sort(p, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart));
+    void *base, *wts, *sf;
+    SE_TRY(buf(p, "base", sizeof(int) * 3 * (size_t)std::max(N, 1), &base));
+    SE_TRY(buf(p, "wts", sizeof(T) * 3 * g.P * (size_t)std::max(N, 1), &wts));
+    SE_TRY(buf(p, "sf", sizeof(T) * C * (size_t)std::max(N, 1), &sf));
+    WinArgs<T> wa;
+    wa.kind = p->window;
+    wa.P = g.P;
+    wa.nu = p->win.nu;
+    wa.alpha = (T)p->win.alpha;
+    wa.beta = (T)p->win.beta;
+    wa.inv_i0beta = (T)(1.0 / p->win.i0beta);
+    wa.pkb = (const T*)p->pkb_coef.p;
+    if (N > 0) {
+      ++p->launches;
+      k_weights<T><<<grid1d(N, 128), 128, 0, st>>>(g, wa, src, perm, N, (int*)base, (T*)wts, p->d_status);
+      ++p->launches;
+      k_sort_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, strengths, perm, N, n_rhs, (T*)sf);
+    }
+    stage.mark();  // 1: bin + weights
+    const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
+    void *grid, *spec, *ugrid;
+    SE_TRY(buf(p, "grid", sizeof(T) * C * G, &grid));
+    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
+    SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
+    if (C <= 3) spread_launch<T, 3>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    else if (C <= 6) spread_launch<T, 6>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    else if (C <= 12) spread_launch<T, 12>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    else if (C <= 24) spread_launch<T, 24>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    else spread_launch<T, 48>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    SE_CUDA(cudaGetLastError());
+    p->last_grid_comps = C;
+    stage.mark();  // 2: spread
+    cufftHandle hf, hi;
+    SE_TRY(get_fft(p, true, C, &hf));
+    SE_TRY(get_fft(p, false, NC, &hi));
+    SE_TRY(fft_exec<T>(hf, true, (T*)grid, (T*)spec));
+    stage.mark();  // 3: fft
+    ScaleArgs<T> sa;
+    sa.n0 = g.n[0];
+    sa.n1 = g.n[1];
+    sa.n2 = g.n[2];
+    sa.h2 = g.n[2] / 2 + 1;
+    sa.kf0 = (T)(2.0 * M_PI / g.L[0]);
+    sa.kf1 = (T)(2.0 * M_PI / g.L[1]);
+    sa.kf2 = (T)(2.0 * M_PI / g.L[2]);
+    sa.inv4xi2 = (T)(1.0 / (4.0 * p->xi * p->xi));
+    sa.g0 = (const T*)p->gtab[0].p;
+    sa.g1 = (const T*)p->gtab[1].p;
+    sa.g2 = (const T*)p->gtab[2].p;
+    ++p->launches;
+    k_scale3p<T><<<grid1d((long long)H, 256), 256, 0, st>>>(sa, kernel, n_rhs, (T*)spec);
+    SE_CUDA(cudaGetLastError());
+    stage.mark();  // 4: scale
+    SE_TRY(fft_exec<T>(hi, false, (T*)ugrid, (T*)spec));
+    stage.mark();  // 5: ifft
+    // targets: star form reuses the sorted sources and their weights
+    const int *tperm = perm, *tbase = (int*)base;
+    const T* tw = (T*)wts;
+    if (!star) {
+      int *perm2, *tstart2;
+      SE_TRY(counting_sort(p, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2));
+      void *base2, *wts2;
+      SE_TRY(buf(p, "tbase", sizeof(int) * 3 * (size_t)std::max(NT, 1), &base2));
+      SE_TRY(buf(p, "twts", sizeof(T) * 3 * g.P * (size_t)std::max(NT, 1), &wts2));
+      if (NT > 0) {
+        ++p->launches;
+        k_weights<T><<<grid1d(NT, 128), 128, 0, st>>>(g, wa, tgt, perm2, NT, (int*)base2, (T*)wts2,
+                                                      p->d_status);
+      }
+      tperm = perm2;
+      tbase = (int*)base2;
+      tw = (T*)wts2;
+    }
+    const T scale = (T)(g.h * g.h * g.h);
+    if (NT > 0) {
+      if (NC <= 3) gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      else if (NC <= 6) gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      else if (NC <= 12) gather_launch<T, 12>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      else if (NC <= 24) gather_launch<T, 24>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      else gather_launch<T, 48>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+    }
+    SE_CUDA(cudaGetLastError());
+    stage.mark();  // 6: gather
+  } else {
+    for (int i = 0; i < 6; ++i) stage.mark();
+  }
+
+  // ---------------- real-space part
+  if (parts & (SE_PART_REAL | SE_PART_CORR)) {
+    CellGeom cg;
+    const int S = 2;
+    for (int d = 0; d < 3; ++d) {
+      int nc = (int)std::floor(S * p->L[d] / p->rc);
+      nc = std::max(1, std::min(nc, 128));
+      cg.nc[d] = nc;
+      double cs = p->L[d] / nc;
+      cg.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
+      cg.periodic[d] = d < p->D;
+      cg.L[d] = p->L[d];
+      cg.inv_cs[d] = 1.0 / cs;
+    }
+    const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
+    int *sperm, *cstart;
+    SE_TRY(counting_sort(p, "cell", N, ncell, cell_keyfun, src, &cg, &sperm, &cstart));
+    typedef typename Vec4<T>::type V4;
+    void *xs, *fs, *xsl;
+    SE_TRY(buf(p, "rs.xs", sizeof(V4) * (size_t)std::max(N, 1), &xs));
+    SE_TRY(buf(p, "rs.xsl", sizeof(V4) * (size_t)std::max(N, 1), &xsl));
+    SE_TRY(buf(p, "rs.fs", sizeof(T) * C * (size_t)std::max(N, 1), &fs));
+    void* tcell;
+    SE_TRY(buf(p, "rs.tcell", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcell));
+    if (N > 0) {
+      ++p->launches;
+      k_sort_positions<T><<<grid1d(N, 256), 256, 0, st>>>(cg, src, sperm, N, (V4*)xs, (V4*)xsl,
+                                                          star ? (int*)tcell : nullptr, p->d_status);
+      ++p->launches;
+      k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, strengths, sperm, N, n_rhs, (T*)fs);
+    }
+    const V4* xt = (V4*)xs;
+    const V4* xtl = (V4*)xsl;
+    const int* tperm = sperm;
+    if (!star) {
+      int *tp2, *ts2;
+      SE_TRY(counting_sort(p, "tcellsort", NT, ncell, cell_keyfun, tgt, &cg, &tp2, &ts2));
+      void *xt2, *xtl2;
+      SE_TRY(buf(p, "rs.xt", sizeof(V4) * (size_t)std::max(NT, 1), &xt2));
+      SE_TRY(buf(p, "rs.xtl", sizeof(V4) * (size_t)std::max(NT, 1), &xtl2));
+      if (NT > 0) {
+        ++p->launches;
+        k_sort_positions<T><<<grid1d(NT, 256), 256, 0, st>>>(cg, tgt, tp2, NT, (V4*)xt2, (V4*)xtl2,
+                                                             (int*)tcell, p->d_status);
+      }
+      xt = (V4*)xt2;
+      xtl = (V4*)xtl2;
+      tperm = tp2;
+    }
+    if ((parts & SE_PART_REAL) && NT > 0) {
+      RealArgs<T> ra;
+      ra.cg = cg;
+      ra.xi = (T)p->xi;
+      ra.rc2 = (T)(p->rc * p->rc);
+      ra.kernel = kernel;
+      ra.n_rhs = n_rhs;
+      ra.nsrc = N;
+      ra.ntgt = NT;
+      ra.xs = (V4*)xs;
+      ra.xsl = (V4*)xsl;
+      ra.xtl = xtl;
+      ra.fs = (T*)fs;
+      ra.cstart = cstart;
+      ra.xt = xt;
+      ra.tperm = tperm;
+      ra.tcell = (int*)tcell;
+      ra.u = u;
+      if (n_rhs <= 1) real_launch<T, 1>(p, ra);
+      else if (n_rhs <= 4) real_launch<T, 4>(p, ra);
+      else if (n_rhs <= 8) real_launch<T, 8>(p, ra);
+      else real_launch<T, 16>(p, ra);
+      SE_CUDA(cudaGetLastError());
+    }
+  }
+  stage.mark();  // 7: real
+
+  // ---------------- corrections (self term lives in the real-space pair loop)
+  if ((parts & SE_PART_CORR) && p->D == 3 && kernel == SE_STRESSLET && N > 0 && NT > 0) {
+    void* sums;
+    SE_TRY(buf(p, "k0sums", sizeof(double) * 4 * n_rhs, &sums));
+    SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * n_rhs, st));
+    ++p->launches;
+    k_k0_sums<T><<<std::min(grid1d(N, 256), 152), 256, 0, st>>>(g, src, strengths, N, n_rhs, (double*)sums,
+                                                                p->d_status);
+    const double vol = p->L[0] * p->L[1] * p->L[2];
+    ++p->launches;
+    k_k0_apply<T><<<grid1d(NT, 256), 256, 0, st>>>(g, star ? src : tgt, NT, n_rhs, (double*)sums,
+                                                  -8.0 * M_PI / vol, u, p->d_status);
+    SE_CUDA(cudaGetLastError());
+  }
+  stage.mark();  // 8: corrections
+  p->timed_pending = p->timers.on;
+  return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status se_eval_parts(se_plan_h p, int kernel, int parts, long long n_src, const double* src,
+                                   const void* strengths, int n_rhs, long long n_tgt, const double* tgt,
+                                   void* u) {
+  if (!p || !u || (n_src > 0 && (!src || !strengths))) return SE_ERR_ARG;
+  if (n_src < 0 || n_src > 0x7fffffffLL || n_rhs < 1) return SE_ERR_ARG;
+  if (tgt && (n_tgt < 0 || n_tgt > 0x7fffffffLL)) return SE_ERR_ARG;
+  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET) {
+    if (kernel == (SE_STOKESLET | SE_STRESSLET)) return SE_ERR_UNSUPPORTED;
+    return SE_ERR_ARG;
+  }
+  if (parts <= 0 || parts > SE_PART_ALL) return SE_ERR_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return SE_ERR_CUDA;
+  if (p->prec == SE_FP32)
+    return eval_impl<float>(p, kernel, parts, n_src, src, (const float*)strengths, n_rhs, n_tgt, tgt,
+                            (float*)u);
+  return eval_impl<double>(p, kernel, parts, n_src, src, (const double*)strengths, n_rhs, n_tgt, tgt,
+                           (double*)u);
+}
+
+extern "C" se_status se_eval(se_plan_h p, int kernel, long long n_src, const double* src,
+                             const void* strengths, int n_rhs, long long n_tgt, const double* tgt, void* u) {
+  return se_eval_parts(p, kernel, SE_PART_ALL, n_src, src, strengths, n_rhs, n_tgt, tgt, u);
+}
+
+extern "C" se_status se_eval_host(se_plan_h p, int kernel, long long n_src, const double* src,
+                                  const void* strengths, int n_rhs, long long n_tgt, const double* tgt,
+                                  void* u) {
+  if (!p || !u || !src || !strengths || n_src < 0 || n_rhs < 1) return SE_ERR_ARG;
+  const bool star = tgt == nullptr;
+  const long long NT = star ? n_src : n_tgt;
+  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const size_t es = p->prec == SE_FP32 ? 4 : 8;
+  const size_t bx = sizeof(double) * 3 * (size_t)n_src;
+  const size_t bf = es * cin * (size_t)n_rhs * n_src;
+  const size_t bt = star ? 0 : sizeof(double) * 3 * (size_t)NT;
+  const size_t bu = es * 3 * (size_t)n_rhs * NT;
+  void *dx, *df, *dt = nullptr, *du;
+  SE_TRY(buf(p, "host.x", bx, &dx));
+  SE_TRY(buf(p, "host.f", bf, &df));
+  if (!star) SE_TRY(buf(p, "host.t", bt, &dt));
+  SE_TRY(buf(p, "host.u", bu, &du));
+  SE_CUDA(cudaMemcpyAsync(dx, src, bx, cudaMemcpyHostToDevice, p->stream));
+  SE_CUDA(cudaMemcpyAsync(df, strengths, bf, cudaMemcpyHostToDevice, p->stream));
+  if (!star) SE_CUDA(cudaMemcpyAsync(dt, tgt, bt, cudaMemcpyHostToDevice, p->stream));
+  SE_TRY(se_eval(p, kernel, n_src, (const double*)dx, df, n_rhs, n_tgt, (const double*)dt, du));
+  SE_CUDA(cudaMemcpyAsync(u, du, bu, cudaMemcpyDeviceToHost, p->stream));
+  return se_sync(p);
+}

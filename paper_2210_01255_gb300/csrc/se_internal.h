@@ -1,0 +1,128 @@
+// Internal declarations of libse: the plan object, launch helpers and kernel entry points.
+// Everything here is private to the shared library; the public interface is include/se.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/se.h"
+
+namespace se {
+
+constexpr int TS = 8;          // spread/gather tile edge (grid points)
+constexpr int MAX_P = 32;      // largest window support
+constexpr int MAX_COMP = 48;   // largest number of spread components (16 RHS x 3)
+
+// Geometry of the grid that gridding writes and gathering reads (Sec. 3.2).
+struct GridGeom {
+  int m[3];         // extent of the spread grid per direction (M_i periodic, M'_i free)
+  int n[3];         // allocated extent of the (possibly zero-padded) FFT grid
+  int periodic[3];  // 1 for the first D directions
+  int ntile[3];     // tiles of TS grid points covering [0, m)
+  double origin[3]; // grid origin o_i: 0 periodic, -dL_i/2 free (Eq. extended-box)
+  double h, inv_h;
+  double L[3];
+  int P;
+};
+
+// Host-side description of the window (Sec. 3.3).
+struct WindowDesc {
+  int kind;      // SE_WIN_*
+  int P;
+  double aw;     // a_w = P h / 2
+  double alpha;  // Gaussian shape (Eq. TG-window)
+  double beta;   // KB shape (Eq. PKB-parameters)
+  double i0beta; // I_0(beta)
+  int nu;        // PKB degree
+  std::vector<double> pkb;  // P x (nu+1) Chebyshev coefficients in the local variable s in [-1,1]
+};
+
+// A growable device buffer.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct Timers {
+  cudaEvent_t ev[10] = {};
+  bool on = false;
+};
+
+}  // namespace se
+
+struct se_plan_t {
+  int D = 3;
+  double L[3] = {1, 1, 1};
+  double xi = 0, rc = 0;
+  int P = 0;
+  int window = SE_WIN_PKB;
+  se_opts opts{};
+  int prec = SE_FP64;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+
+  se::GridGeom geom{};
+  se::WindowDesc win{};
+  double R = 0, s0 = 0, s_star = 0;
+  int kbar_star = 0;
+  double dL[3] = {0, 0, 0};
+
+  // device tables
+  se::DevBuf pkb_coef;     // P*(nu+1) in the plan precision
+  se::DevBuf gtab[3];      // per-direction exp(-k^2/4xi^2) / w^(k)^2, FFT order (plan precision)
+
+  // growable scratch
+  std::map<std::string, se::DevBuf>* bufs = nullptr;
+
+  // cuFFT plans keyed by batch count (forward R2C and inverse C2R)
+  std::map<int, cufftHandle>* fwd = nullptr;
+  std::map<int, cufftHandle>* inv = nullptr;
+
+  // pinned host staging for se_eval_host
+  void* pin = nullptr;
+  size_t pin_bytes = 0;
+
+  // device status word (range errors, timeouts)
+  int* d_status = nullptr;
+
+  se::Timers timers;
+  float times_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
+  int last_grid_comps = 0;
+  bool timed_pending = false;
+  int launches = 0;  // kernels launched by the last evaluation
+};
+
+namespace se {
+
+// buffer helper: returns device pointer with at least `bytes` bytes (grows, never shrinks)
+se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out);
+
+// ---- host-side helpers (se_host.cpp) ----
+double bessel_i0(double x);
+void window_setup(WindowDesc* w, int kind, int P, double h);
+double window_hat(const WindowDesc& w, double k);
+double window_value(const WindowDesc& w, double r);
+
+}  // namespace se
+
+#define SE_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return SE_ERR_CUDA;          \
+  } while (0)
+#define SE_CUFFT(call)                                  \
+  do {                                                  \
+    cufftResult r_ = (call);                            \
+    if (r_ != CUFFT_SUCCESS) return SE_ERR_CUFFT;       \
+  } while (0)
+#define SE_TRY(call)                                    \
+  do {                                                  \
+    se_status s_ = (call);                              \
+    if (s_ != SE_OK) return s_;                         \
+  } while (0)

@@ -1,0 +1,63 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle checks.
+
+Holds no arithmetic of the method: only random point clouds and strengths with the shapes
+and distributions of the paper's random systems (Sec. 4.1: uniform points in the primary
+cell; Sec. 5.2: clustered systems) and of the benchmark configurations.
+"""
+import numpy as np
+
+
+def uniform_points(n, box, seed):
+    """n points uniform in [0,L1) x [0,L2) x [0,L3)."""
+    rng = np.random.default_rng(seed)
+    return rng.random((n, 3)) * np.asarray(box, dtype=float)
+
+
+def clustered_points(n, seed, sigma=0.05, centre=(0.5, 0.5, 0.5)):
+    """Half uniform in the unit cube, half normal around the centre (resampled into the cube)."""
+    rng = np.random.default_rng(seed)
+    nu = n // 2
+    out = np.empty((n, 3))
+    out[:nu] = rng.random((nu, 3))
+    k = nu
+    while k < n:
+        y = rng.normal(centre, sigma, size=(n - k, 3))
+        ok = np.all((y >= 0) & (y < 1), axis=1)
+        y = y[ok]
+        out[k:k + y.shape[0]] = y
+        k += y.shape[0]
+    return out
+
+
+def strengths(kernel, n, seed, n_rhs=None):
+    """Stokeslet / rotlet: f ~ N(0,1)^3. Stresslet: (q, nu) with q ~ N(0,1)^3 and nu ~ N(0,1)^3
+    normalised to unit length. Shape (n, c) or (n_rhs, n, c)."""
+    rng = np.random.default_rng(seed)
+    shape = (n,) if n_rhs is None else (n_rhs, n)
+    if kernel in ("stresslet", 4):
+        q = rng.standard_normal(shape + (3,))
+        nu = rng.standard_normal(shape + (3,))
+        nu /= np.linalg.norm(nu, axis=-1, keepdims=True)
+        return np.concatenate([q, nu], axis=-1)
+    return rng.standard_normal(shape + (3,))
+
+
+def source_quantity(kernel, f):
+    """Q of Eq. (vector-source-quantity) / (tensor-source-quantity) for one RHS."""
+    f = np.asarray(f, dtype=float)
+    if kernel in ("stresslet", 4):
+        t = f[..., :3, None] * f[..., None, 3:]
+        return float(np.sum(t * t))
+    return float(np.sum(f * f))
+
+
+# The benchmark configurations (names describe the workload and its sizes).
+CONFIGS = {
+    "3p_stokeslet_n1000": dict(D=3, box=(1.0, 1.0, 1.0), N=1000, kernels=("stokeslet",),
+                               tol=1e-10, prec="fp64", window="gaussian", seed=0, n_rhs=1),
+    "3p_stresslet_rotlet_n20000": dict(D=3, box=(1.0, 1.0, 1.0), N=20000,
+                                       kernels=("stresslet", "rotlet"), tol=1e-6, prec="fp32",
+                                       window="pkb", seed=1, n_rhs=1),
+    "2p_stokeslet_n200000_rhs8": dict(D=2, box=(1.0, 1.0, 0.5), N=200000, kernels=("stokeslet",),
+                                      tol=1e-6, prec="fp32", window="pkb", seed=2, n_rhs=8),
+}

@@ -1,0 +1,72 @@
+"""The C-ABI library loads and exports every symbol include/se.h declares; host-only logic
+(parameter selection, argument validation) runs without a GPU."""
+import math
+import os
+import re
+
+import pytest
+
+import paper_2210_01255_gb300 as se
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "se.h")).read()
+    return sorted(set(re.findall(r"\b(se_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = se.lib()
+    names = _declared()
+    assert "se_eval" in names and "se_plan_create" in names
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(se.SIGNATURES), "binding and header disagree"
+
+
+def test_status_strings():
+    assert se.se_status_str(0) == "ok"
+    assert "unsupported" in se.se_status_str(-7)
+
+
+def test_plan_argument_validation_without_gpu():
+    # invalid arguments are rejected before any device work
+    for args in [(4, (1, 1, 1), 10.0, 0.3, (32, 32, 32), 8, 2),     # periodicity
+                 (3, (1, 1, 1), -1.0, 0.3, (32, 32, 32), 8, 2),    # xi
+                 (3, (1, 1, 1), 10.0, 0.3, (32, 32, 32), 7, 2),    # odd P
+                 (3, (1, 1, 1), 10.0, 0.3, (32, 32, 32), 8, 9)]:   # window
+        with pytest.raises(se.SeError) as e:
+            se.se_plan_create(*args)
+        assert e.value.code == -1
+
+
+# Table 6 of the paper (uniform system): xi from the neighbour count of Table 5 at N = 1e5,
+# L = 1, Q = 1 and an absolute real-space tolerance of 1e-8 (Sec. 5.2).
+TABLE6 = {("stokeslet", 0): 23.5579, ("stokeslet", 1): 32.3804, ("stokeslet", 2): 41.3955,
+          ("stokeslet", 3): 43.0296, ("stresslet", 0): 19.9813, ("stresslet", 1): 31.1944,
+          ("stresslet", 2): 39.4021, ("stresslet", 3): 39.4021, ("rotlet", 0): 24.5091,
+          ("rotlet", 1): 33.9754, ("rotlet", 2): 43.7207, ("rotlet", 3): 45.4936}
+
+
+@pytest.mark.parametrize("key", sorted(TABLE6))
+def test_autotune_reproduces_table6_xi(key):
+    kernel, D = key
+    o = se.se_opts_default()
+    o.tol_abs = 1e-8
+    r = se.se_autotune(D, (1, 1, 1), se.KERNELS[kernel], 1.0, 100000, 0.0, opts=o, xi=0.0)
+    assert abs(r["xi"] - TABLE6[key]) < 5e-5
+
+
+def test_autotune_rules():
+    # Sec. 4.6 steps on a case of Sec. 4.6 (N=1000, L=1, Q=1, xi=10)
+    o = se.se_opts_default()
+    o.tol_abs = 1e-8
+    r = se.se_autotune(3, (1, 1, 1), se.STOKESLET, 1.0, 1000, 0.0, opts=o, xi=10.0)
+    assert r["P"] % 2 == 0 and r["M"][0] % 4 == 0 and r["M"][0] == r["M"][1] == r["M"][2]
+    # free directions: extended grid of Eq. (extended-grid-size) and s0 of Eq. (upsampling-factor-s0)
+    r0 = se.se_autotune(0, (1, 1, 1), se.STOKESLET, 1.0, 1000, 0.0, opts=o, xi=10.0)
+    M, P = r0["M"][0], r0["P"]
+    Mext = r0["opts"].Mext[0]
+    assert Mext == 4 * math.ceil((M + P + 1.2 * max(P, 8)) / 4)
+    assert abs(r0["opts"].s0 - math.ceil(10 * (1 + math.sqrt(3))) / 10) < 1e-12
