@@ -280,58 +280,72 @@ __global__ void k_sort_strengths(int kernel, const T* __restrict__ f, const int*
 // whose windows reach the tile. No atomics; each grid value is written once.
 
 constexpr int SP_CHUNK = 64;
+constexpr int SP_MAXB = 12;  // max (bin, image) pairs per direction (P <= 32 <= m needs <= 8)
 
+// The source tiles whose points can reach the output tile starting at o (extent TS) along
+// one direction, as (wrapped tile index, grid shift) pairs: a point in cell c reaches the
+// tile iff c in [o - P/2, o + TS - 2 + P/2]. In a periodic direction that cell range is
+// split at multiples of m into one segment per image; each segment maps to whole tiles of
+// the wrapped grid, so no tile is visited twice for the same image.
+__device__ inline int tile_list(const GridGeom& g, int d, int o, int* bins, int* shift) {
+  const int P = g.P, m = g.m[d];
+  int clo = o - P / 2, chi = o + TS - 2 + P / 2;
+  int nb = 0;
+  if (!g.periodic[d]) {
+    clo = max(clo, 0);
+    chi = min(chi, m - 1);
+    for (int b = clo / TS; b <= chi / TS && nb < SP_MAXB; ++b) {
+      bins[nb] = b;
+      shift[nb] = 0;
+      ++nb;
+    }
+    return nb;
+  }
+  int c = clo;
+  while (c <= chi && nb < SP_MAXB) {
+    const int im = fdiv(c, m);
+    const int seg_hi = min(chi, (im + 1) * m - 1);
+    const int a = c - im * m, e = seg_hi - im * m;  // wrapped cells a..e
+    for (int b = a / TS; b <= e / TS && nb < SP_MAXB; ++b) {
+      bins[nb] = b;
+      shift[nb] = im * m;
+      ++nb;
+    }
+    c = seg_hi + 1;
+  }
+  return nb;
+}
+
+// Gridding, Eq. (SE-gridding-disc). Output-driven: the CTA (tile t, slab j) owns the TS^3
+// tile t and the j-th of the source-tile slabs along direction 0; each thread accumulates
+// two grid points along direction 0 over all points of the slab's tiles in registers, and
+// the partial tile is added to the (zeroed) grid. With nslab = 1 the tile is stored.
 template <typename T, int CMAX>
 __global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restrict__ tile_start,
                                                 const int* __restrict__ base, const T* __restrict__ wts,
-                                                const T* __restrict__ sf, int C, T* __restrict__ grid) {
+                                                const T* __restrict__ sf, int C, int nslab, T* __restrict__ grid) {
   __shared__ T s_w[SP_CHUNK][3 * TS];
   __shared__ T s_f[SP_CHUNK][CMAX];
   const int P = g.P;
   const int tid = threadIdx.x;
   const int lz = tid & 7, ly = (tid >> 3) & 7, lx0 = (tid >> 6) * 2;
-  const int t0 = blockIdx.x, t1 = blockIdx.y, t2 = blockIdx.z;
+  const int slab = blockIdx.x % nslab;
+  const int t0 = blockIdx.x / nslab, t1 = blockIdx.y, t2 = blockIdx.z;
   const int o[3] = {t0 * TS, t1 * TS, t2 * TS};
   T acc0[CMAX], acc1[CMAX];
 #pragma unroll
   for (int c = 0; c < CMAX; ++c) acc0[c] = acc1[c] = T(0);
 
-  // range of source tiles whose points can reach this tile: cell c reaches [o, o+TS) iff
-  // c in [o - P/2, o + TS - 2 + P/2]; one extra tile on each side of a periodic direction
-  // whose extent is not a multiple of TS (the wrapped tile is partial)
-  int lo[3], hi[3];
-  for (int d = 0; d < 3; ++d) {
-    lo[d] = fdiv(o[d] - P / 2, TS);
-    hi[d] = fdiv(o[d] + TS - 2 + P / 2, TS);
-    if (g.periodic[d] && (g.m[d] % TS)) {
-      lo[d] -= 1;
-      hi[d] += 1;
-    }
-  }
-  for (int b0 = lo[0]; b0 <= hi[0]; ++b0) {
-    int w0 = b0, sh0 = 0;
-    if (g.periodic[0]) {
-      int im = fdiv(b0, g.ntile[0]);
-      w0 = b0 - im * g.ntile[0];
-      sh0 = im * g.m[0];
-    } else if (b0 < 0 || b0 >= g.ntile[0]) continue;
-    for (int b1 = lo[1]; b1 <= hi[1]; ++b1) {
-      int w1 = b1, sh1 = 0;
-      if (g.periodic[1]) {
-        int im = fdiv(b1, g.ntile[1]);
-        w1 = b1 - im * g.ntile[1];
-        sh1 = im * g.m[1];
-      } else if (b1 < 0 || b1 >= g.ntile[1]) continue;
-      for (int b2 = lo[2]; b2 <= hi[2]; ++b2) {
-        int w2 = b2, sh2 = 0;
-        if (g.periodic[2]) {
-          int im = fdiv(b2, g.ntile[2]);
-          w2 = b2 - im * g.ntile[2];
-          sh2 = im * g.m[2];
-        } else if (b2 < 0 || b2 >= g.ntile[2]) continue;
-        const int bin = (w0 * g.ntile[1] + w1) * g.ntile[2] + w2;
+  __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
+  if (tid < 3) s_nb[tid] = tile_list(g, tid, o[tid], s_bin[tid], s_sh[tid]);
+  __syncthreads();
+  const int nbx = s_nb[0], nby = s_nb[1], nbz = s_nb[2];
+  for (int ix = slab; ix < nbx; ix += nslab) {
+    for (int iy = 0; iy < nby; ++iy) {
+      for (int iz = 0; iz < nbz; ++iz) {
+        const int bin = (s_bin[0][ix] * g.ntile[1] + s_bin[1][iy]) * g.ntile[2] + s_bin[2][iz];
         const int beg = tile_start[bin], end = tile_start[bin + 1];
-        const int rel0 = sh0 - o[0], rel1 = sh1 - o[1], rel2 = sh2 - o[2];
+        const int rel0 = s_sh[0][ix] - o[0], rel1 = s_sh[1][iy] - o[1], rel2 = s_sh[2][iz] - o[2];
         for (int p0 = beg; p0 < end; p0 += SP_CHUNK) {
           const int cnt = min(SP_CHUNK, end - p0);
           __syncthreads();
@@ -347,7 +361,24 @@ __global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restric
             s_f[pp][c] = sf[(size_t)(p0 + pp) * C + c];
           }
           __syncthreads();
-          for (int pp = 0; pp < cnt; ++pp) {
+          int pp = 0;
+          for (; pp + 1 < cnt; pp += 2) {
+            const T wyz0 = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
+            const T wyz1 = s_w[pp + 1][TS + ly] * s_w[pp + 1][2 * TS + lz];
+            if (wyz0 != T(0) || wyz1 != T(0)) {
+              const T wa0 = s_w[pp][lx0] * wyz0, wb0 = s_w[pp][lx0 + 1] * wyz0;
+              const T wa1 = s_w[pp + 1][lx0] * wyz1, wb1 = s_w[pp + 1][lx0 + 1] * wyz1;
+#pragma unroll
+              for (int c = 0; c < CMAX; ++c) {
+                if (c < C) {
+                  const T f0 = s_f[pp][c], f1 = s_f[pp + 1][c];
+                  acc0[c] += wa0 * f0 + wa1 * f1;
+                  acc1[c] += wb0 * f0 + wb1 * f1;
+                }
+              }
+            }
+          }
+          if (pp < cnt) {
             const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
             if (wyz != T(0)) {
               const T wa = s_w[pp][lx0] * wyz, wb = s_w[pp][lx0 + 1] * wyz;
@@ -373,8 +404,13 @@ __global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restric
       if (xx >= g.m[0]) continue;
       const size_t off = ((size_t)xx * g.n[1] + y) * g.n[2] + z;
 #pragma unroll
-      for (int c = 0; c < CMAX; ++c)
-        if (c < C) grid[c * G + off] = xi ? acc1[c] : acc0[c];
+      for (int c = 0; c < CMAX; ++c) {
+        if (c < C) {
+          const T v = xi ? acc1[c] : acc0[c];
+          if (nslab == 1) grid[c * G + off] = v;
+          else atomicAdd(&grid[c * G + off], v);
+        }
+      }
     }
   }
 }
@@ -563,17 +599,95 @@ __device__ inline T dev_erfc(T x);
 template <> __device__ inline float dev_erfc<float>(float x) { return erfcf(x); }
 template <> __device__ inline double dev_erfc<double>(double x) { return erfc(x); }
 
-template <typename T, int RMAX>
+// One pair (target, source image): accumulate G^R(r) . f into acc, or the self term when
+// the separation is exactly zero (the omitted n = m, p = 0 term of the star sum).
+template <typename T, int KERNEL, int RMAX>
+__device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, T c2pi, const T* __restrict__ f,
+                                          int n_rhs, T* acc) {
+  if (rr2 == T(0)) {
+    if (KERNEL == SE_STOKESLET) {
+      const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi), Eq. (3p-stokeslet-self-term)
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < n_rhs)
+          for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[3 * r + q];
+    }
+    return;
+  }
+  const T inv = rsqrt(rr2);
+  const T rn = rr2 * inv;
+  const T inv2 = inv * inv;
+  const T e = exp(-xi2 * rr2);
+  const T ec = dev_erfc(xi * rn) * inv;
+  if (KERNEL == SE_STOKESLET) {
+    // Eq. (stokeslet-real): (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e/sqrt pi
+    const T c1 = ec + c2pi * e;
+    const T c0 = c1 - T(2) * c2pi * e;
+    const T c1i = c1 * inv2;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T* fr = f + 3 * r;
+        const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1i;
+        acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
+        acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
+        acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
+      }
+    }
+  } else if (KERNEL == SE_ROTLET) {
+    // Eq. (rotlet-real): eps_jlm r_m / r^2 (erfc/r + 2 xi e/sqrt pi) f_l = (f x r)_j c
+    const T c1 = (ec + c2pi * e) * inv2;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T* fr = f + 3 * r;
+        acc[3 * r + 0] += c1 * (fr[1] * r2 - fr[2] * r1);
+        acc[3 * r + 1] += c1 * (fr[2] * r0 - fr[0] * r2);
+        acc[3 * r + 2] += c1 * (fr[0] * r1 - fr[1] * r0);
+      }
+    }
+  } else {
+    // Eq. (stresslet-real): -2 r_j r_l r_m / r^4 (3 erfc/r + (3 + 2 xi^2 r^2) 2 xi e/sqrt pi)
+    //   + (delta_jl r_m + delta_mj r_l + delta_lm r_j) 4 xi^3 e / sqrt pi
+    const T A = T(3) * ec + (T(3) + T(2) * xi2 * rr2) * c2pi * e;
+    const T B = T(2) * xi2 * c2pi * e;
+    const T Ai = -T(2) * A * inv2 * inv2;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T* q = f + 6 * r;
+        const T* nu = q + 3;
+        const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
+        const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
+        const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
+        const T c3 = Ai * rq * rnu + qn * B;
+        const T bq = B * rnu, bn = B * rq;
+        acc[3 * r + 0] += c3 * r0 + bq * q[0] + bn * nu[0];
+        acc[3 * r + 1] += c3 * r1 + bq * q[1] + bn * nu[1];
+        acc[3 * r + 2] += c3 * r2 + bq * q[2] + bn * nu[2];
+      }
+    }
+  }
+}
+
+// Real-space sum: a group of GL lanes per target. The group walks the (2S+1)^2 neighbour
+// columns; the cells of one column along direction 2 are contiguous in the sorted order, so
+// each column is one source range per periodic image, split over the lanes; the lanes'
+// partial sums are combined by shuffles.
+template <typename T, int KERNEL, int RMAX, int GL>
 __global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= a.ntgt) return;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = gtid / GL;
+  const int lane = gtid % GL;
+  const bool active = s < a.ntgt;
   typedef typename Vec4<T>::type V4;
-  const V4 xt = a.xt[s];
+  const int sc = active ? s : 0;
+  const V4 xt = a.xt[sc];
   V4 xtl;
   xtl.x = xtl.y = xtl.z = xtl.w = T(0);
-  if (sizeof(T) == 4) xtl = a.xtl[s];
-  const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
-  const int nc = a.kernel == SE_STRESSLET ? 6 : 3;
+  if (sizeof(T) == 4) xtl = a.xtl[sc];
+  const int cx = a.tcell[3 * sc], cy = a.tcell[3 * sc + 1], cz = a.tcell[3 * sc + 2];
+  const int nc = KERNEL == SE_STRESSLET ? 6 : 3;
   const int C = nc * a.n_rhs;
   T acc[3 * RMAX];
 #pragma unroll
@@ -582,114 +696,77 @@ __global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
   const T xi2 = xi * xi;
   const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
   const CellGeom& g = a.cg;
-  for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
-    int ux = cx + dx;
-    double shx_d = 0;
-    if (g.periodic[0]) {
-      int im = fdiv(ux, g.nc[0]);
-      ux -= im * g.nc[0];
-      shx_d = im * g.L[0];
-    } else if (ux < 0 || ux >= g.nc[0]) continue;
-    const T shx = (T)shx_d;
-    for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
-      int uy = cy + dy;
-      double shy_d = 0;
-      if (g.periodic[1]) {
-        int im = fdiv(uy, g.nc[1]);
-        uy -= im * g.nc[1];
-        shy_d = im * g.L[1];
-      } else if (uy < 0 || uy >= g.nc[1]) continue;
-      const T shy = (T)shy_d;
-      for (int dz = -g.range[2]; dz <= g.range[2]; ++dz) {
-        int uz = cz + dz;
-        double shz_d = 0;
-        if (g.periodic[2]) {
-          int im = fdiv(uz, g.nc[2]);
-          uz -= im * g.nc[2];
-          shz_d = im * g.L[2];
-        } else if (uz < 0 || uz >= g.nc[2]) continue;
-        const T shz = (T)shz_d;
-        const int cell = (ux * g.nc[1] + uy) * g.nc[2] + uz;
-        const int beg = a.cstart[cell], end = a.cstart[cell + 1];
-        // image shift in hi + lo parts (exact in FP64; FP32 keeps the rounding of p L)
-        const T shxl = (T)(shx_d - (double)shx), shyl = (T)(shy_d - (double)shy), shzl = (T)(shz_d - (double)shz);
-        for (int j = beg; j < end; ++j) {
-          const V4 xs = a.xs[j];
-          T r0, r1, r2;
-          if (sizeof(T) == 4) {
-            // r = x_target - (x_source + p): every coordinate as hi + lo floats; the sum
-            // x_source_hi + shift is split exactly (Fast2Sum, |shift| >= |x_source|), so the
-            // separation is accurate to the rounding of the final difference
-            const V4 xl = a.xsl[j];
-            const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
-            const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
-            r0 = (xt.x - ax) + ((xtl.x - xl.x) - (shxl + ex));
-            r1 = (xt.y - ay) + ((xtl.y - xl.y) - (shyl + ey));
-            r2 = (xt.z - az) + ((xtl.z - xl.z) - (shzl + ez));
-          } else {
-            r0 = xt.x - (xs.x + shx);
-            r1 = xt.y - (xs.y + shy);
-            r2 = xt.z - (xs.z + shz);
+  if (active) {
+    for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
+      int ux = cx + dx;
+      double shx_d = 0;
+      if (g.periodic[0]) {
+        int im = fdiv(ux, g.nc[0]);
+        ux -= im * g.nc[0];
+        shx_d = im * g.L[0];
+      } else if (ux < 0 || ux >= g.nc[0]) continue;
+      const T shx = (T)shx_d, shxl = (T)(shx_d - (double)shx);
+      for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
+        int uy = cy + dy;
+        double shy_d = 0;
+        if (g.periodic[1]) {
+          int im = fdiv(uy, g.nc[1]);
+          uy -= im * g.nc[1];
+          shy_d = im * g.L[1];
+        } else if (uy < 0 || uy >= g.nc[1]) continue;
+        const T shy = (T)shy_d, shyl = (T)(shy_d - (double)shy);
+        const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
+        int zlo = cz - g.range[2], zend = cz + g.range[2];
+        if (!g.periodic[2]) {
+          zlo = max(zlo, 0);
+          zend = min(zend, g.nc[2] - 1);
+        }
+        while (zlo <= zend) {
+          // one image of direction 2: cells w0..w1 of this column, contiguous
+          const int im = g.periodic[2] ? fdiv(zlo, g.nc[2]) : 0;
+          const int seg_end = g.periodic[2] ? min(zend, (im + 1) * g.nc[2] - 1) : zend;
+          const int w0 = zlo - im * g.nc[2], w1 = seg_end - im * g.nc[2];
+          const double shz_d = im * g.L[2];
+          const T shz = (T)shz_d, shzl = (T)(shz_d - (double)shz);
+          const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
+          for (int j = beg + lane; j < end; j += GL) {
+            const V4 xs = a.xs[j];
+            T r0, r1, r2;
+            if (sizeof(T) == 4) {
+              // hi + lo separation; x_source_hi + shift split exactly (Fast2Sum)
+              const V4 xl = a.xsl[j];
+              const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
+              const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
+              r0 = (xt.x - ax) + ((xtl.x - xl.x) - (shxl + ex));
+              r1 = (xt.y - ay) + ((xtl.y - xl.y) - (shyl + ey));
+              r2 = (xt.z - az) + ((xtl.z - xl.z) - (shzl + ez));
+            } else {
+              r0 = xt.x - (xs.x + shx);
+              r1 = xt.y - (xs.y + shy);
+              r2 = xt.z - (xs.z + shz);
+            }
+            const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
+            if (rr2 < a.rc2) real_pair<T, KERNEL, RMAX>(r0, r1, r2, rr2, xi, xi2, c2pi, a.fs + (size_t)j * C,
+                                                       a.n_rhs, acc);
           }
-          const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
-          if (rr2 >= a.rc2) continue;
-          const T* f = a.fs + (size_t)j * C;
-          if (rr2 == T(0)) {
-            if (a.kernel == SE_STOKESLET) {
-              const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi)
-              for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-                for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[3 * r + q];
-            }
-            continue;
-          }
-          const T rn = sqrt(rr2);
-          const T inv2 = T(1) / rr2;
-          const T e = exp(-xi2 * rr2);
-          const T ec = dev_erfc(xi * rn) / rn;
-          if (a.kernel == SE_STOKESLET) {
-            // (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e / sqrt pi
-            const T c1 = ec + c2pi * e;
-            const T c0 = c1 - T(2) * c2pi * e;
-            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
-              const T* fr = f + 3 * r;
-              const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1 * inv2;
-              acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
-              acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
-              acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
-            }
-          } else if (a.kernel == SE_ROTLET) {
-            // eps_jlm r_m / r^2 (erfc/r + 2 xi e / sqrt pi) f_l = (f x r)_j c
-            const T c1 = (ec + c2pi * e) * inv2;
-            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
-              const T* fr = f + 3 * r;
-              acc[3 * r + 0] += c1 * (fr[1] * r2 - fr[2] * r1);
-              acc[3 * r + 1] += c1 * (fr[2] * r0 - fr[0] * r2);
-              acc[3 * r + 2] += c1 * (fr[0] * r1 - fr[1] * r0);
-            }
-          } else {
-            // -2 r_j r_l r_m / r^4 (3 erfc/r + (3 + 2 xi^2 r^2) 2 xi e/sqrt pi)
-            //   + (delta_jl r_m + delta_mj r_l + delta_lm r_j) 4 xi^3 e / sqrt pi
-            const T A = T(3) * ec + (T(3) + T(2) * xi2 * rr2) * c2pi * e;
-            const T B = T(2) * xi2 * c2pi * e;
-            for (int r = 0; r < a.n_rhs && r < RMAX; ++r) {
-              const T* q = f + 6 * r;
-              const T* nu = q + 3;
-              const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
-              const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
-              const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
-              const T c3 = -T(2) * rq * rnu * inv2 * inv2 * A + qn * B;
-              acc[3 * r + 0] += c3 * r0 + B * (q[0] * rnu + nu[0] * rq);
-              acc[3 * r + 1] += c3 * r1 + B * (q[1] * rnu + nu[1] * rq);
-              acc[3 * r + 2] += c3 * r2 + B * (q[2] * rnu + nu[2] * rq);
-            }
-          }
+          zlo = seg_end + 1;
         }
       }
     }
   }
-  const int i = a.tperm[s];
-  for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-    for (int q = 0; q < 3; ++q) a.u[((size_t)r * a.ntgt + i) * 3 + q] += acc[3 * r + q];
+  // combine the GL lanes of the group
+#pragma unroll
+  for (int k = 0; k < 3 * RMAX; ++k) {
+    T v = acc[k];
+#pragma unroll
+    for (int off = GL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GL);
+    acc[k] = v;
+  }
+  if (active && lane == 0) {
+    const int i = a.tperm[s];
+    for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
+      for (int q = 0; q < 3; ++q) a.u[((size_t)r * a.ntgt + i) * 3 + q] += acc[3 * r + q];
+  }
 }
 
 // sorted positions (wrapped, plan precision, padded to 4) and cell coordinates
@@ -1029,9 +1106,16 @@ se_status fft_exec<double>(cufftHandle h, bool forward, double* real, double* cp
 template <typename T, int CMAX>
 void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C,
                    T* grid) {
-  dim3 grd(p->geom.ntile[0], p->geom.ntile[1], p->geom.ntile[2]);
+  // split the source-tile slabs along direction 0 over several CTAs when there are too few
+  // tiles to fill the GPU; the partial tiles are then added atomically into a zeroed grid
+  const GridGeom& g = p->geom;
+  const long long tiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
+  const int nslab = tiles >= 4 * 152 ? 1 : 3;
+  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+  if (nslab > 1) cudaMemsetAsync(grid, 0, sizeof(T) * C * G, p->stream);
+  dim3 grd(g.ntile[0] * nslab, g.ntile[1], g.ntile[2]);
   ++p->launches;
-  k_spread<T, CMAX><<<grd, 256, 0, p->stream>>>(p->geom, tile_start, base, w, sf, C, grid);
+  k_spread<T, CMAX><<<grd, 256, 0, p->stream>>>(g, tile_start, base, w, sf, C, nslab, grid);
 }
 
 template <typename T, int NC>
@@ -1041,10 +1125,17 @@ void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, c
   k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u);
 }
 
+template <typename T, int K, int R>
+void real_launch_k(se_plan_t* p, const RealArgs<T>& a) {
+  constexpr int GL = 8;
+  ++p->launches;
+  k_real<T, K, R, GL><<<grid1d((long long)a.ntgt * GL, 128), 128, 0, p->stream>>>(a);
+}
 template <typename T, int R>
 void real_launch(se_plan_t* p, const RealArgs<T>& a) {
-  ++p->launches;
-  k_real<T, R><<<grid1d(a.ntgt, 128), 128, 0, p->stream>>>(a);
+  if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, a);
+  else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, a);
+  else real_launch_k<T, SE_STRESSLET, R>(p, a);
 }
 
 template <typename T>
