@@ -55,7 +55,8 @@ typedef enum {
   SE_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed                  */
   SE_ERR_CUFFT = -5,       /* a cuFFT call failed                                          */
   SE_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up                           */
-  SE_ERR_UNSUPPORTED = -7  /* a valid request this build does not implement               */
+  SE_ERR_UNSUPPORTED = -7, /* a valid request this build does not implement               */
+  SE_ERR_CAPACITY = -8     /* the request exceeds a fixed capacity (see se_real_noalloc)    */
 } se_status;
 
 enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4 };
@@ -173,6 +174,32 @@ se_status se_sync(se_plan_h plan);
 
 /* Release the plan and everything it owns. NULL is accepted. */
 void se_destroy(se_plan_h plan);
+
+/*
+ * Real-space sum without any device allocation (this paper has no counterpart: it is an
+ * interface for callers that cannot allocate device memory while they run -- code inside a
+ * framework that owns all device memory through its own pre-allocated pool, or a time-step
+ * loop that must never stall or fail on an allocation).
+ * Computes the same values as se_eval_parts(plan, kernel, SE_PART_REAL, ...) in the star
+ * form (targets = sources) for one right-hand side: the real-space part of
+ * Eq. (real-space-potential-Dp) with the cut-off rc, plus the self term for the stokeslet.
+ *   periodicity, box, xi, rc  as in se_plan_create; kernel: one of SE_STOKESLET, SE_ROTLET,
+ *                             SE_STRESSLET; prec: SE_FP64 (double strengths and u) or SE_FP32.
+ *   n_src, src                device double [n_src][3]; strengths device [n_src][c].
+ *   u                         device [n_src][3], overwritten.
+ *   stream                    cudaStream_t (NULL = legacy default stream); asynchronous.
+ * Scratch: a fixed 16 MiB array inside the library (held by every GPU that loads it until
+ * the process exits); limits n_src <= 65536 and at most 32 cells per direction; larger
+ * requests return SE_ERR_CAPACITY before any work. No cudaMalloc, cudaFree or allocating
+ * library call is made. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) once for that device: make that first call before any stream
+ * capture. Every call shares the one array and keeps its last contents (the counters are
+ * cleared at the start of each call); calls that overlap on the GPU (different streams, or
+ * host threads) race on it and must be serialised by the caller.
+ */
+se_status se_real_noalloc(int periodicity, const double box[3], double xi, double rc, int kernel,
+                          int prec, long long n_src, const double* src, const void* strengths,
+                          void* u, void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* se_status_str(se_status s);

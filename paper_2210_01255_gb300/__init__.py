@@ -21,7 +21,8 @@ WINDOWS = {"gaussian": WIN_GAUSSIAN, "kb": WIN_KB, "pkb": WIN_PKB}
 
 SE_OK = 0
 _STATUS = {0: "ok", -1: "invalid argument", -2: "coordinate out of range", -3: "out of memory",
-           -4: "CUDA error", -5: "cuFFT error", -6: "device wait timed out", -7: "unsupported request"}
+           -4: "CUDA error", -5: "cuFFT error", -6: "device wait timed out", -7: "unsupported request",
+           -8: "request exceeds a fixed capacity"}
 
 
 class SeError(RuntimeError):
@@ -67,6 +68,8 @@ SIGNATURES = {
     "se_sync": (ctypes.c_int, [_P]),
     "se_destroy": (None, [_P]),
     "se_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "se_real_noalloc": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
 }
 
 _lib = None
@@ -171,6 +174,15 @@ def se_sync(plan):
 
 def se_destroy(plan):
     lib().se_destroy(plan)
+
+
+def se_real_noalloc(periodicity, box, xi, rc, kernel_mask, prec, src, strengths, u, stream=None):
+    """Allocation-free real-space sum (star form, one RHS) into u; see include/se.h."""
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    check(lib().se_real_noalloc(int(periodicity), b, float(xi), float(rc), int(kernel_mask), int(prec),
+                                src.shape[0], _ptr(src), _ptr(strengths), _ptr(u),
+                                None if stream is None else ctypes.c_void_p(stream.cuda_stream)),
+          "se_real_noalloc")
 
 
 def se_status_str(code):

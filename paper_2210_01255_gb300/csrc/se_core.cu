@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "se_internal.h"
@@ -1394,4 +1395,146 @@ extern "C" se_status se_eval_host(se_plan_h p, int kernel, long long n_src, cons
   SE_TRY(se_eval(p, kernel, n_src, (const double*)dx, df, n_rhs, n_tgt, (const double*)dt, du));
   SE_CUDA(cudaMemcpyAsync(u, du, bu, cudaMemcpyDeviceToHost, p->stream));
   return se_sync(p);
+}
+
+// ====================================================== allocation-free real-space sum
+//
+// Some callers cannot allocate device memory while they run: code embedded in a framework
+// that owns every byte of device memory through its own pre-allocated pool (a deep-learning
+// runtime, a simulation package with a fixed memory budget), or a time-step loop that must
+// not stall or fail on an allocation. se_real_noalloc serves them: it computes the same
+// real-space sum as se_eval_parts(..., SE_PART_REAL, ...) in the star form, single right-
+// hand side, with all of its scratch (cell keys, counts and starts, sorted positions and
+// strengths) in the fixed array below. Every GPU that loads the library holds this array
+// (SE_NOALLOC_SCRATCH_BYTES) until the process exits.
+
+namespace {
+
+constexpr size_t SE_NOALLOC_SCRATCH_BYTES = 16u << 20;   // 16 MiB
+constexpr int SE_NOALLOC_MAX_POINTS = 65536;
+constexpr int SE_NOALLOC_MAX_CELLS = 32768;              // at most 32 cells per direction
+
+__device__ __align__(256) unsigned char se_noalloc_scratch[SE_NOALLOC_SCRATCH_BYTES];
+
+constexpr int SE_NOALLOC_MAX_DEVICES = 64;
+void* g_noalloc_ptr[SE_NOALLOC_MAX_DEVICES] = {};
+std::mutex g_noalloc_mutex;
+
+// Device address of the scratch array on the current device, looked up once per device.
+se_status noalloc_scratch(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SE_NOALLOC_MAX_DEVICES) return SE_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, se_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return SE_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_ptr[dev];
+  return SE_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+template <typename T>
+se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int kernel, int N,
+                            const double* src, const T* f, T* u, cudaStream_t st) {
+  typedef typename Vec4<T>::type V4;
+  const int nc = kernel == SE_STRESSLET ? 6 : 3;
+  CellGeom cg;
+  const int S = 2;
+  for (int d = 0; d < 3; ++d) {
+    int n = (int)std::floor(S * box[d] / rc);
+    n = std::max(1, std::min(n, 32));
+    cg.nc[d] = n;
+    double cs = box[d] / n;
+    cg.range[d] = (int)std::ceil(rc / cs - 1e-12);
+    cg.periodic[d] = d < D;
+    cg.L[d] = box[d];
+    cg.inv_cs[d] = 1.0 / cs;
+  }
+  const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
+  if (ncell > SE_NOALLOC_MAX_CELLS) return SE_ERR_CAPACITY;
+  // carve the scratch array
+  const size_t n = (size_t)std::max(N, 1);
+  size_t off[10], need = 0;
+  const size_t sizes[10] = {sizeof(int) * n,      sizeof(int) * n,     sizeof(int) * ncell,
+                            sizeof(int) * (ncell + 1), sizeof(int) * n, sizeof(V4) * n,
+                            sizeof(V4) * n,       sizeof(T) * nc * n,  sizeof(int) * 3 * n,
+                            sizeof(int)};
+  for (int i = 0; i < 10; ++i) {
+    off[i] = need;
+    need += align256(sizes[i]);
+  }
+  if (need > SE_NOALLOC_SCRATCH_BYTES) return SE_ERR_CAPACITY;
+  void* base = nullptr;
+  SE_TRY(noalloc_scratch(&base));
+  unsigned char* sb = (unsigned char*)base;
+  int* key = (int*)(sb + off[0]);
+  int* rank = (int*)(sb + off[1]);
+  int* count = (int*)(sb + off[2]);
+  int* start = (int*)(sb + off[3]);
+  int* perm = (int*)(sb + off[4]);
+  V4* xs = (V4*)(sb + off[5]);
+  V4* xsl = (V4*)(sb + off[6]);
+  T* fs = (T*)(sb + off[7]);
+  int* tcell = (int*)(sb + off[8]);
+  int* status = (int*)(sb + off[9]);
+  // the array keeps the previous call's contents: clear the counters and the output
+  SE_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * ncell, st));
+  SE_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
+  SE_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * 3 * (size_t)N, st));
+  if (N == 0) return SE_OK;
+  k_cell_keys<<<grid1d(N, 256), 256, 0, st>>>(cg, src, N, key, rank, count, status);
+  k_scan<<<1, 1024, 0, st>>>(count, start, ncell);
+  k_scatter_perm<<<grid1d(N, 256), 256, 0, st>>>(key, rank, start, N, perm);
+  k_sort_positions<T><<<grid1d(N, 256), 256, 0, st>>>(cg, src, perm, N, xs, xsl, tcell, status);
+  k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, f, perm, N, 1, fs);
+  RealArgs<T> ra;
+  ra.cg = cg;
+  ra.xi = (T)xi;
+  ra.rc2 = (T)(rc * rc);
+  ra.kernel = kernel;
+  ra.n_rhs = 1;
+  ra.nsrc = N;
+  ra.ntgt = N;
+  ra.xs = xs;
+  ra.xsl = xsl;
+  ra.fs = fs;
+  ra.cstart = start;
+  ra.xt = xs;
+  ra.xtl = xsl;
+  ra.tperm = perm;
+  ra.tcell = tcell;
+  ra.u = u;
+  constexpr int GL = 8;
+  const int grid = grid1d((long long)N * GL, 128);
+  if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1, GL><<<grid, 128, 0, st>>>(ra);
+  else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1, GL><<<grid, 128, 0, st>>>(ra);
+  else k_real<T, SE_STRESSLET, 1, GL><<<grid, 128, 0, st>>>(ra);
+  SE_CUDA(cudaGetLastError());
+  return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status se_real_noalloc(int periodicity, const double box[3], double xi, double rc,
+                                     int kernel, int prec, long long n_src, const double* src,
+                                     const void* strengths, void* u, void* stream) {
+  if (periodicity < 0 || periodicity > 3 || !box || !(xi > 0) || !(rc > 0) || !u) return SE_ERR_ARG;
+  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET) return SE_ERR_ARG;
+  if (prec != SE_FP64 && prec != SE_FP32) return SE_ERR_ARG;
+  if (n_src < 0 || (n_src > 0 && (!src || !strengths))) return SE_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(box[d] > 0) || !std::isfinite(box[d])) return SE_ERR_ARG;
+  if (n_src > SE_NOALLOC_MAX_POINTS) return SE_ERR_CAPACITY;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == SE_FP32)
+    return real_noalloc_impl<float>(periodicity, box, xi, rc, kernel, (int)n_src, src, (const float*)strengths,
+                                     (float*)u, st);
+  return real_noalloc_impl<double>(periodicity, box, xi, rc, kernel, (int)n_src, src, (const double*)strengths,
+                                   (double*)u, st);
 }

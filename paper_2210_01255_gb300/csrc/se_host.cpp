@@ -307,6 +307,7 @@ extern "C" const char* se_status_str(se_status s) {
     case SE_ERR_CUFFT: return "cuFFT error";
     case SE_ERR_TIMEOUT: return "device wait timed out";
     case SE_ERR_UNSUPPORTED: return "unsupported request";
+    case SE_ERR_CAPACITY: return "request exceeds a fixed capacity";
   }
   return "unknown status";
 }
