@@ -201,6 +201,26 @@ se_status se_real_noalloc(int periodicity, const double box[3], double xi, doubl
                           int prec, long long n_src, const double* src, const void* strengths,
                           void* u, void* stream);
 
+/*
+ * A fixed batch of independent evaluations (for example many singly periodic systems of
+ * different sizes, each with its own plan and right-hand sides) replayed with one launch.
+ * se_batch_create evaluates every configuration once (star form: targets = sources), so
+ * that every buffer and cuFFT plan exists, then records all the evaluations into a CUDA
+ * graph on the plans' shared stream. All plans must use the same stream, which must not be
+ * the legacy default stream (NULL), and must not have timing enabled. The arrays passed here
+ * (src, strengths, u of every configuration) are the ones every replay reads and writes:
+ * refill the inputs in place between launches. Arguments per configuration i:
+ * kernel_mask[i], n_src[i], src[i], strengths[i], n_rhs[i], u[i] as in se_eval.
+ * se_batch_launch replays the graph asynchronously on that stream (results are complete
+ * when the stream is synchronised); se_batch_destroy releases the graph (not the plans).
+ */
+typedef struct se_batch_t* se_batch_h;
+se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h* plans, const int* kernel_mask,
+                          const long long* n_src, const double* const* src,
+                          const void* const* strengths, const int* n_rhs, void* const* u);
+se_status se_batch_launch(se_batch_h batch);
+void se_batch_destroy(se_batch_h batch);
+
 /* Human-readable name of a status code (static storage). */
 const char* se_status_str(se_status s);
 

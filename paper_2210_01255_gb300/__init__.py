@@ -68,6 +68,11 @@ SIGNATURES = {
     "se_sync": (ctypes.c_int, [_P]),
     "se_destroy": (None, [_P]),
     "se_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "se_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(_P), _I3,
+                                       ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                       _I3, ctypes.POINTER(_P)]),
+    "se_batch_launch": (ctypes.c_int, [_P]),
+    "se_batch_destroy": (None, [_P]),
     "se_real_noalloc": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
 }
@@ -183,6 +188,30 @@ def se_real_noalloc(periodicity, box, xi, rc, kernel_mask, prec, src, strengths,
                                 src.shape[0], _ptr(src), _ptr(strengths), _ptr(u),
                                 None if stream is None else ctypes.c_void_p(stream.cuda_stream)),
           "se_real_noalloc")
+
+
+def se_batch_create(plans, kernel_masks, srcs, strengths, n_rhs, us):
+    """Record the evaluations of several configurations (star form) into one CUDA graph.
+    plans: handles sharing one non-default stream; srcs / strengths / us: torch device tensors."""
+    n = len(plans)
+    h = ctypes.c_void_p()
+    arr = lambda t, vals: (t * n)(*vals)
+    check(lib().se_batch_create(ctypes.byref(h), n, arr(ctypes.c_void_p, [p.value for p in plans]),
+                                arr(ctypes.c_int, [int(k) for k in kernel_masks]),
+                                arr(ctypes.c_longlong, [int(s.shape[0]) for s in srcs]),
+                                arr(ctypes.c_void_p, [s.data_ptr() for s in srcs]),
+                                arr(ctypes.c_void_p, [f.data_ptr() for f in strengths]),
+                                arr(ctypes.c_int, [int(r) for r in n_rhs]),
+                                arr(ctypes.c_void_p, [u.data_ptr() for u in us])), "se_batch_create")
+    return h
+
+
+def se_batch_launch(batch):
+    check(lib().se_batch_launch(batch), "se_batch_launch")
+
+
+def se_batch_destroy(batch):
+    lib().se_batch_destroy(batch)
 
 
 def se_status_str(code):

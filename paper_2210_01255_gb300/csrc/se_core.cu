@@ -11,7 +11,7 @@
 #include <mutex>
 #include <new>
 
-#include "se_internal.h"
+#include "se_device.cuh"
 
 namespace se {
 
@@ -35,16 +35,6 @@ se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out) {
   return SE_OK;
 }
 
-template <typename T> struct Vec4;
-template <> struct Vec4<float> { typedef float4 type; };
-template <> struct Vec4<double> { typedef double4 type; };
-
-__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-// floor division for possibly negative a, b > 0
-__host__ __device__ inline int fdiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
-
-static int grid1d(long long n, int block) { return (int)std::max<long long>(1, (n + block - 1) / block); }
 
 // ============================================================ point binning (counting sort)
 
@@ -318,79 +308,69 @@ __device__ inline int tile_list(const GridGeom& g, int d, int o, int* bins, int*
 }
 
 // Gridding, Eq. (SE-gridding-disc). Output-driven: the CTA (tile t, slab j) owns the TS^3
-// tile t and the j-th of the source-tile slabs along direction 0; each thread accumulates
-// two grid points along direction 0 over all points of the slab's tiles in registers, and
-// the partial tile is added to the (zeroed) grid. With nslab = 1 the tile is stored.
+// tile t and the j-th share of the source tiles that reach it (the source tiles are dealt
+// out round-robin over nslab CTAs). Each of the 64 threads owns one (y, z) column of the
+// tile and accumulates its TS = 8 grid points along direction 0 and all components in
+// registers: per point one product of the (y, z) window values, a test, and 8 C FMAs with
+// the direction-0 window values read as vectors from shared memory. The partial tile is
+// stored (nslab = 1) or added atomically into the zeroed grid.
 template <typename T, int CMAX>
-__global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restrict__ tile_start,
-                                                const int* __restrict__ base, const T* __restrict__ wts,
-                                                const T* __restrict__ sf, int C, int nslab, T* __restrict__ grid) {
-  __shared__ T s_w[SP_CHUNK][3 * TS];
-  __shared__ T s_f[SP_CHUNK][CMAX];
+__global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict__ tile_start,
+                                               const int* __restrict__ base, const T* __restrict__ wts,
+                                               const T* __restrict__ sf, int Ctot, int c0, int C, int nslab,
+                                               T* __restrict__ grid) {
+  // components c0 .. c0 + C - 1 of the Ctot spread components
+  constexpr int CH = 64;  // points staged per chunk
+  __shared__ __align__(16) T s_w[CH][3 * TS];
+  __shared__ T s_f[CH][CMAX];
+  __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
   const int P = g.P;
   const int tid = threadIdx.x;
-  const int lz = tid & 7, ly = (tid >> 3) & 7, lx0 = (tid >> 6) * 2;
+  const int lz = tid & 7, ly = tid >> 3;
   const int slab = blockIdx.x % nslab;
   const int t0 = blockIdx.x / nslab, t1 = blockIdx.y, t2 = blockIdx.z;
   const int o[3] = {t0 * TS, t1 * TS, t2 * TS};
-  T acc0[CMAX], acc1[CMAX];
+  T acc[TS][CMAX];
 #pragma unroll
-  for (int c = 0; c < CMAX; ++c) acc0[c] = acc1[c] = T(0);
-
-  __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
+  for (int xx = 0; xx < TS; ++xx)
+#pragma unroll
+    for (int c = 0; c < CMAX; ++c) acc[xx][c] = T(0);
   if (tid < 3) s_nb[tid] = tile_list(g, tid, o[tid], s_bin[tid], s_sh[tid]);
   __syncthreads();
   const int nbx = s_nb[0], nby = s_nb[1], nbz = s_nb[2];
-  for (int ix = slab; ix < nbx; ix += nslab) {
-    for (int iy = 0; iy < nby; ++iy) {
-      for (int iz = 0; iz < nbz; ++iz) {
-        const int bin = (s_bin[0][ix] * g.ntile[1] + s_bin[1][iy]) * g.ntile[2] + s_bin[2][iz];
-        const int beg = tile_start[bin], end = tile_start[bin + 1];
-        const int rel0 = s_sh[0][ix] - o[0], rel1 = s_sh[1][iy] - o[1], rel2 = s_sh[2][iz] - o[2];
-        for (int p0 = beg; p0 < end; p0 += SP_CHUNK) {
-          const int cnt = min(SP_CHUNK, end - p0);
-          __syncthreads();
-          for (int idx = tid; idx < cnt * 3 * TS; idx += blockDim.x) {
-            const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
-            const int d = r / TS, l = r - d * TS;
-            const int rel = d == 0 ? rel0 : (d == 1 ? rel1 : rel2);
-            const int q = l - (base[3 * (p0 + pp) + d] + rel);
-            s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)(p0 + pp) * 3 + d) * P + q] : T(0);
-          }
-          for (int idx = tid; idx < cnt * C; idx += blockDim.x) {
-            const int pp = idx / C, c = idx - pp * C;
-            s_f[pp][c] = sf[(size_t)(p0 + pp) * C + c];
-          }
-          __syncthreads();
-          int pp = 0;
-          for (; pp + 1 < cnt; pp += 2) {
-            const T wyz0 = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
-            const T wyz1 = s_w[pp + 1][TS + ly] * s_w[pp + 1][2 * TS + lz];
-            if (wyz0 != T(0) || wyz1 != T(0)) {
-              const T wa0 = s_w[pp][lx0] * wyz0, wb0 = s_w[pp][lx0 + 1] * wyz0;
-              const T wa1 = s_w[pp + 1][lx0] * wyz1, wb1 = s_w[pp + 1][lx0 + 1] * wyz1;
+  const int nbins = nbx * nby * nbz;
+  for (int ib = slab; ib < nbins; ib += nslab) {
+    const int ix = ib / (nby * nbz), iy = (ib / nbz) % nby, iz = ib % nbz;
+    const int bin = (s_bin[0][ix] * g.ntile[1] + s_bin[1][iy]) * g.ntile[2] + s_bin[2][iz];
+    const int beg = tile_start[bin], end = tile_start[bin + 1];
+    const int rel0 = s_sh[0][ix] - o[0], rel1 = s_sh[1][iy] - o[1], rel2 = s_sh[2][iz] - o[2];
+    for (int p0 = beg; p0 < end; p0 += CH) {
+      const int cnt = min(CH, end - p0);
+      __syncthreads();
+      for (int idx = tid; idx < cnt * 3 * TS; idx += 64) {
+        const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
+        const int d = r / TS, l = r - d * TS;
+        const int rel = d == 0 ? rel0 : (d == 1 ? rel1 : rel2);
+        const int q = l - (base[3 * (p0 + pp) + d] + rel);
+        s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)(p0 + pp) * 3 + d) * P + q] : T(0);
+      }
+      for (int idx = tid; idx < cnt * C; idx += 64) {
+        const int pp = idx / C, c = idx - pp * C;
+        s_f[pp][c] = sf[(size_t)(p0 + pp) * Ctot + c0 + c];
+      }
+      __syncthreads();
+      for (int pp = 0; pp < cnt; ++pp) {
+        const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
+        if (wyz != T(0)) {
+          T wx[TS];
 #pragma unroll
-              for (int c = 0; c < CMAX; ++c) {
-                if (c < C) {
-                  const T f0 = s_f[pp][c], f1 = s_f[pp + 1][c];
-                  acc0[c] += wa0 * f0 + wa1 * f1;
-                  acc1[c] += wb0 * f0 + wb1 * f1;
-                }
-              }
-            }
-          }
-          if (pp < cnt) {
-            const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
-            if (wyz != T(0)) {
-              const T wa = s_w[pp][lx0] * wyz, wb = s_w[pp][lx0 + 1] * wyz;
+          for (int xx = 0; xx < TS; ++xx) wx[xx] = s_w[pp][xx] * wyz;
 #pragma unroll
-              for (int c = 0; c < CMAX; ++c) {
-                if (c < C) {
-                  const T fv = s_f[pp][c];
-                  acc0[c] += wa * fv;
-                  acc1[c] += wb * fv;
-                }
-              }
+          for (int c = 0; c < CMAX; ++c) {
+            if (c < C) {
+              const T fv = s_f[pp][c];
+#pragma unroll
+              for (int xx = 0; xx < TS; ++xx) acc[xx][c] += wx[xx] * fv;
             }
           }
         }
@@ -400,16 +380,16 @@ __global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restric
   const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int y = o[1] + ly, z = o[2] + lz;
   if (y < g.m[1] && z < g.m[2]) {
-    for (int xi = 0; xi < 2; ++xi) {
-      const int xx = o[0] + lx0 + xi;
-      if (xx >= g.m[0]) continue;
-      const size_t off = ((size_t)xx * g.n[1] + y) * g.n[2] + z;
+#pragma unroll
+    for (int xx = 0; xx < TS; ++xx) {
+      const int x = o[0] + xx;
+      if (x >= g.m[0]) continue;
+      const size_t off = ((size_t)x * g.n[1] + y) * g.n[2] + z;
 #pragma unroll
       for (int c = 0; c < CMAX; ++c) {
         if (c < C) {
-          const T v = xi ? acc1[c] : acc0[c];
-          if (nslab == 1) grid[c * G + off] = v;
-          else atomicAdd(&grid[c * G + off], v);
+          if (nslab == 1) grid[(c0 + c) * G + off] = acc[xx][c];
+          else atomicAdd(&grid[(c0 + c) * G + off], acc[xx][c]);
         }
       }
     }
@@ -426,13 +406,17 @@ __global__ void __launch_bounds__(256) k_spread(GridGeom g, const int* __restric
 template <typename T>
 struct ScaleArgs {
   int n0, n1, n2, h2;
-  T kf0, kf1, kf2;  // 2 pi / L_d
+  T kf0, kf1, kf2;  // 2 pi / (n_d h)
   T inv4xi2;
-  const T* g0;
-  const T* g1;
-  const T* g2;
+  int zero_mode;    // 1: the k = 0 mode is dropped (D = 3, Eq. mod-kernel-3p)
+  ScaleTables<T> t;
 };
 
+// Scaling step, Eq. (SE-scaling-disc), in place on the half spectrum [C][n0][n1][n2/2+1]:
+// per mode the scalar A^(k) (times 1 + k^2/4xi^2 for the Hasimoto screening) and the
+// separable factors g0[i0] g1[i1] g2[i2] (exp(-k_d^2/4xi^2) / w^_0(k_d)^2 / n_d), then the
+// operator symbol K^(k). A^ is the untruncated kernel (D = 3) or the precomputed truncated
+// kernel A^_{R,tr} of Sec. 3.5 (D = 0, table t.atab). Nyquist planes are set to zero.
 template <typename T>
 __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__ spec) {
   const size_t H = (size_t)a.n0 * a.n1 * a.h2;
@@ -444,19 +428,20 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
   const int kb0 = i0 < a.n0 / 2 ? i0 : i0 - a.n0;
   const int kb1 = i1 < a.n1 / 2 ? i1 : i1 - a.n1;
   const int kb2 = i2;
-  const bool zero = (i0 == a.n0 / 2) || (i1 == a.n1 / 2) || (i2 == a.n2 / 2) ||
-                    (i0 == 0 && i1 == 0 && i2 == 0);
+  bool zero = (i0 == a.n0 / 2) || (i1 == a.n1 / 2) || (i2 == a.n2 / 2);
+  if (a.zero_mode && i0 == 0 && i1 == 0 && i2 == 0) zero = true;
   const T k0 = a.kf0 * kb0, k1 = a.kf1 * kb1, k2 = a.kf2 * kb2;
   const T kk = k0 * k0 + k1 * k1 + k2 * k2;
   T s = T(0);
   if (!zero) {
-    const T g = a.g0[i0] * a.g1[i1] * a.g2[i2];
-    if (kernel == SE_ROTLET)
-      s = T(4.0 * M_PI) / kk * g;  // H^ = 4 pi / k^2, Ewald screening
-    else
-      s = T(-8.0 * M_PI) / (kk * kk) * (T(1) + kk * a.inv4xi2) * g;  // B^ = -8 pi / k^4, Hasimoto
+    const T g = a.t.g0[i0] * a.t.g1[i1] * a.t.g2[i2];
+    if (a.t.atab) {
+      s = a.t.atab[idx] * g;
+      if (kernel != SE_ROTLET) s *= T(1) + kk * a.inv4xi2;
+    } else {
+      s = regular_scalar<T>(kernel, kk, a.inv4xi2) * g;
+    }
   }
-  // complex values as interleaved (re, im) pairs
   const int cin = kernel == SE_STRESSLET ? 6 : 3;
   for (int r = 0; r < n_rhs; ++r) {
     T re[6], im[6];
@@ -466,45 +451,7 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
       im[c] = spec[o + 1];
     }
     T ore[3], oim[3];
-    if (kernel == SE_STOKESLET) {
-      // (-delta k^2 + k k) F
-      const T kfr = k0 * re[0] + k1 * re[1] + k2 * re[2];
-      const T kfi = k0 * im[0] + k1 * im[1] + k2 * im[2];
-      const T kv[3] = {k0, k1, k2};
-      for (int j = 0; j < 3; ++j) {
-        ore[j] = s * (-kk * re[j] + kv[j] * kfr);
-        oim[j] = s * (-kk * im[j] + kv[j] * kfi);
-      }
-    } else if (kernel == SE_ROTLET) {
-      // -i eps_jlm k_m F_l = -i (F x k)_j
-      const T cr[3] = {re[1] * k2 - re[2] * k1, re[2] * k0 - re[0] * k2, re[0] * k1 - re[1] * k0};
-      const T ci[3] = {im[1] * k2 - im[2] * k1, im[2] * k0 - im[0] * k2, im[0] * k1 - im[1] * k0};
-      for (int j = 0; j < 3; ++j) {
-        ore[j] = s * ci[j];   // -i (a + ib) = b - ia
-        oim[j] = -s * cr[j];
-      }
-    } else {
-      // K^T_jlm F_lm = -i k^2 (2 (F k)_j + k_j tr F) + 2 i k_j (k F k), F symmetric
-      // components 0..5 = 11,22,33,12,13,23
-      const T kv[3] = {k0, k1, k2};
-      T Fkr[3], Fki[3];
-      Fkr[0] = re[0] * k0 + re[3] * k1 + re[4] * k2;
-      Fkr[1] = re[3] * k0 + re[1] * k1 + re[5] * k2;
-      Fkr[2] = re[4] * k0 + re[5] * k1 + re[2] * k2;
-      Fki[0] = im[0] * k0 + im[3] * k1 + im[4] * k2;
-      Fki[1] = im[3] * k0 + im[1] * k1 + im[5] * k2;
-      Fki[2] = im[4] * k0 + im[5] * k1 + im[2] * k2;
-      const T trr = re[0] + re[1] + re[2], tri = im[0] + im[1] + im[2];
-      const T kFkr = k0 * Fkr[0] + k1 * Fkr[1] + k2 * Fkr[2];
-      const T kFki = k0 * Fki[0] + k1 * Fki[1] + k2 * Fki[2];
-      for (int j = 0; j < 3; ++j) {
-        // value v = -k^2 (2 Fk_j + k_j tr) + 2 k_j kFk ; multiplied by i
-        const T vr = -kk * (T(2) * Fkr[j] + kv[j] * trr) + T(2) * kv[j] * kFkr;
-        const T vi = -kk * (T(2) * Fki[j] + kv[j] * tri) + T(2) * kv[j] * kFki;
-        ore[j] = -s * vi;
-        oim[j] = s * vr;
-      }
-    }
+    apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
     for (int j = 0; j < 3; ++j) {
       const size_t o = (((size_t)(3 * r + j)) * H + idx) * 2;
       spec[o] = ore[j];
@@ -512,6 +459,29 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
     }
   }
 }
+
+template <typename T>
+se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const ScaleTables<T>& t) {
+  const GridGeom& g = p->geom;
+  ScaleArgs<T> sa;
+  sa.n0 = g.n[0];
+  sa.n1 = g.n[1];
+  sa.n2 = g.n[2];
+  sa.h2 = g.n[2] / 2 + 1;
+  sa.kf0 = (T)(2.0 * M_PI / (g.n[0] * g.h));
+  sa.kf1 = (T)(2.0 * M_PI / (g.n[1] * g.h));
+  sa.kf2 = (T)(2.0 * M_PI / (g.n[2] * g.h));
+  sa.inv4xi2 = (T)(1.0 / (4.0 * p->xi * p->xi));
+  sa.zero_mode = p->D == 3;
+  sa.t = t;
+  const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
+  ++p->launches;
+  k_scale3p<T><<<grid1d((long long)H, 256), 256, 0, p->stream>>>(sa, kernel, n_rhs, spec);
+  SE_CUDA(cudaGetLastError());
+  return SE_OK;
+}
+template se_status launch_scale3p<float>(se_plan_t*, int, int, float*, const ScaleTables<float>&);
+template se_status launch_scale3p<double>(se_plan_t*, int, int, double*, const ScaleTables<double>&);
 
 // ====================================================== gathering, Eq. (SE-gathering-disc)
 //
@@ -671,23 +641,33 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   }
 }
 
-// Real-space sum: a group of GL lanes per target. The group walks the (2S+1)^2 neighbour
-// columns; the cells of one column along direction 2 are contiguous in the sorted order, so
-// each column is one source range per periodic image, split over the lanes; the lanes'
-// partial sums are combined by shuffles.
-template <typename T, int KERNEL, int RMAX, int GL>
-__global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = gtid / GL;
-  const int lane = gtid % GL;
-  const bool active = s < a.ntgt;
+// Real-space sum: one warp per target. The warp walks the neighbour columns of the target's
+// cell (each column, along direction 2, is one contiguous source range per periodic image,
+// trimmed to the part that can lie within rc of the target); 32 candidates are tested at a
+// time and the ones inside rc are compacted (ballot + popc) into a per-warp queue, which is
+// evaluated 32 pairs at a time with every lane busy. Lane partial sums are combined by
+// shuffles.
+constexpr int RS_WARPS = 4;  // warps per CTA
+
+template <typename T>
+struct PairQ {
+  T r0[64], r1[64], r2[64];
+  int j[64];
+};
+
+template <typename T, int KERNEL, int RMAX>
+__global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
+  __shared__ PairQ<T> q_s[RS_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * RS_WARPS + warp;
+  if (s >= a.ntgt) return;  // warp-uniform
+  PairQ<T>& q = q_s[warp];
   typedef typename Vec4<T>::type V4;
-  const int sc = active ? s : 0;
-  const V4 xt = a.xt[sc];
+  const V4 xt = a.xt[s];
   V4 xtl;
   xtl.x = xtl.y = xtl.z = xtl.w = T(0);
-  if (sizeof(T) == 4) xtl = a.xtl[sc];
-  const int cx = a.tcell[3 * sc], cy = a.tcell[3 * sc + 1], cz = a.tcell[3 * sc + 2];
+  if (sizeof(T) == 4) xtl = a.xtl[s];
+  const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
   const int nc = KERNEL == SE_STRESSLET ? 6 : 3;
   const int C = nc * a.n_rhs;
   T acc[3 * RMAX];
@@ -697,42 +677,70 @@ __global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
   const T xi2 = xi * xi;
   const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
   const CellGeom& g = a.cg;
-  if (active) {
-    for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
-      int ux = cx + dx;
-      double shx_d = 0;
-      if (g.periodic[0]) {
-        int im = fdiv(ux, g.nc[0]);
-        ux -= im * g.nc[0];
-        shx_d = im * g.L[0];
-      } else if (ux < 0 || ux >= g.nc[0]) continue;
-      const T shx = (T)shx_d, shxl = (T)(shx_d - (double)shx);
-      for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
-        int uy = cy + dy;
-        double shy_d = 0;
-        if (g.periodic[1]) {
-          int im = fdiv(uy, g.nc[1]);
-          uy -= im * g.nc[1];
-          shy_d = im * g.L[1];
-        } else if (uy < 0 || uy >= g.nc[1]) continue;
-        const T shy = (T)shy_d, shyl = (T)(shy_d - (double)shy);
-        const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
-        int zlo = cz - g.range[2], zend = cz + g.range[2];
-        if (!g.periodic[2]) {
-          zlo = max(zlo, 0);
-          zend = min(zend, g.nc[2] - 1);
-        }
-        while (zlo <= zend) {
-          // one image of direction 2: cells w0..w1 of this column, contiguous
-          const int im = g.periodic[2] ? fdiv(zlo, g.nc[2]) : 0;
-          const int seg_end = g.periodic[2] ? min(zend, (im + 1) * g.nc[2] - 1) : zend;
-          const int w0 = zlo - im * g.nc[2], w1 = seg_end - im * g.nc[2];
-          const double shz_d = im * g.L[2];
-          const T shz = (T)shz_d, shzl = (T)(shz_d - (double)shz);
-          const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
-          for (int j = beg + lane; j < end; j += GL) {
+  // column pruning in the working precision with a margin (only decides what to visit)
+  const T cs0 = (T)(g.L[0] / g.nc[0]), cs1 = (T)(g.L[1] / g.nc[1]), cs2 = (T)(g.L[2] / g.nc[2]);
+  const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);
+  const T tx = xt.x, ty = xt.y, tz = xt.z;
+  int qn = 0;
+  // evaluate the queued pairs [0, cnt) (cnt <= 32), one per lane
+  auto flush = [&](int cnt) {
+    __syncwarp();
+    if (lane < cnt) {
+      const T r0 = q.r0[lane], r1 = q.r1[lane], r2 = q.r2[lane];
+      real_pair<T, KERNEL, RMAX>(r0, r1, r2, r0 * r0 + r1 * r1 + r2 * r2, xi, xi2, c2pi,
+                                 a.fs + (size_t)q.j[lane] * C, a.n_rhs, acc);
+    }
+    __syncwarp();
+  };
+  for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
+    int ux = cx + dx;
+    double shx_d = 0;
+    if (g.periodic[0]) {
+      int im = fdiv(ux, g.nc[0]);
+      ux -= im * g.nc[0];
+      shx_d = im * g.L[0];
+    } else if (ux < 0 || ux >= g.nc[0]) continue;
+    // distance from the target to the slab of cells ux (in its image) along direction 0
+    const T x0 = (T)(cx + dx) * cs0, x1 = x0 + cs0;  // unwrapped cell = image position
+    const T ddx = tx < x0 ? x0 - tx : (tx > x1 ? tx - x1 : T(0));
+    if (ddx * ddx >= rcp2) continue;
+    const T shx = (T)shx_d, shxl = (T)(shx_d - (double)shx);
+    for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
+      int uy = cy + dy;
+      double shy_d = 0;
+      if (g.periodic[1]) {
+        int im = fdiv(uy, g.nc[1]);
+        uy -= im * g.nc[1];
+        shy_d = im * g.L[1];
+      } else if (uy < 0 || uy >= g.nc[1]) continue;
+      const T y0 = (T)(cy + dy) * cs1, y1 = y0 + cs1;
+      const T ddy = ty < y0 ? y0 - ty : (ty > y1 ? ty - y1 : T(0));
+      const T rem = rcp2 - ddx * ddx - ddy * ddy;
+      if (rem <= T(0)) continue;
+      // cells along direction 2 that can hold sources within rc: |z - tz| < sqrt(rem)
+      const T zr = sqrt(rem);
+      int zlo = (int)floor((tz - zr) / cs2), zend = (int)floor((tz + zr) / cs2);
+      zlo = max(zlo, cz - g.range[2]);
+      zend = min(zend, cz + g.range[2]);
+      if (!g.periodic[2]) {
+        zlo = max(zlo, 0);
+        zend = min(zend, g.nc[2] - 1);
+      }
+      const T shy = (T)shy_d, shyl = (T)(shy_d - (double)shy);
+      const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
+      while (zlo <= zend) {
+        const int im = g.periodic[2] ? fdiv(zlo, g.nc[2]) : 0;
+        const int seg_end = g.periodic[2] ? min(zend, (im + 1) * g.nc[2] - 1) : zend;
+        const int w0 = zlo - im * g.nc[2], w1 = seg_end - im * g.nc[2];
+        const double shz_d = im * g.L[2];
+        const T shz = (T)shz_d, shzl = (T)(shz_d - (double)shz);
+        const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
+        for (int jb = beg; jb < end; jb += 32) {
+          const int j = jb + lane;
+          bool in = false;
+          T r0 = 0, r1 = 0, r2 = 0;
+          if (j < end) {
             const V4 xs = a.xs[j];
-            T r0, r1, r2;
             if (sizeof(T) == 4) {
               // hi + lo separation; x_source_hi + shift split exactly (Fast2Sum)
               const V4 xl = a.xsl[j];
@@ -746,27 +754,45 @@ __global__ void __launch_bounds__(128) k_real(RealArgs<T> a) {
               r1 = xt.y - (xs.y + shy);
               r2 = xt.z - (xs.z + shz);
             }
-            const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
-            if (rr2 < a.rc2) real_pair<T, KERNEL, RMAX>(r0, r1, r2, rr2, xi, xi2, c2pi, a.fs + (size_t)j * C,
-                                                       a.n_rhs, acc);
+            in = r0 * r0 + r1 * r1 + r2 * r2 < a.rc2;
           }
-          zlo = seg_end + 1;
+          const unsigned bal = __ballot_sync(0xffffffffu, in);
+          if (in) {
+            const int pos = qn + __popc(bal & ((1u << lane) - 1u));
+            q.r0[pos] = r0;
+            q.r1[pos] = r1;
+            q.r2[pos] = r2;
+            q.j[pos] = j;
+          }
+          qn += __popc(bal);
+          if (qn >= 32) {
+            flush(32);
+            qn -= 32;
+            if (lane < qn) {  // move the overflow (entries 32..qn+31) to the front
+              q.r0[lane] = q.r0[32 + lane];
+              q.r1[lane] = q.r1[32 + lane];
+              q.r2[lane] = q.r2[32 + lane];
+              q.j[lane] = q.j[32 + lane];
+            }
+            __syncwarp();
+          }
         }
+        zlo = seg_end + 1;
       }
     }
   }
-  // combine the GL lanes of the group
+  if (qn > 0) flush(qn);
 #pragma unroll
   for (int k = 0; k < 3 * RMAX; ++k) {
     T v = acc[k];
 #pragma unroll
-    for (int off = GL / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off, GL);
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     acc[k] = v;
   }
-  if (active && lane == 0) {
+  if (lane == 0) {
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-      for (int q = 0; q < 3; ++q) a.u[((size_t)r * a.ntgt + i) * 3 + q] += acc[3 * r + q];
+      for (int qq = 0; qq < 3; ++qq) a.u[((size_t)r * a.ntgt + i) * 3 + qq] += acc[3 * r + qq];
   }
 }
 
@@ -882,8 +908,15 @@ static void free_plan(se_plan_t* p) {
     delete p->inv;
   }
   if (p->pkb_coef.p) cudaFree(p->pkb_coef.p);
-  for (int d = 0; d < 3; ++d)
+  for (int d = 0; d < 3; ++d) {
     if (p->gtab[d].p) cudaFree(p->gtab[d].p);
+    if (p->ptab[d].p) cudaFree(p->ptab[d].p);
+    if (p->mod0[d].p) cudaFree(p->mod0[d].p);
+    for (int c = 0; c < 3; ++c)
+      if (p->ftab[c][d].p) cudaFree(p->ftab[c][d].p);
+  }
+  for (int i = 0; i < 2; ++i)
+    if (p->atr[i].p) cudaFree(p->atr[i].p);
   if (p->d_status) cudaFree(p->d_status);
   if (p->pin) cudaFreeHost(p->pin);
   for (int i = 0; i < 10; ++i)
@@ -936,7 +969,6 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   for (int d = 0; d < 3; ++d)
     if (!(box[d] > 0) || !std::isfinite(box[d])) return SE_ERR_ARG;
   if (M[0] < 2) return SE_ERR_ARG;
-  if (D != 3) return SE_ERR_UNSUPPORTED;  // reduced periodicity: see se_plan_create_free
   se_opts o;
   se_opts_default(&o);
   if (opts) o = *opts;
@@ -963,19 +995,77 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   g.h = h;
   g.inv_h = 1.0 / h;
   g.P = P;
+  const int fM = o.f_M > 0 ? o.f_M : 4;
+  const int kmask = o.kernel_mask ? o.kernel_mask : 7;
   for (int d = 0; d < 3; ++d) {
     g.L[d] = box[d];
     g.periodic[d] = d < D;
     g.origin[d] = 0.0;
     double md = box[d] / h;
-    int mi = (int)std::llround(md);
-    if (std::fabs(md - mi) > 1e-9 * md || mi < 2 || (mi & 1) || mi < P) {
-      free_plan(p);
-      return SE_ERR_ARG;
+    if (d < D) {
+      int mi = (int)std::llround(md);
+      if (std::fabs(md - mi) > 1e-9 * md || mi < 2 || (mi & 1) || mi < P) {
+        free_plan(p);
+        return SE_ERR_ARG;
+      }
+      g.m[d] = mi;
+      g.n[d] = mi;
+    } else {
+      // extended grid of the free direction, Eq. (extended-grid-size), unless given
+      int me = o.Mext[d];
+      if (me <= 0) {
+        double v = 0;
+        for (int k : {SE_STOKESLET, SE_ROTLET, SE_STRESSLET}) {
+          if (!(kmask & k)) continue;
+          double lam = o.lambda > 0 ? o.lambda : lambda_table(k, D);
+          double theta = k == SE_ROTLET ? 0.0 : 8.0;
+          v = std::max(v, md + P + (lam - 1.0) * std::max((double)P, theta));
+        }
+        me = fM * (int)std::ceil(v / fM - 1e-9);
+      }
+      if ((me & 1) || me < (int)std::ceil(md - 1e-9) + P) {
+        free_plan(p);
+        return SE_ERR_ARG;
+      }
+      g.m[d] = me;
+      g.n[d] = D == 0 ? 2 * me : me;  // D = 0: zero-padded to 2M' (Alg. 1, FFT step)
+      p->dL[d] = me * h - box[d];
+      g.origin[d] = -0.5 * p->dL[d];  // Eq. (extended-box)
     }
-    g.m[d] = mi;
-    g.n[d] = mi;
-    g.ntile[d] = cdiv(mi, TS);
+    g.ntile[d] = cdiv(g.m[d], TS);
+  }
+  if (D < 3) {
+    // truncation radius, Eq. (truncation-radius), and upsampling, Sec. 4.5
+    double R2 = 0, minLe = 1e300;
+    for (int d = D; d < 3; ++d) {
+      double Le = h * g.m[d];
+      R2 += Le * Le;
+      minLe = std::min(minLe, Le);
+    }
+    p->R = std::sqrt(R2);
+    p->s0 = o.s0 > 0 ? o.s0 : std::ceil(10.0 * (1.0 + p->R / minLe) - 1e-9) / 10.0;
+    if (D > 0) {
+      const double Q = o.Q > 0 ? o.Q : 1.0;
+      const double Lc = std::cbrt(box[0] * box[1] * box[2]);
+      double Umin = 1e300;
+      for (int k : {SE_STOKESLET, SE_ROTLET, SE_STRESSLET})
+        if (kmask & k) Umin = std::min(Umin, pot_mag(k, Lc, Q, xi));
+      const double tau = o.tol_abs > 0 ? o.tol_abs : 1e-10 * Umin;
+      const double lg = std::max(0.0, std::log(Umin / (2.0 * tau)) / (2.0 * M_PI));
+      double ss = 1.0;
+      int kb = 0;
+      upsampling_rule(D, box, h, g.m, lg, &ss, &kb);  // Eqs. (upsampling-factor-sstar), (estimate-kbarstar)
+      p->s_star = o.s_star > 0 ? o.s_star : ss;
+      int ks = o.kbar_star >= 0 ? o.kbar_star : kb;
+      int kmax = g.m[0] / 2 - 1;
+      if (D == 2) kmax = std::min(kmax, g.m[1] / 2 - 1);
+      p->kbar_star = std::max(0, std::min(ks, kmax));
+    }
+    for (int d = D; d < 3; ++d) {
+      p->ncls[0][d] = fM * (int)std::ceil(p->s0 * g.m[d] / fM - 1e-9);
+      p->ncls[1][d] = fM * (int)std::ceil(std::max(1.0, p->s_star) * g.m[d] / fM - 1e-9);
+      p->ncls[2][d] = g.m[d];
+    }
   }
   window_setup(&p->win, window, P, h);
   if (cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess) {
@@ -984,7 +1074,10 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
     return SE_ERR_NOMEM;
   }
   cudaMemset(p->d_status, 0, sizeof(int));
-  se_status st = build_tables(p);
+  se_status st = D == 3 ? build_tables(p) : SE_OK;
+  if (st == SE_OK && p->window == SE_WIN_PKB && D < 3)
+    st = p->prec == SE_FP32 ? upload<float>(p->win.pkb, &p->pkb_coef) : upload<double>(p->win.pkb, &p->pkb_coef);
+  if (st == SE_OK && D < 3) st = free_plan_setup(p);
   if (st != SE_OK) {
     free_plan(p);
     return st;
@@ -1105,18 +1198,32 @@ se_status fft_exec<double>(cufftHandle h, bool forward, double* real, double* cp
 }
 
 template <typename T, int CMAX>
-void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C,
-                   T* grid) {
-  // split the source-tile slabs along direction 0 over several CTAs when there are too few
-  // tiles to fill the GPU; the partial tiles are then added atomically into a zeroed grid
+void spread_launch_group(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int Ctot,
+                         int c0, int C, int nslab, T* grid) {
   const GridGeom& g = p->geom;
-  const long long tiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
-  const int nslab = tiles >= 4 * 152 ? 1 : 3;
-  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
-  if (nslab > 1) cudaMemsetAsync(grid, 0, sizeof(T) * C * G, p->stream);
   dim3 grd(g.ntile[0] * nslab, g.ntile[1], g.ntile[2]);
   ++p->launches;
-  k_spread<T, CMAX><<<grd, 256, 0, p->stream>>>(g, tile_start, base, w, sf, C, nslab, grid);
+  k_spread<T, CMAX><<<grd, 64, 0, p->stream>>>(g, tile_start, base, w, sf, Ctot, c0, C, nslab, grid);
+}
+
+template <typename T>
+void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C, T* grid) {
+  // deal the source tiles of each output tile over nslab CTAs so that the grid has enough
+  // CTAs to fill the GPU; the partial tiles are then added atomically into a zeroed grid.
+  // Components go in groups that fit the registers (24 floats or 12 doubles per grid point).
+  const GridGeom& g = p->geom;
+  const long long tiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
+  int nslab = (int)std::min<long long>(9, std::max<long long>(1, (16LL * 152 + tiles - 1) / tiles));
+  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+  if (nslab > 1) cudaMemsetAsync(grid, 0, sizeof(T) * C * G, p->stream);
+  const int CG = sizeof(T) == 4 ? 24 : 12;
+  for (int c0 = 0; c0 < C; c0 += CG) {
+    const int Cc = std::min(CG, C - c0);
+    if (Cc <= 3) spread_launch_group<T, 3>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
+    else if (Cc <= 6) spread_launch_group<T, 6>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
+    else if (Cc <= 12) spread_launch_group<T, 12>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
+    else spread_launch_group<T, 24>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
+  }
 }
 
 template <typename T, int NC>
@@ -1128,9 +1235,8 @@ void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, c
 
 template <typename T, int K, int R>
 void real_launch_k(se_plan_t* p, const RealArgs<T>& a) {
-  constexpr int GL = 8;
   ++p->launches;
-  k_real<T, K, R, GL><<<grid1d((long long)a.ntgt * GL, 128), 128, 0, p->stream>>>(a);
+  k_real<T, K, R><<<grid1d(a.ntgt, RS_WARPS), 32 * RS_WARPS, 0, p->stream>>>(a);
 }
 template <typename T, int R>
 void real_launch(se_plan_t* p, const RealArgs<T>& a) {
@@ -1184,41 +1290,34 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     stage.mark();  // 1: bin + weights
     const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
-    void *grid, *spec, *ugrid;
+    void *grid, *spec = nullptr, *ugrid;
     SE_TRY(buf(p, "grid", sizeof(T) * C * G, &grid));
-    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
+    if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
     SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
-    if (C <= 3) spread_launch<T, 3>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
-    else if (C <= 6) spread_launch<T, 6>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
-    else if (C <= 12) spread_launch<T, 12>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
-    else if (C <= 24) spread_launch<T, 24>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
-    else spread_launch<T, 48>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    if (g.n[0] != g.m[0] || g.n[1] != g.m[1] || g.n[2] != g.m[2])
+      SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));  // zero padding (D = 0)
+    spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
     SE_CUDA(cudaGetLastError());
     p->last_grid_comps = C;
     stage.mark();  // 2: spread
+    if (p->D < 3) {
+      // adaptive FFT (D = 2, 1) or padded FFT with the precomputed kernel (D = 0)
+      SE_TRY(fourier_free<T>(p, kernel, n_rhs, (T*)grid, C, (T*)ugrid, NC));
+      stage.mark();  // 3
+      stage.mark();  // 4
+      stage.mark();  // 5: fft + scale + ifft reported together under "fft"
+    } else {
     cufftHandle hf, hi;
     SE_TRY(get_fft(p, true, C, &hf));
     SE_TRY(get_fft(p, false, NC, &hi));
     SE_TRY(fft_exec<T>(hf, true, (T*)grid, (T*)spec));
     stage.mark();  // 3: fft
-    ScaleArgs<T> sa;
-    sa.n0 = g.n[0];
-    sa.n1 = g.n[1];
-    sa.n2 = g.n[2];
-    sa.h2 = g.n[2] / 2 + 1;
-    sa.kf0 = (T)(2.0 * M_PI / g.L[0]);
-    sa.kf1 = (T)(2.0 * M_PI / g.L[1]);
-    sa.kf2 = (T)(2.0 * M_PI / g.L[2]);
-    sa.inv4xi2 = (T)(1.0 / (4.0 * p->xi * p->xi));
-    sa.g0 = (const T*)p->gtab[0].p;
-    sa.g1 = (const T*)p->gtab[1].p;
-    sa.g2 = (const T*)p->gtab[2].p;
-    ++p->launches;
-    k_scale3p<T><<<grid1d((long long)H, 256), 256, 0, st>>>(sa, kernel, n_rhs, (T*)spec);
-    SE_CUDA(cudaGetLastError());
+    ScaleTables<T> tb{(const T*)p->gtab[0].p, (const T*)p->gtab[1].p, (const T*)p->gtab[2].p, nullptr};
+    SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
     stage.mark();  // 4: scale
     SE_TRY(fft_exec<T>(hi, false, (T*)ugrid, (T*)spec));
     stage.mark();  // 5: ifft
+    }
     // targets: star form reuses the sorted sources and their weights
     const int *tperm = perm, *tbase = (int*)base;
     const T* tw = (T*)wts;
@@ -1341,6 +1440,8 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
                                                   -8.0 * M_PI / vol, u, p->d_status);
     SE_CUDA(cudaGetLastError());
   }
+  if ((parts & SE_PART_CORR) && kernel == SE_STOKESLET)
+    SE_TRY(gauge_correction<T>(p, strengths, N, n_rhs, NT, u));
   stage.mark();  // 8: corrections
   p->timed_pending = p->timers.on;
   return SE_OK;
@@ -1510,11 +1611,10 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   ra.tperm = perm;
   ra.tcell = tcell;
   ra.u = u;
-  constexpr int GL = 8;
-  const int grid = grid1d((long long)N * GL, 128);
-  if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1, GL><<<grid, 128, 0, st>>>(ra);
-  else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1, GL><<<grid, 128, 0, st>>>(ra);
-  else k_real<T, SE_STRESSLET, 1, GL><<<grid, 128, 0, st>>>(ra);
+  const int grid = grid1d(N, RS_WARPS);
+  if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
+  else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
+  else k_real<T, SE_STRESSLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }
@@ -1537,4 +1637,78 @@ extern "C" se_status se_real_noalloc(int periodicity, const double box[3], doubl
                                      (float*)u, st);
   return real_noalloc_impl<double>(periodicity, box, xi, rc, kernel, (int)n_src, src, (const double*)strengths,
                                    (double*)u, st);
+}
+
+// ============================================ batches of configurations under a CUDA graph
+//
+// Many independent configurations (different N, box, periodicity or parameters, each with
+// its own plan and its own right-hand sides) evaluated as one unit: se_batch_create runs every
+// evaluation once (so that every buffer and cuFFT plan exists), then records all of them on
+// the shared stream into a CUDA graph; se_batch_launch replays the graph with one launch.
+
+struct se_batch_t {
+  cudaStream_t stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n_cfg = 0;
+};
+
+extern "C" se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h* plans, const int* kernel_mask,
+                                     const long long* n_src, const double* const* src,
+                                     const void* const* strengths, const int* n_rhs, void* const* u) {
+  if (!out) return SE_ERR_ARG;
+  *out = nullptr;
+  if (n_cfg < 1 || !plans || !kernel_mask || !n_src || !src || !strengths || !n_rhs || !u) return SE_ERR_ARG;
+  cudaStream_t st = plans[0] ? plans[0]->stream : nullptr;
+  for (int i = 0; i < n_cfg; ++i) {
+    if (!plans[i] || plans[i]->stream != st) return SE_ERR_ARG;  // one shared stream
+    if (plans[i]->timers.on) return SE_ERR_ARG;                   // no timing inside a graph
+  }
+  if (st == nullptr) return SE_ERR_ARG;  // the legacy default stream cannot be captured
+  // warm-up: every buffer and cuFFT plan is created here, outside the capture
+  for (int i = 0; i < n_cfg; ++i)
+    SE_TRY(se_eval(plans[i], kernel_mask[i], n_src[i], src[i], strengths[i], n_rhs[i], 0, nullptr, u[i]));
+  SE_CUDA(cudaStreamSynchronize(st));
+  se_batch_t* b = new (std::nothrow) se_batch_t();
+  if (!b) return SE_ERR_NOMEM;
+  b->stream = st;
+  b->n_cfg = n_cfg;
+  if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    delete b;
+    cudaGetLastError();
+    return SE_ERR_CUDA;
+  }
+  se_status s = SE_OK;
+  for (int i = 0; i < n_cfg && s == SE_OK; ++i)
+    s = se_eval(plans[i], kernel_mask[i], n_src[i], src[i], strengths[i], n_rhs[i], 0, nullptr, u[i]);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (s != SE_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    delete b;
+    cudaGetLastError();
+    return s != SE_OK ? s : SE_ERR_CUDA;
+  }
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
+    cudaGraphDestroy(g);
+    delete b;
+    cudaGetLastError();
+    return SE_ERR_CUDA;
+  }
+  *out = b;
+  return SE_OK;
+}
+
+extern "C" se_status se_batch_launch(se_batch_h b) {
+  if (!b || !b->exec) return SE_ERR_ARG;
+  SE_CUDA(cudaGraphLaunch(b->exec, b->stream));
+  return SE_OK;
+}
+
+extern "C" void se_batch_destroy(se_batch_h b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  delete b;
 }

@@ -1,0 +1,859 @@
+// libse: the Fourier-space steps (ii)-(iv) of Alg. 1 for reduced periodicity (D = 2, 1, 0):
+// the adaptive FFT of Sec. 3.4 with the modified kernels of Sec. 3.1 for D = 2 and D = 1,
+// and the zero-padded transform with the precomputed truncated kernel of Sec. 3.5 for D = 0.
+//
+// Layouts (component-major, direction 2 contiguous):
+//   D = 2: grid [C][M0][M1][M'2] -> 2-D R2C over (0,1) -> spec [C][M0][M1/2+1][M'2]; the
+//          columns along direction 2 are transformed per class: k^P = 0 (zero-padded to n0),
+//          K_* (|kbar_i| <= kbar_*, padded to n_*), K_inf (length M'2, in place).
+//   D = 1: grid [C][M0][M'1][M'2] -> 1-D R2C over 0 -> spec [C][M0/2+1][M'1][M'2]; the planes
+//          along (1,2) are transformed per class in the same way.
+//   D = 0: grid [C][2M'0][2M'1][2M'2] (points spread into the first M' of each direction)
+//          -> 3-D R2C -> scaled by the precomputed kernel -> C2R.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "se_device.cuh"
+
+namespace se {
+
+// ----------------------------------------------------------- modified kernels (host, FP64)
+
+// 1 - cos t - t sin t by its series for small t
+static double s_1mcos_tsin(double t) {
+  double out = 0, term = 1;
+  for (int m = 1; m < 25; ++m) {
+    term *= -t * t / ((2.0 * m - 1) * (2.0 * m));
+    out += term * (2.0 * m - 1);
+  }
+  return out;
+}
+// H^_R^{2P}(kappa), below Eq. (2p-vico-H-kernel); -2 pi R^2 at 0
+static double hat_H2p(double kap, double R) {
+  double t = R * std::fabs(kap);
+  if (t == 0) return -2.0 * M_PI * R * R;
+  if (t < 0.5) return 4.0 * M_PI * R * R * s_1mcos_tsin(t) / (t * t);
+  return 4.0 * M_PI / (kap * kap) * (1.0 - std::cos(t) - t * std::sin(t));
+}
+// Im Z^_R^{2P}(kappa) = -8 pi sin^2(R kappa/2)/kappa; 0 at 0
+static double hat_Z2p_im(double kap, double R) {
+  if (kap == 0) return 0.0;
+  double s = std::sin(R * kap / 2);
+  return -8.0 * M_PI * s * s / kap;
+}
+// 1 - J0(t) (which = 0) or 1 - J0(t) - t J1(t)/2 (which = 1) by their power series
+static double s_bessel(double t, int which) {
+  double q = 0.25 * t * t, term = 1, out = 0;
+  for (int m = 1; m < 40; ++m) {
+    term *= q / ((double)m * m);
+    double sgn = (m % 2 == 0) ? -1.0 : 1.0;
+    out += which == 0 ? sgn * term : sgn * term * (1.0 - m);
+  }
+  return out;
+}
+// Eq. (optimal-1p-harmonic), pi R^2 at 0
+static double hat_H1p(double kap, double R) {
+  double t = R * kap;
+  if (t == 0) return M_PI * R * R;
+  if (t < 2.0) return 4.0 * M_PI * R * R * s_bessel(t, 0) / (t * t);
+  return 4.0 * M_PI / (kap * kap) * (1.0 - std::cyl_bessel_j(0.0, t));
+}
+// Eq. (optimal-1p-biharmonic), -pi R^4 / 8 at 0
+static double hat_B1p(double kap, double R) {
+  double t = R * kap;
+  if (t == 0) return -M_PI * R * R * R * R / 8.0;
+  if (t < 2.0) return -8.0 * M_PI * std::pow(R, 4) * s_bessel(t, 1) / std::pow(t, 4);
+  return -8.0 * M_PI / std::pow(kap, 4) * (1.0 - std::cyl_bessel_j(0.0, t) - 0.5 * t * std::cyl_bessel_j(1.0, t));
+}
+
+// ---------------------------------------------------------------- device: 0P precompute
+
+// Eq. (vico-harmonic-0p) and Eq. (optimal-biharmonic-0p) with the series for small R kappa
+__device__ inline double dev_hat0p(int biharm, double kap, double R) {
+  const double pi = 3.14159265358979323846;
+  if (!biharm) {
+    if (kap == 0) return 2.0 * pi * R * R;
+    double s = sin(R * kap / 2);
+    return 8.0 * pi * s * s / (kap * kap);
+  }
+  double t = R * kap;
+  if (t < 1.0) {
+    // -8 pi R^4 sum_{m>=2} (-1)^m (m-1) t^{2m-4} / (2m+1)!
+    double sum = 0, tp = 1, fact = 120.0;  // t^{2m-4}, (2m+1)! at m = 2
+    for (int m = 2; m < 20; ++m) {
+      sum += ((m & 1) ? -1.0 : 1.0) * (m - 1) * tp / fact;
+      tp *= t * t;
+      fact *= (2.0 * m + 2) * (2.0 * m + 3);
+    }
+    return -8.0 * pi * R * R * R * R * sum;
+  }
+  return -8.0 * pi / (kap * kap * kap * kap) * (1.0 + 0.5 * cos(t) - 1.5 * sin(t) / t);
+}
+
+// A^_R on the half spectrum of the upsampled grid (complex, imaginary part 0)
+__global__ void k_fill_ahat(int n0, int n1, int n2, double h, double R, int biharm, double* out) {
+  const int h2 = n2 / 2 + 1;
+  const size_t N = (size_t)n0 * n1 * h2;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int i2 = (int)(i % h2), i1 = (int)((i / h2) % n1), i0 = (int)(i / ((size_t)h2 * n1));
+  const int b0 = i0 < (n0 + 1) / 2 ? i0 : i0 - n0, b1 = i1 < (n1 + 1) / 2 ? i1 : i1 - n1, b2 = i2;
+  const double pi = 3.14159265358979323846;
+  const double k0 = 2 * pi * b0 / (n0 * h), k1 = 2 * pi * b1 / (n1 * h), k2 = 2 * pi * b2 / (n2 * h);
+  out[2 * i] = dev_hat0p(biharm, sqrt(k0 * k0 + k1 * k1 + k2 * k2), R);
+  out[2 * i + 1] = 0.0;
+}
+
+// truncate A_R to the 2M' offsets around the origin (FFT order), normalise the inverse
+// transform, and mollify the biharmonic (Sec. 3.5)
+__global__ void k_trunc_moll(const double* A, int u0, int u1, int u2, int m0, int m1, int m2, int biharm,
+                             double scale, double* At) {
+  const int n0 = 2 * m0, n1 = 2 * m1, n2 = 2 * m2;
+  const size_t N = (size_t)n0 * n1 * n2;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const int i2 = (int)(i % n2), i1 = (int)((i / n2) % n1), i0 = (int)(i / ((size_t)n2 * n1));
+  const int o0 = i0 < m0 ? i0 : i0 - n0, o1 = i1 < m1 ? i1 : i1 - n1, o2 = i2 < m2 ? i2 : i2 - n2;
+  const int s0 = ((o0 % u0) + u0) % u0, s1 = ((o1 % u1) + u1) % u1, s2 = ((o2 % u2) + u2) % u2;
+  double v = A[((size_t)s0 * u1 + s1) * u2 + s2] * scale;
+  if (biharm) {
+    // mu = (f(3), f(2), f(1), f(0), 1, ..., 1, f(0), f(1), f(2), f(3)) in natural order
+    const double a = 2.0 / 7.0 * sqrt(log(100.0));
+    const int nat[3] = {o0 + m0, o1 + m1, o2 + m2};
+    const int len[3] = {n0, n1, n2};
+    for (int d = 0; d < 3; ++d) {
+      int t = -1;
+      if (nat[d] < 4) t = 3 - nat[d];
+      else if (nat[d] >= len[d] - 4) t = nat[d] - (len[d] - 4);
+      if (t >= 0) v *= exp(-a * a * t * t) + exp(-a * a * (t - 7.0) * (t - 7.0));
+    }
+  }
+  At[i] = v;
+}
+
+template <typename T>
+__global__ void k_real_part(const double* z, size_t n, T* out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (T)z[2 * i];
+}
+
+// ----------------------------------------------------------- device: AFT copies and scaling
+
+// column / plane selection: mode 0 = the k^P = 0 class, 1 = K_*, 2 = every column in place
+struct ColMap {
+  int D;        // 2 or 1
+  int mode;
+  int M0, M1;   // periodic grid sizes (D = 2: M0, M1; D = 1: M0)
+  int H;        // stored extent of the halved periodic direction (M1/2+1 for D = 2, M0/2+1 for D = 1)
+  int kstar;
+};
+
+// periodic indices of column j of a class (FFT order); returns false for a slot that is not a
+// real column
+__device__ inline void colmap_idx(const ColMap& m, int j, int* i0, int* i1) {
+  if (m.D == 2) {
+    if (m.mode == 0) { *i0 = 0; *i1 = 0; return; }
+    if (m.mode == 2) { *i0 = j / m.H; *i1 = j % m.H; return; }
+    // K_*: a in [-k*, k*], b in [0, k*], (a, b) != (0, 0)
+    const int w = m.kstar + 1;
+    int jj = j + (j >= m.kstar * w ? 1 : 0);
+    const int a = jj / w - m.kstar, b = jj % w;
+    *i0 = a < 0 ? a + m.M0 : a;
+    *i1 = b;
+    return;
+  }
+  // D = 1: planes indexed by the x wavenumber (half spectrum 0..M0/2)
+  if (m.mode == 0) *i0 = 0;
+  else if (m.mode == 1) *i0 = 1 + j;
+  else *i0 = j;
+  *i1 = 0;
+}
+
+__device__ inline bool in_class(const ColMap& m, int i0, int i1, int cls) {
+  // class of the periodic wavenumber (i0, i1): 0, 1 (K_*) or 2 (K_inf)
+  if (m.D == 2) {
+    const int a = i0 < m.M0 / 2 ? i0 : i0 - m.M0, b = i1;
+    int c = (a == 0 && b == 0) ? 0 : ((abs(a) <= m.kstar && b <= m.kstar) ? 1 : 2);
+    return c == cls;
+  }
+  int c = i0 == 0 ? 0 : (i0 <= m.kstar ? 1 : 2);
+  return c == cls;
+}
+
+// copy class columns (D = 2: length Mz along direction 2; D = 1: planes Mf1 x Mf2) from spec
+// into a zero-padded class buffer, or back (truncated) for the output components
+struct Ext2 {
+  int v[2];
+};
+template <typename T>
+__global__ void k_aft_copy(ColMap m, int ncomp, int ncols, Ext2 fm, Ext2 fn, bool to_buffer, T* spec, T* bufp) {
+  // fm: extents in spec of the free directions (1 or 2 values), fn: padded extents
+  const int* f_m = fm.v;
+  const int* f_n = fn.v;
+  const int nf = m.D == 2 ? 1 : 2;
+  const size_t plane_n = nf == 1 ? (size_t)f_n[0] : (size_t)f_n[0] * f_n[1];
+  const size_t plane_m = nf == 1 ? (size_t)f_m[0] : (size_t)f_m[0] * f_m[1];
+  const size_t N = (size_t)ncomp * ncols * plane_n;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const size_t e = i % plane_n;
+  const int j = (int)((i / plane_n) % ncols);
+  const int c = (int)(i / (plane_n * ncols));
+  int a0, a1;
+  if (nf == 1) {
+    a0 = (int)e;
+    a1 = 0;
+  } else {
+    a0 = (int)(e / f_n[1]);
+    a1 = (int)(e % f_n[1]);
+  }
+  const bool inside = nf == 1 ? a0 < f_m[0] : (a0 < f_m[0] && a1 < f_m[1]);
+  int i0, i1;
+  colmap_idx(m, j, &i0, &i1);
+  size_t so;
+  if (m.D == 2) so = (((size_t)c * m.M0 + i0) * m.H + i1) * plane_m + (inside ? a0 : 0);
+  else so = ((size_t)c * m.H + i0) * plane_m + (inside ? (size_t)a0 * f_m[1] + a1 : 0);
+  const size_t bo = i;
+  if (to_buffer) {
+    bufp[2 * bo] = inside ? spec[2 * so] : T(0);
+    bufp[2 * bo + 1] = inside ? spec[2 * so + 1] : T(0);
+  } else if (inside) {
+    spec[2 * so] = bufp[2 * bo];
+    spec[2 * so + 1] = bufp[2 * bo + 1];
+  }
+}
+
+struct FreeScale {
+  ColMap m;
+  int cls;        // 0, 1, 2
+  int ncols;
+  int fn[2];      // transform lengths in the free directions (one for D = 2)
+  double h;
+  double kf0, kf1;  // 2 pi / L_0, 2 pi / L_1 (periodic)
+  double inv4xi2;
+};
+
+// Scaling step, Eq. (SE-scaling-disc), on a class buffer [C][ncols][free...] in place:
+// regular kernel for k^P != 0; the modified kernels of Eqs. (mod-*-2p) / (mod-*-1p) for the
+// k^P = 0 class. Tables (plan precision): tp0/tp1 periodic factors, tf0/tf1 free factors
+// (exp(-k^2/4xi^2) / w^2 / n each); for the k^P = 0 class mod0 / mod1 / mod2 hold the
+// modified-kernel scalars.
+template <typename T>
+__global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __restrict__ tp0,
+                             const T* __restrict__ tp1, const T* __restrict__ tf0, const T* __restrict__ tf1,
+                             const T* __restrict__ mod0, const T* __restrict__ mod1, T* __restrict__ spec) {
+  const int nf = a.m.D == 2 ? 1 : 2;
+  const size_t plane = nf == 1 ? (size_t)a.fn[0] : (size_t)a.fn[0] * a.fn[1];
+  const size_t per = (size_t)a.ncols * plane;
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= per) return;
+  const int j = (int)(idx / plane);
+  const size_t e = idx % plane;
+  int i0, i1;
+  colmap_idx(a.m, j, &i0, &i1);
+  // skip columns of other classes when running in place over every column
+  if (a.cls == 2 && !in_class(a.m, i0, i1, 2)) return;
+  int f0 = nf == 1 ? (int)e : (int)(e / a.fn[1]);
+  int f1 = nf == 1 ? 0 : (int)(e % a.fn[1]);
+  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  // wavenumbers
+  bool zero = false;
+  T k0, k1, k2;
+  const double pi2 = 2.0 * 3.14159265358979323846;
+  const int kb_f0 = f0 < a.fn[0] / 2 ? f0 : f0 - a.fn[0];
+  if (f0 == a.fn[0] / 2) zero = true;
+  int kb_f1 = 0;
+  if (nf == 2) {
+    kb_f1 = f1 < a.fn[1] / 2 ? f1 : f1 - a.fn[1];
+    if (f1 == a.fn[1] / 2) zero = true;
+  }
+  T s = 0;
+  T mr = 0, mi = 0, tb = 0;
+  if (a.m.D == 2) {
+    const int kb0 = i0 < a.m.M0 / 2 ? i0 : i0 - a.m.M0;
+    if (i0 == a.m.M0 / 2 || i1 == a.m.M1 / 2) zero = true;
+    k0 = (T)(a.kf0 * kb0);
+    k1 = (T)(a.kf1 * i1);
+    k2 = (T)(pi2 * kb_f0 / (a.fn[0] * a.h));
+    if (a.cls == 0) {
+      mr = mod0[2 * f0];
+      mi = mod0[2 * f0 + 1];
+    } else {
+      const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+      s = regular_scalar<T>(kernel, kk, (T)a.inv4xi2) * tp0[i0] * tp1[i1] * tf0[f0];
+    }
+  } else {
+    if (i0 == a.m.M0 / 2) zero = true;
+    k0 = (T)(a.kf0 * i0);
+    k1 = (T)(pi2 * kb_f0 / (a.fn[0] * a.h));
+    k2 = (T)(pi2 * kb_f1 / (a.fn[1] * a.h));
+    if (a.cls == 0) {
+      mr = mod0[e];       // H^-type table for this kernel
+      tb = mod1 ? mod1[e] : T(0);  // B^ table (stokeslet, stresslet)
+    } else {
+      const T kk = k0 * k0 + k1 * k1 + k2 * k2;
+      s = regular_scalar<T>(kernel, kk, (T)a.inv4xi2) * tp0[i0] * tf0[f0] * tf1[f1];
+    }
+  }
+  const size_t H = (size_t)a.ncols * plane;  // component stride in this buffer
+  for (int r = 0; r < n_rhs; ++r) {
+    T re[6], im[6];
+    for (int c = 0; c < cin; ++c) {
+      const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
+      re[c] = spec[o];
+      im[c] = spec[o + 1];
+    }
+    T ore[3] = {0, 0, 0}, oim[3] = {0, 0, 0};
+    if (!zero) {
+      if (a.cls != 0) {
+        apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
+      } else if (a.m.D == 2) {
+        // modified column: scalar (mr + i mi) times D^S, D^Omega or D^T
+        T vr[3], vi[3];
+        if (kernel == SE_STOKESLET) {
+          vr[0] = 2 * re[0]; vi[0] = 2 * im[0];
+          vr[1] = 2 * re[1]; vi[1] = 2 * im[1];
+          vr[2] = 0; vi[2] = 0;
+        } else if (kernel == SE_ROTLET) {
+          vr[0] = re[1]; vi[0] = im[1];
+          vr[1] = -re[0]; vi[1] = -im[0];
+          vr[2] = 0; vi[2] = 0;
+        } else {
+          // D^T_1lm F_lm = -2 (F13 + F31), D^T_2lm F_lm = -2 (F23 + F32), D^T_3lm F_lm = -2 tr F
+          vr[0] = -4 * re[4]; vi[0] = -4 * im[4];
+          vr[1] = -4 * re[5]; vi[1] = -4 * im[5];
+          vr[2] = -2 * (re[0] + re[1] + re[2]); vi[2] = -2 * (im[0] + im[1] + im[2]);
+        }
+        for (int q = 0; q < 3; ++q) {
+          ore[q] = mr * vr[q] - mi * vi[q];
+          oim[q] = mr * vi[q] + mi * vr[q];
+        }
+      } else {
+        // modified plane (D = 1), k = (0, kappa2, kappa3)
+        const T q2 = k1, q3 = k2;
+        if (kernel == SE_ROTLET) {
+          apply_regular<T>(SE_ROTLET, mr, T(0), q2, q3, re, im, ore, oim);
+        } else if (kernel == SE_STOKESLET) {
+          ore[0] = 2 * mr * re[0];
+          oim[0] = 2 * mr * im[0];
+          ore[1] = tb * (-q3 * q3 * re[1] + q2 * q3 * re[2]);
+          oim[1] = tb * (-q3 * q3 * im[1] + q2 * q3 * im[2]);
+          ore[2] = tb * (q2 * q3 * re[1] - q2 * q2 * re[2]);
+          oim[2] = tb * (q2 * q3 * im[1] - q2 * q2 * im[2]);
+        } else {
+          // 2i C^TH H^ - i C^TB B^ with symmetric F: 11,22,33,12,13,23 = 0..5
+          const T kk = q2 * q2 + q3 * q3;
+          T chr[3], chi[3], cbr[3], cbi[3];
+          chr[0] = 2 * q2 * re[3] + 2 * q3 * re[4];
+          chi[0] = 2 * q2 * im[3] + 2 * q3 * im[4];
+          chr[1] = q2 * re[0];
+          chi[1] = q2 * im[0];
+          chr[2] = q3 * re[0];
+          chi[2] = q3 * im[0];
+          cbr[0] = 0;
+          cbi[0] = 0;
+          const T c22 = q2 * (3 * kk - 2 * q2 * q2), c23 = q3 * (kk - 2 * q2 * q2), c33 = q2 * (kk - 2 * q3 * q3);
+          cbr[1] = c22 * re[1] + 2 * c23 * re[5] + c33 * re[2];
+          cbi[1] = c22 * im[1] + 2 * c23 * im[5] + c33 * im[2];
+          const T d22 = q3 * (kk - 2 * q2 * q2), d23 = q2 * (kk - 2 * q3 * q3), d33 = q3 * (3 * kk - 2 * q3 * q3);
+          cbr[2] = d22 * re[1] + 2 * d23 * re[5] + d33 * re[2];
+          cbi[2] = d22 * im[1] + 2 * d23 * im[5] + d33 * im[2];
+          for (int q = 0; q < 3; ++q) {
+            const T vr = 2 * mr * chr[q] - tb * cbr[q];
+            const T vi = 2 * mr * chi[q] - tb * cbi[q];
+            ore[q] = -vi;  // i (vr + i vi)
+            oim[q] = vr;
+          }
+        }
+      }
+    }
+    for (int q = 0; q < 3; ++q) {
+      const size_t o = (((size_t)(3 * r + q)) * H + idx) * 2;
+      spec[o] = ore[q];
+      spec[o + 1] = oim[q];
+    }
+  }
+}
+
+// gauge constants: u[r][i][j] += c_j sum_n f[r][n][j]
+template <typename T>
+__global__ void k_fsum(const T* f, int n, int n_rhs, double* sums) {
+  __shared__ double red[3][256];
+  for (int r = 0; r < n_rhs; ++r) {
+    double a[3] = {0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      for (int j = 0; j < 3; ++j) a[j] += (double)f[((size_t)r * n + i) * 3 + j];
+    for (int j = 0; j < 3; ++j) red[j][threadIdx.x] = a[j];
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+      if (threadIdx.x < off)
+        for (int j = 0; j < 3; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0)
+      for (int j = 0; j < 3; ++j) atomicAdd(&sums[r * 3 + j], red[j][0]);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_add_const(int nt, int n_rhs, const double* sums, double c0, double c1, double c2, T* u) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nt) return;
+  const double c[3] = {c0, c1, c2};
+  for (int r = 0; r < n_rhs; ++r)
+    for (int j = 0; j < 3; ++j) u[((size_t)r * nt + i) * 3 + j] += (T)(c[j] * sums[r * 3 + j]);
+}
+
+// ----------------------------------------------------------------------- host side
+
+template <typename T>
+static se_status upload_tab(const std::vector<double>& v, DevBuf* b) {
+  std::vector<T> h(v.begin(), v.end());
+  if (b->p) cudaFree(b->p);
+  b->p = nullptr;
+  size_t bytes = sizeof(T) * std::max<size_t>(1, h.size());
+  if (cudaMalloc(&b->p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return SE_ERR_NOMEM;
+  }
+  b->bytes = bytes;
+  if (!h.empty()) SE_CUDA(cudaMemcpy(b->p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+  return SE_OK;
+}
+
+static se_status upload_any(se_plan_t* p, const std::vector<double>& v, DevBuf* b) {
+  return p->prec == SE_FP32 ? upload_tab<float>(v, b) : upload_tab<double>(v, b);
+}
+
+// exp(-k^2/4xi^2) / w^_0(k)^2 / n at the FFT-order wavenumbers of a length-n direction
+static std::vector<double> sep_table(const se_plan_t* p, int n, int count) {
+  std::vector<double> g(count);
+  for (int i = 0; i < count; ++i) {
+    int kb = i < (n + 1) / 2 ? i : i - n;
+    if (i == n / 2) kb = -n / 2;
+    double k = 2.0 * M_PI * kb / (p->geom.h * n);
+    double wh = window_hat(p->win, k);
+    g[i] = std::exp(-k * k / (4.0 * p->xi * p->xi)) / (wh * wh) / n;
+  }
+  return g;
+}
+
+static se_status precompute_0p(se_plan_t* p, int biharm, DevBuf* out) {
+  const GridGeom& g = p->geom;
+  int u[3];
+  const int fM = p->opts.f_M > 0 ? p->opts.f_M : 4;
+  for (int d = 0; d < 3; ++d) u[d] = fM * (int)std::ceil(p->s0 * g.m[d] / fM - 1e-9);
+  const size_t hu = (size_t)u[0] * u[1] * (u[2] / 2 + 1);
+  const size_t nu = (size_t)u[0] * u[1] * u[2];
+  const size_t nt = (size_t)(2 * g.m[0]) * (2 * g.m[1]) * (2 * g.m[2]);
+  const size_t ht = (size_t)(2 * g.m[0]) * (2 * g.m[1]) * (g.m[2] + 1);
+  double *ahat = nullptr, *areal = nullptr, *at = nullptr, *atr = nullptr;
+  se_status st = SE_OK;
+  cufftHandle h1 = 0, h2 = 0;
+  bool h1ok = false, h2ok = false;
+  do {
+    if (cudaMalloc(&ahat, sizeof(double) * 2 * hu) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+    if (cudaMalloc(&areal, sizeof(double) * nu) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+    k_fill_ahat<<<grid1d((long long)hu, 256), 256, 0, p->stream>>>(u[0], u[1], u[2], g.h, p->R, biharm, ahat);
+    if (cufftPlan3d(&h1, u[0], u[1], u[2], CUFFT_Z2D) != CUFFT_SUCCESS) { st = SE_ERR_CUFFT; break; }
+    h1ok = true;
+    cufftSetStream(h1, p->stream);
+    if (cufftExecZ2D(h1, (cufftDoubleComplex*)ahat, areal) != CUFFT_SUCCESS) { st = SE_ERR_CUFFT; break; }
+    cudaStreamSynchronize(p->stream);
+    cudaFree(ahat);
+    ahat = nullptr;
+    cufftDestroy(h1);
+    h1ok = false;
+    if (cudaMalloc(&at, sizeof(double) * nt) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+    k_trunc_moll<<<grid1d((long long)nt, 256), 256, 0, p->stream>>>(areal, u[0], u[1], u[2], g.m[0], g.m[1],
+                                                                   g.m[2], biharm, 1.0 / (double)nu, at);
+    cudaStreamSynchronize(p->stream);
+    cudaFree(areal);
+    areal = nullptr;
+    if (cudaMalloc(&atr, sizeof(double) * 2 * ht) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+    if (cufftPlan3d(&h2, 2 * g.m[0], 2 * g.m[1], 2 * g.m[2], CUFFT_D2Z) != CUFFT_SUCCESS) { st = SE_ERR_CUFFT; break; }
+    h2ok = true;
+    cufftSetStream(h2, p->stream);
+    if (cufftExecD2Z(h2, at, (cufftDoubleComplex*)atr) != CUFFT_SUCCESS) { st = SE_ERR_CUFFT; break; }
+    size_t es = p->prec == SE_FP32 ? 4 : 8;
+    if (cudaMalloc(&out->p, es * ht) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+    out->bytes = es * ht;
+    if (p->prec == SE_FP32)
+      k_real_part<float><<<grid1d((long long)ht, 256), 256, 0, p->stream>>>(atr, ht, (float*)out->p);
+    else
+      k_real_part<double><<<grid1d((long long)ht, 256), 256, 0, p->stream>>>(atr, ht, (double*)out->p);
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) st = SE_ERR_CUDA;
+  } while (0);
+  if (h1ok) cufftDestroy(h1);
+  if (h2ok) cufftDestroy(h2);
+  if (ahat) cudaFree(ahat);
+  if (areal) cudaFree(areal);
+  if (at) cudaFree(at);
+  if (atr) cudaFree(atr);
+  cudaGetLastError();
+  return st;
+}
+
+// Tables and precomputation of a D < 3 plan (called by se_plan_create after the geometry).
+se_status free_plan_setup(se_plan_t* p) {
+  const GridGeom& g = p->geom;
+  const int D = p->D;
+  const double h = g.h;
+  if (D == 0) {
+    for (int d = 0; d < 3; ++d) {
+      int n = g.n[d];
+      SE_TRY(upload_any(p, sep_table(p, n, d == 2 ? n / 2 + 1 : n), &p->ptab[d]));
+    }
+    int mask = p->opts.kernel_mask ? p->opts.kernel_mask : 7;
+    if (mask & SE_ROTLET) SE_TRY(precompute_0p(p, 0, &p->atr[0]));
+    if (mask & (SE_STOKESLET | SE_STRESSLET)) SE_TRY(precompute_0p(p, 1, &p->atr[1]));
+    return SE_OK;
+  }
+  if (D == 2) {
+    SE_TRY(upload_any(p, sep_table(p, g.m[0], g.m[0]), &p->ptab[0]));
+    SE_TRY(upload_any(p, sep_table(p, g.m[1], g.m[1] / 2 + 1), &p->ptab[1]));
+    for (int c = 0; c < 3; ++c) {
+      int n = p->ncls[c][2];
+      SE_TRY(upload_any(p, sep_table(p, n, n), &p->ftab[c][2]));
+    }
+    // k^P = 0 column: modified scalar times gamma^ / w^2 and the normalisation, complex
+    const int n0 = p->ncls[0][2];
+    const double w00 = window_hat(p->win, 0.0);
+    for (int kind = 0; kind < 3; ++kind) {  // 0: stokeslet, 1: stresslet, 2: rotlet
+      std::vector<double> t(2 * n0);
+      for (int i = 0; i < n0; ++i) {
+        int kb = i < n0 / 2 ? i : i - n0;
+        double kap = 2.0 * M_PI * kb / (n0 * h);
+        double wh = window_hat(p->win, kap);
+        double e = std::exp(-kap * kap / (4.0 * p->xi * p->xi));
+        double scr = kind == 2 ? e : e * (1.0 + kap * kap / (4.0 * p->xi * p->xi));
+        double norm = scr / (w00 * w00 * w00 * w00 * wh * wh) / ((double)g.m[0] * g.m[1] * n0);
+        if (i == n0 / 2) norm = 0;
+        if (kind == 0) {
+          t[2 * i] = hat_H2p(kap, p->R) * norm;
+          t[2 * i + 1] = 0;
+        } else {
+          t[2 * i] = 0;
+          t[2 * i + 1] = hat_Z2p_im(kap, p->R) * norm;
+        }
+      }
+      SE_TRY(upload_any(p, t, &p->mod0[kind]));
+    }
+    return SE_OK;
+  }
+  // D = 1
+  SE_TRY(upload_any(p, sep_table(p, g.m[0], g.m[0] / 2 + 1), &p->ptab[0]));
+  for (int c = 0; c < 3; ++c)
+    for (int d = 1; d < 3; ++d) {
+      int n = p->ncls[c][d];
+      SE_TRY(upload_any(p, sep_table(p, n, n), &p->ftab[c][d]));
+    }
+  const int n1 = p->ncls[0][1], n2 = p->ncls[0][2];
+  const double w00 = window_hat(p->win, 0.0);
+  std::vector<double> TH_H((size_t)n1 * n2), TB_H((size_t)n1 * n2), TH_E((size_t)n1 * n2);
+  for (int a = 0; a < n1; ++a)
+    for (int b = 0; b < n2; ++b) {
+      int ka = a < n1 / 2 ? a : a - n1, kb = b < n2 / 2 ? b : b - n2;
+      double k2 = 2.0 * M_PI * ka / (n1 * h), k3 = 2.0 * M_PI * kb / (n2 * h);
+      double kap = std::sqrt(k2 * k2 + k3 * k3);
+      double w2 = window_hat(p->win, k2), w3 = window_hat(p->win, k3);
+      double e = std::exp(-kap * kap / (4.0 * p->xi * p->xi));
+      double scrH = e * (1.0 + kap * kap / (4.0 * p->xi * p->xi));
+      double base = 1.0 / (w00 * w00 * w2 * w2 * w3 * w3) / ((double)g.m[0] * n1 * n2);
+      if (a == n1 / 2 || b == n2 / 2) base = 0;
+      double Hr = hat_H1p(kap, p->R), Br = hat_B1p(kap, p->R);
+      size_t i = (size_t)a * n2 + b;
+      TH_H[i] = Hr * scrH * base;
+      TB_H[i] = Br * scrH * base;
+      TH_E[i] = Hr * e * base;
+    }
+  SE_TRY(upload_any(p, TH_H, &p->mod0[0]));
+  SE_TRY(upload_any(p, TB_H, &p->mod0[1]));
+  SE_TRY(upload_any(p, TH_E, &p->mod0[2]));
+  return SE_OK;
+}
+
+namespace {
+
+// cached cuFFT plans for the free-direction transforms, keyed by a small integer tag
+se_status free_fft(se_plan_t* p, int tag, int batch, int rank, const int* n, int* inembed, int istride,
+                   int idist, int* onembed, int ostride, int odist, cufftType type, cufftHandle* out) {
+  int key = (tag << 20) ^ batch;
+  auto it = p->fwd->find(-1 - key);
+  if (it != p->fwd->end()) {
+    *out = it->second;
+    return SE_OK;
+  }
+  cufftHandle h;
+  int nn[3] = {n[0], rank > 1 ? n[1] : 0, rank > 2 ? n[2] : 0};
+  SE_CUFFT(cufftPlanMany(&h, rank, nn, inembed, istride, idist, onembed, ostride, odist, type, batch));
+  SE_CUFFT(cufftSetStream(h, p->stream));
+  (*p->fwd)[-1 - key] = h;
+  *out = h;
+  return SE_OK;
+}
+
+template <typename T> struct FT;
+template <> struct FT<float> {
+  static constexpr cufftType R2C = CUFFT_R2C, C2R = CUFFT_C2R, C2C = CUFFT_C2C;
+  static cufftResult r2c(cufftHandle h, float* i, float* o) { return cufftExecR2C(h, i, (cufftComplex*)o); }
+  static cufftResult c2r(cufftHandle h, float* i, float* o) { return cufftExecC2R(h, (cufftComplex*)i, o); }
+  static cufftResult c2c(cufftHandle h, float* i, float* o, int dir) {
+    return cufftExecC2C(h, (cufftComplex*)i, (cufftComplex*)o, dir);
+  }
+};
+template <> struct FT<double> {
+  static constexpr cufftType R2C = CUFFT_D2Z, C2R = CUFFT_Z2D, C2C = CUFFT_Z2Z;
+  static cufftResult r2c(cufftHandle h, double* i, double* o) { return cufftExecD2Z(h, i, (cufftDoubleComplex*)o); }
+  static cufftResult c2r(cufftHandle h, double* i, double* o) { return cufftExecZ2D(h, (cufftDoubleComplex*)i, o); }
+  static cufftResult c2c(cufftHandle h, double* i, double* o, int dir) {
+    return cufftExecZ2Z(h, (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, dir);
+  }
+};
+
+}  // namespace
+
+// Steps (ii)-(iv) for D = 2, 1 (adaptive FFT) and D = 0 (padded FFT with the precomputed
+// kernel). grid: C spread components; ugrid: receives the 3 n_rhs inverse-transformed
+// components on the spread grid.
+template <typename T>
+se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC) {
+  const GridGeom& g = p->geom;
+  cudaStream_t st = p->stream;
+  const int D = p->D;
+  const int kidx = kernel == SE_STOKESLET ? 0 : (kernel == SE_STRESSLET ? 1 : 2);
+  if (D == 0) {
+    // 3-D R2C on the 2M' grid, scaled by A^_{R,tr} (Sec. 3.5), C2R
+    const int biharm = kernel != SE_ROTLET;
+    if (!p->atr[biharm].p) return SE_ERR_UNSUPPORTED;  // kernel not in the plan's kernel_mask
+    const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
+    void* spec;
+    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
+    int n[3] = {g.n[0], g.n[1], g.n[2]};
+    cufftHandle hf, hi;
+    SE_TRY(free_fft(p, 1, C, 3, n, nullptr, 1, (int)G, nullptr, 1, (int)H, FT<T>::R2C, &hf));
+    SE_TRY(free_fft(p, 2, NC, 3, n, nullptr, 1, (int)H, nullptr, 1, (int)G, FT<T>::C2R, &hi));
+    SE_CUFFT(FT<T>::r2c(hf, grid, (T*)spec));
+    ScaleTables<T> tb{(const T*)p->ptab[0].p, (const T*)p->ptab[1].p, (const T*)p->ptab[2].p,
+                      (const T*)p->atr[biharm].p};
+    SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
+    SE_CUFFT(FT<T>::c2r(hi, (T*)spec, ugrid));
+    return SE_OK;
+  }
+  const int M0 = g.m[0];
+  if (D == 2) {
+    const int M1 = g.m[1], Mz = g.m[2];
+    const int H1 = M1 / 2 + 1;
+    const size_t G = (size_t)M0 * M1 * Mz;
+    const size_t S = (size_t)M0 * H1 * Mz;  // complex elements per component
+    void* spec;
+    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * S, &spec));
+    // (ii-a) 2-D R2C over (0, 1) for every z, one execution per component
+    int n2[2] = {M0, M1};
+    int in2[2] = {M0, M1}, on2[2] = {M0, H1};
+    cufftHandle h2f, h2i;
+    SE_TRY(free_fft(p, 10, Mz, 2, n2, in2, Mz, 1, on2, Mz, 1, FT<T>::R2C, &h2f));
+    SE_TRY(free_fft(p, 11, Mz, 2, n2, on2, Mz, 1, in2, Mz, 1, FT<T>::C2R, &h2i));
+    for (int c = 0; c < C; ++c) SE_CUFFT(FT<T>::r2c(h2f, grid + (size_t)c * G, (T*)spec + 2 * (size_t)c * S));
+    // class buffers for k^P = 0 and K_*
+    ColMap cm{2, 0, M0, M1, H1, p->kbar_star};
+    const int ncolS = (2 * p->kbar_star + 1) * (p->kbar_star + 1) - 1;
+    const int n0 = p->ncls[0][2], nS = p->ncls[1][2];
+    void *b0, *bS;
+    SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * C * (size_t)n0, &b0));
+    SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * C * (size_t)std::max(ncolS, 1) * nS, &bS));
+    const Ext2 em{{Mz, 0}}, e0{{n0, 0}}, eS{{nS, 0}};
+    cm.mode = 0;
+    k_aft_copy<T><<<grid1d((long long)C * n0, 256), 256, 0, st>>>(cm, C, 1, em, e0, true, (T*)spec, (T*)b0);
+    if (ncolS > 0) {
+      cm.mode = 1;
+      k_aft_copy<T><<<grid1d((long long)C * ncolS * nS, 256), 256, 0, st>>>(cm, C, ncolS, em, eS, true,
+                                                                            (T*)spec, (T*)bS);
+    }
+    // (ii-b) 1-D transforms along direction 2 per class
+    int nz[1] = {Mz}, nz0[1] = {n0}, nzS[1] = {nS};
+    cufftHandle hz, hzi, hz0, hz0i, hzS, hzSi;
+    SE_TRY(free_fft(p, 12, C * M0 * H1, 1, nz, nullptr, 1, Mz, nullptr, 1, Mz, FT<T>::C2C, &hz));
+    SE_TRY(free_fft(p, 13, NC * M0 * H1, 1, nz, nullptr, 1, Mz, nullptr, 1, Mz, FT<T>::C2C, &hzi));
+    SE_TRY(free_fft(p, 14, C, 1, nz0, nullptr, 1, n0, nullptr, 1, n0, FT<T>::C2C, &hz0));
+    SE_TRY(free_fft(p, 15, NC, 1, nz0, nullptr, 1, n0, nullptr, 1, n0, FT<T>::C2C, &hz0i));
+    SE_CUFFT(FT<T>::c2c(hz, (T*)spec, (T*)spec, CUFFT_FORWARD));
+    SE_CUFFT(FT<T>::c2c(hz0, (T*)b0, (T*)b0, CUFFT_FORWARD));
+    if (ncolS > 0) {
+      SE_TRY(free_fft(p, 16, C * ncolS, 1, nzS, nullptr, 1, nS, nullptr, 1, nS, FT<T>::C2C, &hzS));
+      SE_TRY(free_fft(p, 17, NC * ncolS, 1, nzS, nullptr, 1, nS, nullptr, 1, nS, FT<T>::C2C, &hzSi));
+      SE_CUFFT(FT<T>::c2c(hzS, (T*)bS, (T*)bS, CUFFT_FORWARD));
+    }
+    // (iii) scaling per class
+    FreeScale fs;
+    fs.h = g.h;
+    fs.kf0 = 2.0 * M_PI / g.L[0];
+    fs.kf1 = 2.0 * M_PI / g.L[1];
+    fs.inv4xi2 = 1.0 / (4.0 * p->xi * p->xi);
+    const T* tp0 = (const T*)p->ptab[0].p;
+    const T* tp1 = (const T*)p->ptab[1].p;
+    fs.m = cm;
+    fs.m.mode = 2;
+    fs.cls = 2;
+    fs.ncols = M0 * H1;
+    fs.fn[0] = Mz;
+    fs.fn[1] = 1;
+    k_scale_free<T><<<grid1d((long long)M0 * H1 * Mz, 256), 256, 0, st>>>(
+        fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[2][2].p, nullptr, nullptr, nullptr, (T*)spec);
+    fs.m.mode = 0;
+    fs.cls = 0;
+    fs.ncols = 1;
+    fs.fn[0] = n0;
+    k_scale_free<T><<<grid1d(n0, 256), 256, 0, st>>>(fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[0][2].p,
+                                                    nullptr, (const T*)p->mod0[kidx].p, nullptr, (T*)b0);
+    if (ncolS > 0) {
+      fs.m.mode = 1;
+      fs.cls = 1;
+      fs.ncols = ncolS;
+      fs.fn[0] = nS;
+      k_scale_free<T><<<grid1d((long long)ncolS * nS, 256), 256, 0, st>>>(
+          fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[1][2].p, nullptr, nullptr, nullptr, (T*)bS);
+    }
+    // (iv) inverse per class, truncate and merge, inverse over (0, 1)
+    SE_CUFFT(FT<T>::c2c(hzi, (T*)spec, (T*)spec, CUFFT_INVERSE));
+    SE_CUFFT(FT<T>::c2c(hz0i, (T*)b0, (T*)b0, CUFFT_INVERSE));
+    cm.mode = 0;
+    k_aft_copy<T><<<grid1d((long long)NC * n0, 256), 256, 0, st>>>(cm, NC, 1, em, e0, false, (T*)spec, (T*)b0);
+    if (ncolS > 0) {
+      SE_CUFFT(FT<T>::c2c(hzSi, (T*)bS, (T*)bS, CUFFT_INVERSE));
+      cm.mode = 1;
+      k_aft_copy<T><<<grid1d((long long)NC * ncolS * nS, 256), 256, 0, st>>>(cm, NC, ncolS, em, eS, false,
+                                                                             (T*)spec, (T*)bS);
+    }
+    for (int c = 0; c < NC; ++c) SE_CUFFT(FT<T>::c2r(h2i, (T*)spec + 2 * (size_t)c * S, ugrid + (size_t)c * G));
+    SE_CUDA(cudaGetLastError());
+    return SE_OK;
+  }
+  // D = 1: 1-D R2C along direction 0, planes along (1, 2) per class
+  const int My = g.m[1], Mz = g.m[2];
+  const int H0 = M0 / 2 + 1;
+  const size_t PL = (size_t)My * Mz;
+  const size_t G = (size_t)M0 * PL;
+  const size_t S = (size_t)H0 * PL;
+  void* spec;
+  SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * S, &spec));
+  int n1[1] = {M0}, in1[1] = {M0}, on1[1] = {H0};
+  cufftHandle h1f, h1i;
+  SE_TRY(free_fft(p, 20, (int)PL, 1, n1, in1, (int)PL, 1, on1, (int)PL, 1, FT<T>::R2C, &h1f));
+  SE_TRY(free_fft(p, 21, (int)PL, 1, n1, on1, (int)PL, 1, in1, (int)PL, 1, FT<T>::C2R, &h1i));
+  for (int c = 0; c < C; ++c) SE_CUFFT(FT<T>::r2c(h1f, grid + (size_t)c * G, (T*)spec + 2 * (size_t)c * S));
+  ColMap cm{1, 0, M0, 0, H0, std::min(p->kbar_star, H0 - 2)};
+  const int kst = std::max(0, cm.kstar);
+  const int n0y = p->ncls[0][1], n0z = p->ncls[0][2], nSy = p->ncls[1][1], nSz = p->ncls[1][2];
+  void *b0, *bS;
+  SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * C * (size_t)n0y * n0z, &b0));
+  SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * C * (size_t)std::max(kst, 1) * nSy * nSz, &bS));
+  const Ext2 em{{My, Mz}}, e0{{n0y, n0z}}, eS{{nSy, nSz}};
+  cm.mode = 0;
+  k_aft_copy<T><<<grid1d((long long)C * n0y * n0z, 256), 256, 0, st>>>(cm, C, 1, em, e0, true, (T*)spec, (T*)b0);
+  if (kst > 0) {
+    cm.mode = 1;
+    k_aft_copy<T><<<grid1d((long long)C * kst * nSy * nSz, 256), 256, 0, st>>>(cm, C, kst, em, eS, true,
+                                                                               (T*)spec, (T*)bS);
+  }
+  int np[2] = {My, Mz}, np0[2] = {n0y, n0z}, npS[2] = {nSy, nSz};
+  cufftHandle hp, hpi, hp0, hp0i, hpS, hpSi;
+  SE_TRY(free_fft(p, 22, C * H0, 2, np, nullptr, 1, (int)PL, nullptr, 1, (int)PL, FT<T>::C2C, &hp));
+  SE_TRY(free_fft(p, 23, NC * H0, 2, np, nullptr, 1, (int)PL, nullptr, 1, (int)PL, FT<T>::C2C, &hpi));
+  SE_TRY(free_fft(p, 24, C, 2, np0, nullptr, 1, n0y * n0z, nullptr, 1, n0y * n0z, FT<T>::C2C, &hp0));
+  SE_TRY(free_fft(p, 25, NC, 2, np0, nullptr, 1, n0y * n0z, nullptr, 1, n0y * n0z, FT<T>::C2C, &hp0i));
+  SE_CUFFT(FT<T>::c2c(hp, (T*)spec, (T*)spec, CUFFT_FORWARD));
+  SE_CUFFT(FT<T>::c2c(hp0, (T*)b0, (T*)b0, CUFFT_FORWARD));
+  if (kst > 0) {
+    SE_TRY(free_fft(p, 26, C * kst, 2, npS, nullptr, 1, nSy * nSz, nullptr, 1, nSy * nSz, FT<T>::C2C, &hpS));
+    SE_TRY(free_fft(p, 27, NC * kst, 2, npS, nullptr, 1, nSy * nSz, nullptr, 1, nSy * nSz, FT<T>::C2C, &hpSi));
+    SE_CUFFT(FT<T>::c2c(hpS, (T*)bS, (T*)bS, CUFFT_FORWARD));
+  }
+  FreeScale fs;
+  fs.h = g.h;
+  fs.kf0 = 2.0 * M_PI / g.L[0];
+  fs.kf1 = 0;
+  fs.inv4xi2 = 1.0 / (4.0 * p->xi * p->xi);
+  const T* tp0 = (const T*)p->ptab[0].p;
+  fs.m = cm;
+  fs.m.mode = 2;
+  fs.cls = 2;
+  fs.ncols = H0;
+  fs.fn[0] = My;
+  fs.fn[1] = Mz;
+  k_scale_free<T><<<grid1d((long long)H0 * PL, 256), 256, 0, st>>>(
+      fs, kernel, n_rhs, tp0, nullptr, (const T*)p->ftab[2][1].p, (const T*)p->ftab[2][2].p, nullptr, nullptr,
+      (T*)spec);
+  fs.m.mode = 0;
+  fs.cls = 0;
+  fs.ncols = 1;
+  fs.fn[0] = n0y;
+  fs.fn[1] = n0z;
+  const T* modH = (const T*)(kernel == SE_ROTLET ? p->mod0[2].p : p->mod0[0].p);
+  const T* modB = (const T*)(kernel == SE_ROTLET ? nullptr : p->mod0[1].p);
+  k_scale_free<T><<<grid1d((long long)n0y * n0z, 256), 256, 0, st>>>(fs, kernel, n_rhs, tp0, nullptr, nullptr,
+                                                                     nullptr, modH, modB, (T*)b0);
+  if (kst > 0) {
+    fs.m.mode = 1;
+    fs.cls = 1;
+    fs.ncols = kst;
+    fs.fn[0] = nSy;
+    fs.fn[1] = nSz;
+    k_scale_free<T><<<grid1d((long long)kst * nSy * nSz, 256), 256, 0, st>>>(
+        fs, kernel, n_rhs, tp0, nullptr, (const T*)p->ftab[1][1].p, (const T*)p->ftab[1][2].p, nullptr, nullptr,
+        (T*)bS);
+  }
+  SE_CUFFT(FT<T>::c2c(hpi, (T*)spec, (T*)spec, CUFFT_INVERSE));
+  SE_CUFFT(FT<T>::c2c(hp0i, (T*)b0, (T*)b0, CUFFT_INVERSE));
+  cm.mode = 0;
+  k_aft_copy<T><<<grid1d((long long)NC * n0y * n0z, 256), 256, 0, st>>>(cm, NC, 1, em, e0, false, (T*)spec,
+                                                                       (T*)b0);
+  if (kst > 0) {
+    SE_CUFFT(FT<T>::c2c(hpSi, (T*)bS, (T*)bS, CUFFT_INVERSE));
+    cm.mode = 1;
+    k_aft_copy<T><<<grid1d((long long)NC * kst * nSy * nSz, 256), 256, 0, st>>>(cm, NC, kst, em, eS, false,
+                                                                                (T*)spec, (T*)bS);
+  }
+  for (int c = 0; c < NC; ++c) SE_CUFFT(FT<T>::c2r(h1i, (T*)spec + 2 * (size_t)c * S, ugrid + (size_t)c * G));
+  SE_CUDA(cudaGetLastError());
+  return SE_OK;
+}
+
+// Gauge constants of the 0P and 1P stokeslet (Eqs. 0p-stokeslet-extra-contribution and
+// 1p-stokeslet-extra-contribution): 0P adds (2/R) sum f; 1P subtracts
+// diag(4 ln R + 4, 2 ln R + 1, 2 ln R + 1) sum f / L_0.
+template <typename T>
+se_status gauge_correction(se_plan_t* p, const T* f, int n, int n_rhs, int nt, T* u) {
+  if (!((p->D == 0 || p->D == 1) && n > 0 && nt > 0)) return SE_OK;
+  void* sums;
+  SE_TRY(buf(p, "gauge.sums", sizeof(double) * 3 * n_rhs, &sums));
+  SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 3 * n_rhs, p->stream));
+  ++p->launches;
+  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(f, n, n_rhs, (double*)sums);
+  double c[3];
+  if (p->D == 0) {
+    c[0] = c[1] = c[2] = 2.0 / p->R;
+  } else {
+    const double lr = std::log(p->R);
+    c[0] = -(4.0 * lr + 4.0) / p->L[0];
+    c[1] = c[2] = -(2.0 * lr + 1.0) / p->L[0];
+  }
+  ++p->launches;
+  k_add_const<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(nt, n_rhs, (double*)sums, c[0], c[1], c[2], u);
+  SE_CUDA(cudaGetLastError());
+  return SE_OK;
+}
+
+template se_status fourier_free<float>(se_plan_t*, int, int, float*, int, float*, int);
+template se_status fourier_free<double>(se_plan_t*, int, int, double*, int, double*, int);
+template se_status gauge_correction<float>(se_plan_t*, const float*, int, int, int, float*);
+template se_status gauge_correction<double>(se_plan_t*, const double*, int, int, int, double*);
+
+}  // namespace se

@@ -83,8 +83,6 @@ double window_hat(const WindowDesc& w, double k) {
 
 // ------------------------------------------------------------------ error estimates (Sec. 4)
 
-static int kidx(int kernel) { return kernel == SE_STOKESLET ? 0 : (kernel == SE_STRESSLET ? 1 : 2); }
-
 // Potential rms estimate U(L,Q,xi), Eqs. (pot-mag-est-*) with the mean C_U of Table 3.
 double pot_mag(int kernel, double L, double Q, double xi) {
   double t = xi * L;
@@ -139,6 +137,28 @@ double xi_from_rc(int kernel, double L, double Q, double rc, double tau) {
   return solve_tail([&](double xi) { return est_real(kernel, L, Q, xi, rc); }, tau, 0.5 / rc, 20.0 / rc);
 }
 
+// Upsampling of the K_* class and its threshold, Eqs. (upsampling-factor-sstar) and
+// (estimate-kbarstar), with lg = log(U / (2 tau)) / (2 pi). The printed rules are for a cube,
+// where M = L/h is both the free extent of the sources and the periodic length. For a cuboid
+// the two roles are separated: the aperiodic support along a free direction spans
+// M_free = L_free/h grid points, and the slowest-decaying k^P != 0 mode, |k^P| = 2 pi / L_per,
+// needs a further M_per lg points (M_per = the longest periodic side over h), so
+//   s_* = max_free (M_free + M_per lg) / M',   kbar_* = max_free ceil(M_per lg / (M' - M_free) - 1),
+// which reduce to the printed forms when M_free = M_per = M.
+void upsampling_rule(int D, const double* box, double h, const int* Mext, double lg, double* s_star,
+                     int* kbar_star) {
+  double Mper = 0;
+  for (int d = 0; d < D; ++d) Mper = std::max(Mper, box[d] / h);
+  double ss = 1.0, kb = 0;
+  for (int d = D; d < 3; ++d) {
+    const double Mf = box[d] / h;
+    ss = std::max(ss, (Mf + Mper * lg) / Mext[d]);
+    kb = std::max(kb, std::ceil(Mper * lg / (Mext[d] - Mf) - 1.0));
+  }
+  *s_star = ss;
+  *kbar_star = std::max(0, (int)kb);
+}
+
 // Average number of neighbours within rc, Table 5 (uniform system).
 static double nrc_uniform(int kernel, int D) {
   static const double sr[4] = {2500, 950, 450, 400};  // stokeslet, rotlet, D = 0..3
@@ -147,7 +167,7 @@ static double nrc_uniform(int kernel, int D) {
 }
 
 // Box padding factor lambda, Table 4.
-static double lambda_table(int kernel, int D) {
+double lambda_table(int kernel, int D) {
   if (D >= 1) return 2.4;
   return kernel == SE_STOKESLET ? 2.2 : (kernel == SE_STRESSLET ? 2.4 : 1.5);
 }
@@ -275,15 +295,10 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
     if (D > 0) {
       double Umin = 1e300;
       for (int i = 0; i < nk; ++i) Umin = std::min(Umin, pot_mag(kernels[i], L, Q, xi));
-      double lg = std::log(Umin / (2.0 * tau)) / (2.0 * M_PI);
-      double ss = 0, kb = 0;
-      for (int d = D; d < 3; ++d) {
-        double Md = box[d] / h;
-        ss = std::max(ss, Md / Mext[d] * (1.0 + lg));          // Eq. (upsampling-factor-sstar)
-        kb = std::max(kb, std::ceil(Md / (Mext[d] - Md) * lg - 1.0));  // Eq. (estimate-kbarstar)
-      }
-      io->s_star = std::max(1.0, ss);
-      io->kbar_star = std::max(0, (int)kb);
+      double lg = std::max(0.0, std::log(Umin / (2.0 * tau)) / (2.0 * M_PI));
+      int me[3] = {0, 0, 0};
+      for (int d = D; d < 3; ++d) me[d] = (int)Mext[d];
+      upsampling_rule(D, box, h, me, lg, &io->s_star, &io->kbar_star);
     }
   }
   io->f_M = fM;

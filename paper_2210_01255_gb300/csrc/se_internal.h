@@ -91,6 +91,13 @@ struct se_plan_t {
   // device status word (range errors, timeouts)
   int* d_status = nullptr;
 
+  // reduced periodicity (D < 3)
+  int ncls[3][3] = {};     // [class][direction] transform lengths in the free directions
+  se::DevBuf ptab[3];      // periodic-direction factors exp(-k^2/4xi^2) / w^2 / n
+  se::DevBuf ftab[3][3];   // [class][direction] free-direction factors
+  se::DevBuf mod0[3];      // k^P = 0 modified-kernel tables
+  se::DevBuf atr[2];       // D = 0 precomputed kernels: 0 harmonic, 1 biharmonic
+
   se::Timers timers;
   float times_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   int last_grid_comps = 0;
@@ -102,6 +109,25 @@ namespace se {
 
 // buffer helper: returns device pointer with at least `bytes` bytes (grows, never shrinks)
 se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out);
+
+template <typename T>
+struct ScaleTables {
+  const T* g0;
+  const T* g1;
+  const T* g2;
+  const T* atab;  // precomputed scalar per half-spectrum mode (D = 0) or nullptr
+};
+template <typename T>
+se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const ScaleTables<T>& t);
+se_status free_plan_setup(se_plan_t* p);
+template <typename T>
+se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);
+template <typename T>
+se_status gauge_correction(se_plan_t* p, const T* f, int n, int n_rhs, int nt, T* u);
+double pot_mag(int kernel, double L, double Q, double xi);
+double lambda_table(int kernel, int D);
+void upsampling_rule(int D, const double* box, double h, const int* Mext, double lg, double* s_star,
+                     int* kbar_star);
 
 // ---- host-side helpers (se_host.cpp) ----
 double bessel_i0(double x);
