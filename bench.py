@@ -148,6 +148,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -233,6 +234,10 @@ def main():
         work["spread"] += 2.0 * N * P ** 3 * C        # one FMA per tap per component
         work.setdefault("gather", 0.0)
         work["gather"] += 2.0 * N * P ** 3 * 3
+    # real space: pairs within rc for the uniform density of this workload, 60 flops per pair
+    vol = float(np.prod(cfg["box"]))
+    work["real"] = sum(60.0 * N * (N - 1) / vol * 4.0 / 3.0 * math.pi * params[k]["rc"] ** 3
+                       for k in cfg["kernels"])
     dom = max(per_stage, key=per_stage.get)
     roof = None
     pk = peaks()
@@ -240,13 +245,11 @@ def main():
         ach = work[dom] / (per_stage[dom] * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived)"}
-    elif dom == "real":
-        roof = {"bound": "alu", "kernel": "real", "achieved": None, "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": None, "traffic": None}
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (derived, nominal)"}
     else:
         roof = {"bound": "hbm", "kernel": dom, "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                 "frac": None, "traffic": None}
+    roof["per_stage_tflops"] = {k: work[k] / (per_stage[k] * 1e-3) / 1e12 for k in work if per_stage[k] > 0}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
@@ -267,6 +270,36 @@ def main():
         e2e = {"value": targets_per_step * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    # the plain FP64 single-RHS form of the same workload and tolerance (comparison of the metric)
+    fp64 = None
+    if not args.no_fp64:
+        plans64, f64 = {}, {}
+        for k in cfg["kernels"]:
+            t = params[k]
+            plans64[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp64",
+                                 stream=stream)
+            f64[k] = torch.tensor(fs[k].astype(np.float64), device=dev)
+        u64 = {k: torch.empty((1, N, 3), dtype=torch.float64, device=dev) for k in cfg["kernels"]}
+
+        def step64():
+            for k in cfg["kernels"]:
+                plans64[k].evaluate(k, xdev, f64[k], out=u64[k])
+
+        for _ in range(3):
+            step64()
+        torch.cuda.synchronize()
+        n64 = max(3, args.steps // 4)
+        ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
+        for s_ in range(n64):
+            flush.zero_()
+            ev64[s_][0].record(stream)
+            step64()
+            ev64[s_][1].record(stream)
+        torch.cuda.synchronize()
+        t64 = sum(a.elapsed_time(b) for a, b in ev64)
+        fp64 = {"value": targets_per_step * n64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / n64,
+                "form": "FP64, one RHS per evaluation, same parameters"}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -275,7 +308,7 @@ def main():
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "stage_ms_per_step": per_stage, "roofline": roof, "clocks": clocks, "e2e": e2e,
-            "gpu_launches": launches}
+            "gpu_launches": launches, "fp64_plain": fp64}
 
     # ---- CPU baseline (rank 0, N = 1): the oracle on a bounded sample; also the GPU error there
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

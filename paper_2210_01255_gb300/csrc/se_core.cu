@@ -554,6 +554,7 @@ struct RealArgs {
   CellGeom cg;
   T xi, rc2;
   int kernel, n_rhs, nsrc, ntgt;
+  T Lhi[3], Llo[3];                  // box lengths as hi + lo parts (image shifts)
   const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
   const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
   const T* fs;                       // sorted strengths [ns][c * n_rhs]
@@ -651,9 +652,18 @@ constexpr int RS_WARPS = 4;  // warps per CTA
 
 template <typename T>
 struct PairQ {
-  T r0[64], r1[64], r2[64];
   int j[64];
+  int img[64];  // packed image offsets (3 x 8 bits, biased by 128)
 };
+
+// wrap an unwrapped cell index into [0, n) and return the image number
+__device__ __forceinline__ int wrap_cell(int u, int n, int* im) {
+  int k = 0;
+  while (u < 0) { u += n; --k; }
+  while (u >= n) { u -= n; ++k; }
+  *im = k;
+  return u;
+}
 
 template <typename T, int KERNEL, int RMAX>
 __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
@@ -677,8 +687,9 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   const T xi2 = xi * xi;
   const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
   const CellGeom& g = a.cg;
-  // column pruning in the working precision with a margin (only decides what to visit)
-  const T cs0 = (T)(g.L[0] / g.nc[0]), cs1 = (T)(g.L[1] / g.nc[1]), cs2 = (T)(g.L[2] / g.nc[2]);
+  // candidate pre-test on the hi parts with a slightly larger radius; the exact test runs
+  // on the hi + lo separation when the pair is evaluated
+  const T cs0 = a.Lhi[0] / T(g.nc[0]), cs1 = a.Lhi[1] / T(g.nc[1]), cs2 = a.Lhi[2] / T(g.nc[2]);
   const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);
   const T tx = xt.x, ty = xt.y, tz = xt.z;
   int qn = 0;
@@ -686,37 +697,48 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   auto flush = [&](int cnt) {
     __syncwarp();
     if (lane < cnt) {
-      const T r0 = q.r0[lane], r1 = q.r1[lane], r2 = q.r2[lane];
-      real_pair<T, KERNEL, RMAX>(r0, r1, r2, r0 * r0 + r1 * r1 + r2 * r2, xi, xi2, c2pi,
-                                 a.fs + (size_t)q.j[lane] * C, a.n_rhs, acc);
+      const int j = q.j[lane], pk = q.img[lane];
+      const T i0 = T((pk & 255) - 128), i1 = T(((pk >> 8) & 255) - 128), i2 = T(((pk >> 16) & 255) - 128);
+      const V4 xs = a.xs[j];
+      T r0, r1, r2;
+      if (sizeof(T) == 4) {
+        // r = x_target - (x_source + p): hi + lo parts, x_source_hi + shift split exactly
+        const V4 xl = a.xsl[j];
+        const T shx = i0 * a.Lhi[0], shy = i1 * a.Lhi[1], shz = i2 * a.Lhi[2];
+        const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
+        const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
+        r0 = (xt.x - ax) + ((xtl.x - xl.x) - (i0 * a.Llo[0] + ex));
+        r1 = (xt.y - ay) + ((xtl.y - xl.y) - (i1 * a.Llo[1] + ey));
+        r2 = (xt.z - az) + ((xtl.z - xl.z) - (i2 * a.Llo[2] + ez));
+      } else {
+        r0 = xt.x - (xs.x + i0 * a.Lhi[0]);
+        r1 = xt.y - (xs.y + i1 * a.Lhi[1]);
+        r2 = xt.z - (xs.z + i2 * a.Lhi[2]);
+      }
+      const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
+      if (rr2 < a.rc2)
+        real_pair<T, KERNEL, RMAX>(r0, r1, r2, rr2, xi, xi2, c2pi, a.fs + (size_t)j * C, a.n_rhs, acc);
     }
     __syncwarp();
   };
   for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
-    int ux = cx + dx;
-    double shx_d = 0;
-    if (g.periodic[0]) {
-      int im = fdiv(ux, g.nc[0]);
-      ux -= im * g.nc[0];
-      shx_d = im * g.L[0];
-    } else if (ux < 0 || ux >= g.nc[0]) continue;
-    // distance from the target to the slab of cells ux (in its image) along direction 0
-    const T x0 = (T)(cx + dx) * cs0, x1 = x0 + cs0;  // unwrapped cell = image position
+    int imx = 0, ux = cx + dx;
+    if (g.periodic[0]) ux = wrap_cell(ux, g.nc[0], &imx);
+    else if (ux < 0 || ux >= g.nc[0]) continue;
+    // distance from the target to the slab of this image of cell ux along direction 0
+    const T x0 = T(cx + dx) * cs0, x1 = x0 + cs0;
     const T ddx = tx < x0 ? x0 - tx : (tx > x1 ? tx - x1 : T(0));
     if (ddx * ddx >= rcp2) continue;
-    const T shx = (T)shx_d, shxl = (T)(shx_d - (double)shx);
+    const T shx = T(imx) * a.Lhi[0];
     for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
-      int uy = cy + dy;
-      double shy_d = 0;
-      if (g.periodic[1]) {
-        int im = fdiv(uy, g.nc[1]);
-        uy -= im * g.nc[1];
-        shy_d = im * g.L[1];
-      } else if (uy < 0 || uy >= g.nc[1]) continue;
-      const T y0 = (T)(cy + dy) * cs1, y1 = y0 + cs1;
+      int imy = 0, uy = cy + dy;
+      if (g.periodic[1]) uy = wrap_cell(uy, g.nc[1], &imy);
+      else if (uy < 0 || uy >= g.nc[1]) continue;
+      const T y0 = T(cy + dy) * cs1, y1 = y0 + cs1;
       const T ddy = ty < y0 ? y0 - ty : (ty > y1 ? ty - y1 : T(0));
       const T rem = rcp2 - ddx * ddx - ddy * ddy;
       if (rem <= T(0)) continue;
+      const T shy = T(imy) * a.Lhi[1];
       // cells along direction 2 that can hold sources within rc: |z - tz| < sqrt(rem)
       const T zr = sqrt(rem);
       int zlo = (int)floor((tz - zr) / cs2), zend = (int)floor((tz + zr) / cs2);
@@ -726,58 +748,40 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
         zlo = max(zlo, 0);
         zend = min(zend, g.nc[2] - 1);
       }
-      const T shy = (T)shy_d, shyl = (T)(shy_d - (double)shy);
       const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
       while (zlo <= zend) {
-        const int im = g.periodic[2] ? fdiv(zlo, g.nc[2]) : 0;
-        const int seg_end = g.periodic[2] ? min(zend, (im + 1) * g.nc[2] - 1) : zend;
-        const int w0 = zlo - im * g.nc[2], w1 = seg_end - im * g.nc[2];
-        const double shz_d = im * g.L[2];
-        const T shz = (T)shz_d, shzl = (T)(shz_d - (double)shz);
+        int imz = 0, w0 = zlo;
+        if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
+        const int w1 = min(g.nc[2] - 1, w0 + (zend - zlo));  // up to the end of this image
+        const T shz = T(imz) * a.Lhi[2];
+        const int pk = (imx + 128) | ((imy + 128) << 8) | ((imz + 128) << 16);
         const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
         for (int jb = beg; jb < end; jb += 32) {
           const int j = jb + lane;
           bool in = false;
-          T r0 = 0, r1 = 0, r2 = 0;
           if (j < end) {
             const V4 xs = a.xs[j];
-            if (sizeof(T) == 4) {
-              // hi + lo separation; x_source_hi + shift split exactly (Fast2Sum)
-              const V4 xl = a.xsl[j];
-              const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
-              const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
-              r0 = (xt.x - ax) + ((xtl.x - xl.x) - (shxl + ex));
-              r1 = (xt.y - ay) + ((xtl.y - xl.y) - (shyl + ey));
-              r2 = (xt.z - az) + ((xtl.z - xl.z) - (shzl + ez));
-            } else {
-              r0 = xt.x - (xs.x + shx);
-              r1 = xt.y - (xs.y + shy);
-              r2 = xt.z - (xs.z + shz);
-            }
-            in = r0 * r0 + r1 * r1 + r2 * r2 < a.rc2;
+            const T r0 = xt.x - (xs.x + shx), r1 = xt.y - (xs.y + shy), r2 = xt.z - (xs.z + shz);
+            in = r0 * r0 + r1 * r1 + r2 * r2 < rcp2;
           }
           const unsigned bal = __ballot_sync(0xffffffffu, in);
           if (in) {
             const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-            q.r0[pos] = r0;
-            q.r1[pos] = r1;
-            q.r2[pos] = r2;
             q.j[pos] = j;
+            q.img[pos] = pk;
           }
           qn += __popc(bal);
           if (qn >= 32) {
             flush(32);
             qn -= 32;
-            if (lane < qn) {  // move the overflow (entries 32..qn+31) to the front
-              q.r0[lane] = q.r0[32 + lane];
-              q.r1[lane] = q.r1[32 + lane];
-              q.r2[lane] = q.r2[32 + lane];
+            if (lane < qn) {  // move the overflow (entries 32 .. qn+31) to the front
               q.j[lane] = q.j[32 + lane];
+              q.img[lane] = q.img[32 + lane];
             }
             __syncwarp();
           }
         }
-        zlo = seg_end + 1;
+        zlo += w1 - w0 + 1;
       }
     }
   }
@@ -1402,6 +1406,10 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     if ((parts & SE_PART_REAL) && NT > 0) {
       RealArgs<T> ra;
       ra.cg = cg;
+      for (int d = 0; d < 3; ++d) {
+        ra.Lhi[d] = (T)p->L[d];
+        ra.Llo[d] = (T)(p->L[d] - (double)ra.Lhi[d]);
+      }
       ra.xi = (T)p->xi;
       ra.rc2 = (T)(p->rc * p->rc);
       ra.kernel = kernel;
@@ -1596,6 +1604,10 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, f, perm, N, 1, fs);
   RealArgs<T> ra;
   ra.cg = cg;
+  for (int d = 0; d < 3; ++d) {
+    ra.Lhi[d] = (T)box[d];
+    ra.Llo[d] = (T)(box[d] - (double)ra.Lhi[d]);
+  }
   ra.xi = (T)xi;
   ra.rc2 = (T)(rc * rc);
   ra.kernel = kernel;
