@@ -12,6 +12,7 @@
 #include <new>
 
 #include "se_device.cuh"
+#include "se_erfc_fit.h"
 
 namespace se {
 
@@ -132,8 +133,9 @@ __global__ void k_scatter_perm(const int* __restrict__ key, const int* __restric
 }
 
 // counting sort by key; returns perm (sorted -> original) and start[nk+1]
-static se_status counting_sort(se_plan_t* p, const char* tag, int n, int nk,
-                               void (*keyfun)(se_plan_t*, const double*, int, int*, int*, int*, const void*),
+static se_status counting_sort(se_plan_t* p, cudaStream_t st, const char* tag, int n, int nk,
+                               void (*keyfun)(se_plan_t*, cudaStream_t, const double*, int, int*, int*, int*,
+                                              const void*),
                                const double* x, const void* geom, int** perm_out, int** start_out) {
   std::string t(tag);
   void *key, *rank, *count, *start, *perm;
@@ -142,14 +144,13 @@ static se_status counting_sort(se_plan_t* p, const char* tag, int n, int nk,
   SE_TRY(buf(p, (t + ".count").c_str(), sizeof(int) * (size_t)nk, &count));
   SE_TRY(buf(p, (t + ".start").c_str(), sizeof(int) * (size_t)(nk + 1), &start));
   SE_TRY(buf(p, (t + ".perm").c_str(), sizeof(int) * (size_t)n, &perm));
-  SE_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)nk, p->stream));
-  if (n > 0) keyfun(p, x, n, (int*)key, (int*)rank, (int*)count, geom);
+  SE_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)nk, st));
+  if (n > 0) keyfun(p, st, x, n, (int*)key, (int*)rank, (int*)count, geom);
   ++p->launches;
-  k_scan<<<1, 1024, 0, p->stream>>>((int*)count, (int*)start, nk);
+  k_scan<<<1, 1024, 0, st>>>((int*)count, (int*)start, nk);
   if (n > 0) {
     ++p->launches;
-    k_scatter_perm<<<grid1d(n, 256), 256, 0, p->stream>>>((int*)key, (int*)rank, (int*)start, n,
-                                                           (int*)perm);
+    k_scatter_perm<<<grid1d(n, 256), 256, 0, st>>>((int*)key, (int*)rank, (int*)start, n, (int*)perm);
   }
   SE_CUDA(cudaGetLastError());
   *perm_out = (int*)perm;
@@ -157,17 +158,15 @@ static se_status counting_sort(se_plan_t* p, const char* tag, int n, int nk,
   return SE_OK;
 }
 
-static void tile_keyfun(se_plan_t* p, const double* x, int n, int* key, int* rank, int* count,
+static void tile_keyfun(se_plan_t* p, cudaStream_t st, const double* x, int n, int* key, int* rank, int* count,
                         const void* geom) {
   ++p->launches;
-  k_tile_keys<<<grid1d(n, 256), 256, 0, p->stream>>>(*(const GridGeom*)geom, x, n, key, rank, count,
-                                                     p->d_status);
+  k_tile_keys<<<grid1d(n, 256), 256, 0, st>>>(*(const GridGeom*)geom, x, n, key, rank, count, p->d_status);
 }
-static void cell_keyfun(se_plan_t* p, const double* x, int n, int* key, int* rank, int* count,
+static void cell_keyfun(se_plan_t* p, cudaStream_t st, const double* x, int n, int* key, int* rank, int* count,
                         const void* geom) {
   ++p->launches;
-  k_cell_keys<<<grid1d(n, 256), 256, 0, p->stream>>>(*(const CellGeom*)geom, x, n, key, rank, count,
-                                                     p->d_status);
+  k_cell_keys<<<grid1d(n, 256), 256, 0, st>>>(*(const CellGeom*)geom, x, n, key, rank, count, p->d_status);
 }
 
 // ================================================================ window weights (Sec. 3.3)
@@ -494,34 +493,42 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
                                                 const T* __restrict__ F, int nt, int NC, T scale,
                                                 T* __restrict__ u) {
   __shared__ T s_w[8][3 * MAX_P];
+  __shared__ int s_xo[8][MAX_P];  // wrapped direction-0 plane offsets of the P taps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * 8 + warp;
   if (s >= nt) return;
   const int P = g.P;
+  const int n12 = g.n[1] * g.n[2];
   for (int i = lane; i < 3 * P; i += 32) s_w[warp][i] = wts[(size_t)s * 3 * P + i];
   const int b0 = base[3 * s], b1 = base[3 * s + 1], b2 = base[3 * s + 2];
+  if (lane < P) {
+    int xx = b0 + lane;
+    if (g.periodic[0]) { if (xx < 0) xx += g.m[0]; else if (xx >= g.m[0]) xx -= g.m[0]; }
+    s_xo[warp][lane] = xx * n12;
+  }
   __syncwarp();
   T acc[NCMAX];
 #pragma unroll
   for (int c = 0; c < NCMAX; ++c) acc[c] = T(0);
-  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+  const int G = g.n[0] * n12;  // grid points per component (< 2^31, checked at plan creation)
   const T* w0 = s_w[warp];
   const T* w1 = s_w[warp] + P;
   const T* w2 = s_w[warp] + 2 * P;
+  const int* xo = s_xo[warp];
   for (int l = lane; l < P * P; l += 32) {
     const int b = l / P, c = l - b * P;
     int y = b1 + b, z = b2 + c;
     if (g.periodic[1]) { if (y < 0) y += g.m[1]; else if (y >= g.m[1]) y -= g.m[1]; }
     if (g.periodic[2]) { if (z < 0) z += g.m[2]; else if (z >= g.m[2]) z -= g.m[2]; }
     const T wyz = w1[b] * w2[c];
+    const T* Fyz = F + (y * g.n[2] + z);
+#pragma unroll 4
     for (int a = 0; a < P; ++a) {
-      int xx = b0 + a;
-      if (g.periodic[0]) { if (xx < 0) xx += g.m[0]; else if (xx >= g.m[0]) xx -= g.m[0]; }
-      const size_t off = ((size_t)xx * g.n[1] + y) * g.n[2] + z;
+      const T* Fp = Fyz + xo[a];
       const T wv = w0[a] * wyz;
 #pragma unroll
       for (int k = 0; k < NCMAX; ++k)
-        if (k < NC) acc[k] += wv * F[k * G + off];
+        if (k < NC) acc[k] += wv * Fp[(size_t)k * G];
     }
   }
 #pragma unroll
@@ -534,10 +541,9 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
   }
   if (lane == 0) {
     const int i = perm ? perm[s] : s;
-    for (int k = 0; k < NC; ++k) {
-      const int r = k / 3, j = k - 3 * r;
-      u[((size_t)r * nt + i) * 3 + j] = scale * acc[k];
-    }
+#pragma unroll
+    for (int k = 0; k < NCMAX; ++k)
+      if (k < NC) u[((size_t)(k / 3) * nt + i) * 3 + k % 3] = scale * acc[k];
   }
 }
 
@@ -555,6 +561,7 @@ struct RealArgs {
   T xi, rc2;
   int kernel, n_rhs, nsrc, ntgt;
   T Lhi[3], Llo[3];                  // box lengths as hi + lo parts (image shifts)
+  int overwrite;                     // 1: u = sum, 0: u += sum
   const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
   const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
   const T* fs;                       // sorted strengths [ns][c * n_rhs]
@@ -566,10 +573,27 @@ struct RealArgs {
   T* u;
 };
 
+// erfc(x), x >= 0, given g = exp(-x^2) (computed anyway for the Gaussian terms).
+// FP32: erfc(x) = g t R(t), t = 1 / (1 + a x), R the degree-10 polynomial of se_erfc_fit.h
+// (relative error of the fit < 1e-8; a few FP32 ulp after rounding). FP64: the library erfc.
 template <typename T>
-__device__ inline T dev_erfc(T x);
-template <> __device__ inline float dev_erfc<float>(float x) { return erfcf(x); }
-template <> __device__ inline double dev_erfc<double>(double x) { return erfc(x); }
+__device__ inline T dev_erfc_g(T x, T g);
+template <> __device__ __forceinline__ float dev_erfc_g<float>(float x, float g) {
+  const float t = __frcp_rn(fmaf(float(SE_ERFC_FIT_A), x, 1.0f));
+  float r = float(SE_ERFC_FIT_C10);
+  r = fmaf(r, t, float(SE_ERFC_FIT_C9));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C8));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C7));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C6));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C5));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C4));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C3));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C2));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C1));
+  r = fmaf(r, t, float(SE_ERFC_FIT_C0));
+  return g * (t * r);
+}
+template <> __device__ __forceinline__ double dev_erfc_g<double>(double x, double) { return erfc(x); }
 
 // One pair (target, source image): accumulate G^R(r) . f into acc, or the self term when
 // the separation is exactly zero (the omitted n = m, p = 0 term of the star sum).
@@ -590,7 +614,7 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   const T rn = rr2 * inv;
   const T inv2 = inv * inv;
   const T e = exp(-xi2 * rr2);
-  const T ec = dev_erfc(xi * rn) * inv;
+  const T ec = dev_erfc_g(xi * rn, e) * inv;
   if (KERNEL == SE_STOKESLET) {
     // Eq. (stokeslet-real): (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e/sqrt pi
     const T c1 = ec + c2pi * e;
@@ -796,7 +820,10 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   if (lane == 0) {
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-      for (int qq = 0; qq < 3; ++qq) a.u[((size_t)r * a.ntgt + i) * 3 + qq] += acc[3 * r + qq];
+      for (int qq = 0; qq < 3; ++qq) {
+        T* o = a.u + ((size_t)r * a.ntgt + i) * 3 + qq;
+        *o = a.overwrite ? acc[3 * r + qq] : *o + acc[3 * r + qq];
+      }
   }
 }
 
@@ -923,8 +950,11 @@ static void free_plan(se_plan_t* p) {
     if (p->atr[i].p) cudaFree(p->atr[i].p);
   if (p->d_status) cudaFree(p->d_status);
   if (p->pin) cudaFreeHost(p->pin);
-  for (int i = 0; i < 10; ++i)
+  for (int i = 0; i < 12; ++i)
     if (p->timers.ev[i]) cudaEventDestroy(p->timers.ev[i]);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->side) cudaStreamDestroy(p->side);
   delete p;
 }
 
@@ -1038,6 +1068,10 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
     }
     g.ntile[d] = cdiv(g.m[d], TS);
   }
+  if ((double)g.n[0] * g.n[1] * g.n[2] >= 2147483647.0) {  // grid offsets are 32-bit per component
+    free_plan(p);
+    return SE_ERR_UNSUPPORTED;
+  }
   if (D < 3) {
     // truncation radius, Eq. (truncation-radius), and upsampling, Sec. 4.5
     double R2 = 0, minLe = 1e300;
@@ -1086,7 +1120,10 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
     free_plan(p);
     return st;
   }
-  for (int i = 0; i < 10; ++i) cudaEventCreate(&p->timers.ev[i]);
+  for (int i = 0; i < 12; ++i) cudaEventCreate(&p->timers.ev[i]);
+  cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+  cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
   *out = p;
   return SE_OK;
 }
@@ -1119,6 +1156,11 @@ extern "C" se_status se_get_info(se_plan_h p, se_info* info) {
       float ms = 0;
       cudaEventElapsedTime(&ms, p->timers.ev[i], p->timers.ev[i + 1]);
       p->times_ms[i] = ms;
+    }
+    if (p->real_timed) {  // the real-space kernel itself, timed on the side stream
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, p->timers.ev[10], p->timers.ev[11]) == cudaSuccess) p->times_ms[6] = ms;
+      cudaGetLastError();
     }
     p->timed_pending = false;
   }
@@ -1238,15 +1280,22 @@ void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, c
 }
 
 template <typename T, int K, int R>
-void real_launch_k(se_plan_t* p, const RealArgs<T>& a) {
+void real_launch_k(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
   ++p->launches;
-  k_real<T, K, R><<<grid1d(a.ntgt, RS_WARPS), 32 * RS_WARPS, 0, p->stream>>>(a);
+  k_real<T, K, R><<<grid1d(a.ntgt, RS_WARPS), 32 * RS_WARPS, 0, st>>>(a);
 }
 template <typename T, int R>
-void real_launch(se_plan_t* p, const RealArgs<T>& a) {
-  if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, a);
-  else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, a);
-  else real_launch_k<T, SE_STRESSLET, R>(p, a);
+void real_launch(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
+  if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, st, a);
+  else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, st, a);
+  else real_launch_k<T, SE_STRESSLET, R>(p, st, a);
+}
+
+// u += v elementwise (join of the real-space part computed on the side stream)
+template <typename T>
+__global__ void k_axpy1(size_t n, const T* __restrict__ v, T* __restrict__ u) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) u[i] += v[i];
 }
 
 template <typename T>
@@ -1268,11 +1317,106 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
 
   if (!(parts & SE_PART_FOURIER)) SE_CUDA(cudaMemsetAsync(u, 0, sizeof(T) * (size_t)NC * NT, st));
 
+  // ---------------- real-space part: on the side stream, concurrent with the Fourier part,
+  // into its own buffer, joined below (or on the main stream when there is no Fourier part)
+  const bool overlap = (parts & SE_PART_REAL) && (parts & SE_PART_FOURIER) && NT > 0 && p->side;
+  cudaStream_t rs = overlap ? p->side : st;
+  T* ureal = nullptr;
+  if (overlap) {
+    void* ub;
+    SE_TRY(buf(p, "ureal", sizeof(T) * (size_t)NC * NT, &ub));
+    ureal = (T*)ub;
+    SE_CUDA(cudaEventRecord(p->ev_fork, st));
+    SE_CUDA(cudaStreamWaitEvent(rs, p->ev_fork, 0));
+  }
+  // ---------------- real-space part
+  if (parts & (SE_PART_REAL | SE_PART_CORR)) {
+    CellGeom cg;
+    const int S = 2;
+    for (int d = 0; d < 3; ++d) {
+      int nc = (int)std::floor(S * p->L[d] / p->rc);
+      nc = std::max(1, std::min(nc, 128));
+      cg.nc[d] = nc;
+      double cs = p->L[d] / nc;
+      cg.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
+      cg.periodic[d] = d < p->D;
+      cg.L[d] = p->L[d];
+      cg.inv_cs[d] = 1.0 / cs;
+    }
+    const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
+    int *sperm, *cstart;
+    SE_TRY(counting_sort(p, rs, "cell", N, ncell, cell_keyfun, src, &cg, &sperm, &cstart));
+    typedef typename Vec4<T>::type V4;
+    void *xs, *fs, *xsl;
+    SE_TRY(buf(p, "rs.xs", sizeof(V4) * (size_t)std::max(N, 1), &xs));
+    SE_TRY(buf(p, "rs.xsl", sizeof(V4) * (size_t)std::max(N, 1), &xsl));
+    SE_TRY(buf(p, "rs.fs", sizeof(T) * C * (size_t)std::max(N, 1), &fs));
+    void* tcell;
+    SE_TRY(buf(p, "rs.tcell", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcell));
+    if (N > 0) {
+      ++p->launches;
+      k_sort_positions<T><<<grid1d(N, 256), 256, 0, rs>>>(cg, src, sperm, N, (V4*)xs, (V4*)xsl,
+                                                          star ? (int*)tcell : nullptr, p->d_status);
+      ++p->launches;
+      k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, rs>>>(kernel, strengths, sperm, N, n_rhs, (T*)fs);
+    }
+    const V4* xt = (V4*)xs;
+    const V4* xtl = (V4*)xsl;
+    const int* tperm = sperm;
+    if (!star) {
+      int *tp2, *ts2;
+      SE_TRY(counting_sort(p, rs, "tcellsort", NT, ncell, cell_keyfun, tgt, &cg, &tp2, &ts2));
+      void *xt2, *xtl2;
+      SE_TRY(buf(p, "rs.xt", sizeof(V4) * (size_t)std::max(NT, 1), &xt2));
+      SE_TRY(buf(p, "rs.xtl", sizeof(V4) * (size_t)std::max(NT, 1), &xtl2));
+      if (NT > 0) {
+        ++p->launches;
+        k_sort_positions<T><<<grid1d(NT, 256), 256, 0, rs>>>(cg, tgt, tp2, NT, (V4*)xt2, (V4*)xtl2,
+                                                             (int*)tcell, p->d_status);
+      }
+      xt = (V4*)xt2;
+      xtl = (V4*)xtl2;
+      tperm = tp2;
+    }
+    if ((parts & SE_PART_REAL) && NT > 0) {
+      RealArgs<T> ra;
+      ra.cg = cg;
+      for (int d = 0; d < 3; ++d) {
+        ra.Lhi[d] = (T)p->L[d];
+        ra.Llo[d] = (T)(p->L[d] - (double)ra.Lhi[d]);
+      }
+      ra.xi = (T)p->xi;
+      ra.rc2 = (T)(p->rc * p->rc);
+      ra.kernel = kernel;
+      ra.n_rhs = n_rhs;
+      ra.nsrc = N;
+      ra.ntgt = NT;
+      ra.xs = (V4*)xs;
+      ra.xsl = (V4*)xsl;
+      ra.xtl = xtl;
+      ra.fs = (T*)fs;
+      ra.cstart = cstart;
+      ra.xt = xt;
+      ra.tperm = tperm;
+      ra.tcell = (int*)tcell;
+      ra.u = overlap ? ureal : u;
+      ra.overwrite = overlap ? 1 : 0;
+      if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
+      if (n_rhs <= 1) real_launch<T, 1>(p, rs, ra);
+      else if (n_rhs <= 4) real_launch<T, 4>(p, rs, ra);
+      else if (n_rhs <= 8) real_launch<T, 8>(p, rs, ra);
+      else real_launch<T, 16>(p, rs, ra);
+      if (p->timers.on) cudaEventRecord(p->timers.ev[11], rs);
+      SE_CUDA(cudaGetLastError());
+    }
+  }
+  if (overlap) SE_CUDA(cudaEventRecord(p->ev_join, rs));
+
   // ---------------- Fourier-space part (Alg. 1)
   if (parts & SE_PART_FOURIER) {
     const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     int *perm, *tstart;
-    SE_TRY(counting_sort(p, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart));
+    SE_TRY(counting_sort(p, st, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart));
     void *base, *wts, *sf;
     SE_TRY(buf(p, "base", sizeof(int) * 3 * (size_t)std::max(N, 1), &base));
     SE_TRY(buf(p, "wts", sizeof(T) * 3 * g.P * (size_t)std::max(N, 1), &wts));
@@ -1327,7 +1471,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     const T* tw = (T*)wts;
     if (!star) {
       int *perm2, *tstart2;
-      SE_TRY(counting_sort(p, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2));
+      SE_TRY(counting_sort(p, st, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2));
       void *base2, *wts2;
       SE_TRY(buf(p, "tbase", sizeof(int) * 3 * (size_t)std::max(NT, 1), &base2));
       SE_TRY(buf(p, "twts", sizeof(T) * 3 * g.P * (size_t)std::max(NT, 1), &wts2));
@@ -1354,85 +1498,14 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     for (int i = 0; i < 6; ++i) stage.mark();
   }
 
-  // ---------------- real-space part
-  if (parts & (SE_PART_REAL | SE_PART_CORR)) {
-    CellGeom cg;
-    const int S = 2;
-    for (int d = 0; d < 3; ++d) {
-      int nc = (int)std::floor(S * p->L[d] / p->rc);
-      nc = std::max(1, std::min(nc, 128));
-      cg.nc[d] = nc;
-      double cs = p->L[d] / nc;
-      cg.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
-      cg.periodic[d] = d < p->D;
-      cg.L[d] = p->L[d];
-      cg.inv_cs[d] = 1.0 / cs;
-    }
-    const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
-    int *sperm, *cstart;
-    SE_TRY(counting_sort(p, "cell", N, ncell, cell_keyfun, src, &cg, &sperm, &cstart));
-    typedef typename Vec4<T>::type V4;
-    void *xs, *fs, *xsl;
-    SE_TRY(buf(p, "rs.xs", sizeof(V4) * (size_t)std::max(N, 1), &xs));
-    SE_TRY(buf(p, "rs.xsl", sizeof(V4) * (size_t)std::max(N, 1), &xsl));
-    SE_TRY(buf(p, "rs.fs", sizeof(T) * C * (size_t)std::max(N, 1), &fs));
-    void* tcell;
-    SE_TRY(buf(p, "rs.tcell", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcell));
-    if (N > 0) {
-      ++p->launches;
-      k_sort_positions<T><<<grid1d(N, 256), 256, 0, st>>>(cg, src, sperm, N, (V4*)xs, (V4*)xsl,
-                                                          star ? (int*)tcell : nullptr, p->d_status);
-      ++p->launches;
-      k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, strengths, sperm, N, n_rhs, (T*)fs);
-    }
-    const V4* xt = (V4*)xs;
-    const V4* xtl = (V4*)xsl;
-    const int* tperm = sperm;
-    if (!star) {
-      int *tp2, *ts2;
-      SE_TRY(counting_sort(p, "tcellsort", NT, ncell, cell_keyfun, tgt, &cg, &tp2, &ts2));
-      void *xt2, *xtl2;
-      SE_TRY(buf(p, "rs.xt", sizeof(V4) * (size_t)std::max(NT, 1), &xt2));
-      SE_TRY(buf(p, "rs.xtl", sizeof(V4) * (size_t)std::max(NT, 1), &xtl2));
-      if (NT > 0) {
-        ++p->launches;
-        k_sort_positions<T><<<grid1d(NT, 256), 256, 0, st>>>(cg, tgt, tp2, NT, (V4*)xt2, (V4*)xtl2,
-                                                             (int*)tcell, p->d_status);
-      }
-      xt = (V4*)xt2;
-      xtl = (V4*)xtl2;
-      tperm = tp2;
-    }
-    if ((parts & SE_PART_REAL) && NT > 0) {
-      RealArgs<T> ra;
-      ra.cg = cg;
-      for (int d = 0; d < 3; ++d) {
-        ra.Lhi[d] = (T)p->L[d];
-        ra.Llo[d] = (T)(p->L[d] - (double)ra.Lhi[d]);
-      }
-      ra.xi = (T)p->xi;
-      ra.rc2 = (T)(p->rc * p->rc);
-      ra.kernel = kernel;
-      ra.n_rhs = n_rhs;
-      ra.nsrc = N;
-      ra.ntgt = NT;
-      ra.xs = (V4*)xs;
-      ra.xsl = (V4*)xsl;
-      ra.xtl = xtl;
-      ra.fs = (T*)fs;
-      ra.cstart = cstart;
-      ra.xt = xt;
-      ra.tperm = tperm;
-      ra.tcell = (int*)tcell;
-      ra.u = u;
-      if (n_rhs <= 1) real_launch<T, 1>(p, ra);
-      else if (n_rhs <= 4) real_launch<T, 4>(p, ra);
-      else if (n_rhs <= 8) real_launch<T, 8>(p, ra);
-      else real_launch<T, 16>(p, ra);
-      SE_CUDA(cudaGetLastError());
-    }
+  if (overlap) {
+    SE_CUDA(cudaStreamWaitEvent(st, p->ev_join, 0));
+    const size_t nu = (size_t)NC * NT;
+    ++p->launches;
+    k_axpy1<T><<<grid1d((long long)nu, 256), 256, 0, st>>>(nu, ureal, u);
+    SE_CUDA(cudaGetLastError());
   }
-  stage.mark();  // 7: real
+  stage.mark();  // 7: real (join)
 
   // ---------------- corrections (self term lives in the real-space pair loop)
   if ((parts & SE_PART_CORR) && p->D == 3 && kernel == SE_STRESSLET && N > 0 && NT > 0) {
@@ -1452,6 +1525,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     SE_TRY(gauge_correction<T>(p, strengths, N, n_rhs, NT, u));
   stage.mark();  // 8: corrections
   p->timed_pending = p->timers.on;
+  p->real_timed = p->timers.on && (parts & SE_PART_REAL) && NT > 0;
   return SE_OK;
 }
 
@@ -1623,6 +1697,7 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   ra.tperm = perm;
   ra.tcell = tcell;
   ra.u = u;
+  ra.overwrite = 0;
   const int grid = grid1d(N, RS_WARPS);
   if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
   else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);

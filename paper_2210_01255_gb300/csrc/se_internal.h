@@ -50,7 +50,7 @@ struct DevBuf {
 };
 
 struct Timers {
-  cudaEvent_t ev[10] = {};
+  cudaEvent_t ev[12] = {};
   bool on = false;
 };
 
@@ -102,6 +102,10 @@ struct se_plan_t {
   float times_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
   int last_grid_comps = 0;
   bool timed_pending = false;
+  bool real_timed = false;
+  // side stream for the real-space part (forked from and joined to the plan's stream)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int launches = 0;  // kernels launched by the last evaluation
 };
 
