@@ -77,8 +77,15 @@ typedef struct {
   double Q;          /* source quantity Q of Eqs. (vector/tensor-source-quantity) for the rules (0 = 1) */
   int kernel_mask;   /* kernels the plan will be used with (for the free-direction rules); 0 = all */
   void* stream;      /* cudaStream_t to issue work on; NULL = the legacy default stream   */
-  int flags;         /* reserved, 0                                                         */
+  int flags;         /* SE_FLAG_* bits, 0 = defaults                                        */
 } se_opts;
+
+/* se_opts.flags: with SE_FLAG_TC_GRIDDING, FP32 gridding (Alg. 1, gridding step) with window
+ * support P <= 16 runs on the tensor cores (tcgen05.mma kind::tf32, operands split into high
+ * and low TF32 parts for FP32 accuracy; same results as the CUDA-core gridding to FP32
+ * rounding). Without it (default), and always for FP64 or P > 16, gridding runs on the CUDA
+ * cores. */
+enum { SE_FLAG_TC_GRIDDING = 1 };
 
 /* Fill *opts with the defaults above. */
 se_status se_opts_default(se_opts* opts);

@@ -269,43 +269,6 @@ __global__ void k_sort_strengths(int kernel, const T* __restrict__ f, const int*
 // direction 0 and accumulates all components in registers over the points of the tiles
 // whose windows reach the tile. No atomics; each grid value is written once.
 
-constexpr int SP_CHUNK = 64;
-constexpr int SP_MAXB = 12;  // max (bin, image) pairs per direction (P <= 32 <= m needs <= 8)
-
-// The source tiles whose points can reach the output tile starting at o (extent TS) along
-// one direction, as (wrapped tile index, grid shift) pairs: a point in cell c reaches the
-// tile iff c in [o - P/2, o + TS - 2 + P/2]. In a periodic direction that cell range is
-// split at multiples of m into one segment per image; each segment maps to whole tiles of
-// the wrapped grid, so no tile is visited twice for the same image.
-__device__ inline int tile_list(const GridGeom& g, int d, int o, int* bins, int* shift) {
-  const int P = g.P, m = g.m[d];
-  int clo = o - P / 2, chi = o + TS - 2 + P / 2;
-  int nb = 0;
-  if (!g.periodic[d]) {
-    clo = max(clo, 0);
-    chi = min(chi, m - 1);
-    for (int b = clo / TS; b <= chi / TS && nb < SP_MAXB; ++b) {
-      bins[nb] = b;
-      shift[nb] = 0;
-      ++nb;
-    }
-    return nb;
-  }
-  int c = clo;
-  while (c <= chi && nb < SP_MAXB) {
-    const int im = fdiv(c, m);
-    const int seg_hi = min(chi, (im + 1) * m - 1);
-    const int a = c - im * m, e = seg_hi - im * m;  // wrapped cells a..e
-    for (int b = a / TS; b <= e / TS && nb < SP_MAXB; ++b) {
-      bins[nb] = b;
-      shift[nb] = im * m;
-      ++nb;
-    }
-    c = seg_hi + 1;
-  }
-  return nb;
-}
-
 // Gridding, Eq. (SE-gridding-disc). Output-driven: the CTA (tile t, slab j) owns the TS^3
 // tile t and the j-th share of the source tiles that reach it (the source tiles are dealt
 // out round-robin over nslab CTAs). Each of the 64 threads owns one (y, z) column of the
@@ -323,8 +286,9 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
   __shared__ __align__(16) T s_w[CH][3 * TS];
   __shared__ T s_f[CH][CMAX];
   __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
+  __shared__ int s_list[CH], s_wcnt[2];
   const int P = g.P;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lz = tid & 7, ly = tid >> 3;
   const int slab = blockIdx.x % nslab;
   const int t0 = blockIdx.x / nslab, t1 = blockIdx.y, t2 = blockIdx.z;
@@ -334,7 +298,7 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
   for (int xx = 0; xx < TS; ++xx)
 #pragma unroll
     for (int c = 0; c < CMAX; ++c) acc[xx][c] = T(0);
-  if (tid < 3) s_nb[tid] = tile_list(g, tid, o[tid], s_bin[tid], s_sh[tid]);
+  if (tid < 3) s_nb[tid] = tile_list(g, tid, o[tid], TS, s_bin[tid], s_sh[tid]);
   __syncthreads();
   const int nbx = s_nb[0], nby = s_nb[1], nbz = s_nb[2];
   const int nbins = nbx * nby * nbz;
@@ -346,19 +310,34 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
     for (int p0 = beg; p0 < end; p0 += CH) {
       const int cnt = min(CH, end - p0);
       __syncthreads();
-      for (int idx = tid; idx < cnt * 3 * TS; idx += 64) {
+      // keep the points of the chunk whose support [base + rel, base + rel + P) meets the
+      // tile [0, TS) in all three directions (a source tile is reached only in part)
+      bool reach = false;
+      if (tid < cnt) {
+        const int* bp = base + 3 * (size_t)(p0 + tid);
+        const int s0 = bp[0] + rel0, s1 = bp[1] + rel1, s2 = bp[2] + rel2;
+        reach = s0 < TS && s0 + P > 0 && s1 < TS && s1 + P > 0 && s2 < TS && s2 + P > 0;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, reach);
+      if (lane == 0) s_wcnt[warp] = __popc(bal);
+      __syncthreads();
+      const int nreach = s_wcnt[0] + s_wcnt[1];
+      if (reach) s_list[(warp ? s_wcnt[0] : 0) + __popc(bal & ((1u << lane) - 1u))] = p0 + tid;
+      __syncthreads();
+      for (int idx = tid; idx < nreach * 3 * TS; idx += 64) {
         const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
         const int d = r / TS, l = r - d * TS;
         const int rel = d == 0 ? rel0 : (d == 1 ? rel1 : rel2);
-        const int q = l - (base[3 * (p0 + pp) + d] + rel);
-        s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)(p0 + pp) * 3 + d) * P + q] : T(0);
+        const int gp = s_list[pp];
+        const int q = l - (base[3 * gp + d] + rel);
+        s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)gp * 3 + d) * P + q] : T(0);
       }
-      for (int idx = tid; idx < cnt * C; idx += 64) {
+      for (int idx = tid; idx < nreach * C; idx += 64) {
         const int pp = idx / C, c = idx - pp * C;
-        s_f[pp][c] = sf[(size_t)(p0 + pp) * Ctot + c0 + c];
+        s_f[pp][c] = sf[(size_t)s_list[pp] * Ctot + c0 + c];
       }
       __syncthreads();
-      for (int pp = 0; pp < cnt; ++pp) {
+      for (int pp = 0; pp < nreach; ++pp) {
         const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
         if (wyz != T(0)) {
           T wx[TS];
@@ -562,6 +541,7 @@ struct RealArgs {
   int kernel, n_rhs, nsrc, ntgt;
   T Lhi[3], Llo[3];                  // box lengths as hi + lo parts (image shifts)
   int overwrite;                     // 1: u = sum, 0: u += sum
+  int maxseg, cols_per_round;        // segment-table layout (real_seg_setup)
   const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
   const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
   const T* fs;                       // sorted strengths [ns][c * n_rhs]
@@ -666,19 +646,39 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   }
 }
 
-// Real-space sum: one warp per target. The warp walks the neighbour columns of the target's
-// cell (each column, along direction 2, is one contiguous source range per periodic image,
-// trimmed to the part that can lie within rc of the target); 32 candidates are tested at a
-// time and the ones inside rc are compacted (ballot + popc) into a per-warp queue, which is
-// evaluated 32 pairs at a time with every lane busy. Lane partial sums are combined by
-// shuffles.
-constexpr int RS_WARPS = 4;  // warps per CTA
+// Real-space sum: one warp per target.
+// (1) Column table: the neighbour columns of the target's cell (along direction 2, trimmed to
+//     the cells that can hold sources within rc, split at periodic images into contiguous
+//     source ranges, "segments") are set up one column per lane, all cstart loads in flight
+//     at once; a warp scan lays the segments out as one flat candidate list.
+// (2) Candidates: the warp walks the flat list U x 32 at a time (U = 4 independent loads per
+//     lane in FP32, 2 in FP64), tests them on the hi parts and compacts the ones inside rc (ballot + popc)
+//     into a per-warp ring of pairs.
+// (3) Pairs: whenever 32 are queued they are evaluated one per lane with the exact hi + lo
+//     separation. Lane partial sums are combined by shuffles.
+// More than 32 columns (or more segments than the table holds) are done in rounds.
+constexpr int RS_WARPS = 4;    // warps per CTA
+constexpr int RS_SEGCAP = 64;  // column segments per round
+constexpr int RS_RING = 256;   // pair ring entries (power of two, >= 32 (RS_U + 1))
+template <typename T>
+struct RsU {  // candidate chunks of 32 in flight per lane
+  static constexpr int value = sizeof(T) == 4 ? 4 : 2;
+};
 
 template <typename T>
-struct PairQ {
-  int j[64];
-  int img[64];  // packed image offsets (3 x 8 bits, biased by 128)
+struct RealSmem {
+  typename Vec4<T>::type seg[RS_SEGCAP];  // image shift (x, y, z); w: first source - flat start
+  int start[RS_SEGCAP + 1];              // flat start of each segment (+ total)
+  int len[RS_SEGCAP];
+  int pk[RS_SEGCAP];                     // packed image numbers (3 x 8 bits, biased by 128)
+  int ring_j[RS_RING];
+  int ring_pk[RS_RING];
 };
+
+__device__ __forceinline__ float ipack(int v, float) { return __int_as_float(v); }
+__device__ __forceinline__ double ipack(int v, double) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int iunpack(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int iunpack(double v) { return (int)__double_as_longlong(v); }
 
 // wrap an unwrapped cell index into [0, n) and return the image number
 __device__ __forceinline__ int wrap_cell(int u, int n, int* im) {
@@ -691,11 +691,11 @@ __device__ __forceinline__ int wrap_cell(int u, int n, int* im) {
 
 template <typename T, int KERNEL, int RMAX>
 __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
-  __shared__ PairQ<T> q_s[RS_WARPS];
+  __shared__ RealSmem<T> sm_all[RS_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * RS_WARPS + warp;
   if (s >= a.ntgt) return;  // warp-uniform
-  PairQ<T>& q = q_s[warp];
+  RealSmem<T>& sm = sm_all[warp];
   typedef typename Vec4<T>::type V4;
   const V4 xt = a.xt[s];
   V4 xtl;
@@ -716,12 +716,15 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   const T cs0 = a.Lhi[0] / T(g.nc[0]), cs1 = a.Lhi[1] / T(g.nc[1]), cs2 = a.Lhi[2] / T(g.nc[2]);
   const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);
   const T tx = xt.x, ty = xt.y, tz = xt.z;
-  int qn = 0;
+  const T inv_cs2 = T(g.nc[2]) / a.Lhi[2];
+  unsigned head = 0, tail = 0;  // pair ring [head, tail)
+  // evaluate the pairs ring[head .. head + cnt) (cnt <= 32), one per lane
   // evaluate the queued pairs [0, cnt) (cnt <= 32), one per lane
   auto flush = [&](int cnt) {
     __syncwarp();
     if (lane < cnt) {
-      const int j = q.j[lane], pk = q.img[lane];
+      const int e = (head + lane) & (RS_RING - 1);
+      const int j = sm.ring_j[e], pk = sm.ring_pk[e];
       const T i0 = T((pk & 255) - 128), i1 = T(((pk >> 8) & 255) - 128), i2 = T(((pk >> 16) & 255) - 128);
       const V4 xs = a.xs[j];
       T r0, r1, r2;
@@ -745,71 +748,131 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
     }
     __syncwarp();
   };
-  for (int dx = -g.range[0]; dx <= g.range[0]; ++dx) {
-    int imx = 0, ux = cx + dx;
-    if (g.periodic[0]) ux = wrap_cell(ux, g.nc[0], &imx);
-    else if (ux < 0 || ux >= g.nc[0]) continue;
-    // distance from the target to the slab of this image of cell ux along direction 0
-    const T x0 = T(cx + dx) * cs0, x1 = x0 + cs0;
-    const T ddx = tx < x0 ? x0 - tx : (tx > x1 ? tx - x1 : T(0));
-    if (ddx * ddx >= rcp2) continue;
-    const T shx = T(imx) * a.Lhi[0];
-    for (int dy = -g.range[1]; dy <= g.range[1]; ++dy) {
-      int imy = 0, uy = cy + dy;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const int rx = g.range[0], ry = g.range[1];
+  const int ncy = 2 * ry + 1, ncol = (2 * rx + 1) * ncy;
+  const int maxseg = a.maxseg, cpr = a.cols_per_round;
+  for (int c0 = 0; c0 < ncol; c0 += cpr) {
+    // ---- (1) segments of columns c0 .. c0 + cpr - 1, column c0 + lane on this lane
+    __syncwarp();
+    const int slot0 = lane * maxseg;
+    int nseg = 0, tot = 0;
+    const int k = c0 + lane;
+    if (lane < cpr && k < ncol) {
+      const int kx = k / ncy;
+      const int dx = kx - rx, dy = k - kx * ncy - ry;
+      int imx = 0, imy = 0, ux = cx + dx, uy = cy + dy;
+      bool ok = true;
+      if (g.periodic[0]) ux = wrap_cell(ux, g.nc[0], &imx);
+      else ok = ux >= 0 && ux < g.nc[0];
       if (g.periodic[1]) uy = wrap_cell(uy, g.nc[1], &imy);
-      else if (uy < 0 || uy >= g.nc[1]) continue;
-      const T y0 = T(cy + dy) * cs1, y1 = y0 + cs1;
-      const T ddy = ty < y0 ? y0 - ty : (ty > y1 ? ty - y1 : T(0));
-      const T rem = rcp2 - ddx * ddx - ddy * ddy;
-      if (rem <= T(0)) continue;
-      const T shy = T(imy) * a.Lhi[1];
-      // cells along direction 2 that can hold sources within rc: |z - tz| < sqrt(rem)
-      const T zr = sqrt(rem);
-      int zlo = (int)floor((tz - zr) / cs2), zend = (int)floor((tz + zr) / cs2);
-      zlo = max(zlo, cz - g.range[2]);
-      zend = min(zend, cz + g.range[2]);
-      if (!g.periodic[2]) {
-        zlo = max(zlo, 0);
-        zend = min(zend, g.nc[2] - 1);
-      }
-      const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
-      while (zlo <= zend) {
-        int imz = 0, w0 = zlo;
-        if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
-        const int w1 = min(g.nc[2] - 1, w0 + (zend - zlo));  // up to the end of this image
-        const T shz = T(imz) * a.Lhi[2];
-        const int pk = (imx + 128) | ((imy + 128) << 8) | ((imz + 128) << 16);
-        const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
-        for (int jb = beg; jb < end; jb += 32) {
-          const int j = jb + lane;
-          bool in = false;
-          if (j < end) {
-            const V4 xs = a.xs[j];
-            const T r0 = xt.x - (xs.x + shx), r1 = xt.y - (xs.y + shy), r2 = xt.z - (xs.z + shz);
-            in = r0 * r0 + r1 * r1 + r2 * r2 < rcp2;
+      else ok = ok && uy >= 0 && uy < g.nc[1];
+      if (ok) {
+        // distance from the target to this image of the column, directions 0 and 1
+        const T x0 = T(cx + dx) * cs0, x1 = x0 + cs0;
+        const T ddx = tx < x0 ? x0 - tx : (tx > x1 ? tx - x1 : T(0));
+        const T y0 = T(cy + dy) * cs1, y1 = y0 + cs1;
+        const T ddy = ty < y0 ? y0 - ty : (ty > y1 ? ty - y1 : T(0));
+        const T rem = rcp2 - ddx * ddx - ddy * ddy;
+        if (rem > T(0)) {
+          // cells along direction 2 that can hold sources within rc: |z - tz| < sqrt(rem)
+          const T zr = sqrt(rem);
+          int zlo = (int)floor((tz - zr) * inv_cs2), zend = (int)floor((tz + zr) * inv_cs2);
+          zlo = max(zlo, cz - g.range[2]);
+          zend = min(zend, cz + g.range[2]);
+          if (!g.periodic[2]) {
+            zlo = max(zlo, 0);
+            zend = min(zend, g.nc[2] - 1);
           }
-          const unsigned bal = __ballot_sync(0xffffffffu, in);
-          if (in) {
-            const int pos = qn + __popc(bal & ((1u << lane) - 1u));
-            q.j[pos] = j;
-            q.img[pos] = pk;
-          }
-          qn += __popc(bal);
-          if (qn >= 32) {
-            flush(32);
-            qn -= 32;
-            if (lane < qn) {  // move the overflow (entries 32 .. qn+31) to the front
-              q.j[lane] = q.j[32 + lane];
-              q.img[lane] = q.img[32 + lane];
-            }
-            __syncwarp();
+          const T shx = T(imx) * a.Lhi[0], shy = T(imy) * a.Lhi[1];
+          const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
+          while (zlo <= zend && nseg < maxseg) {
+            int imz = 0, w0 = zlo;
+            if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
+            const int w1 = min(g.nc[2] - 1, w0 + (zend - zlo));  // up to the end of this image
+            const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
+            V4 sg;
+            sg.x = shx;
+            sg.y = shy;
+            sg.z = T(imz) * a.Lhi[2];
+            sg.w = ipack(beg, T());
+            sm.seg[slot0 + nseg] = sg;
+            sm.len[slot0 + nseg] = end - beg;
+            sm.pk[slot0 + nseg] = (imx + 128) | ((imy + 128) << 8) | ((imz + 128) << 16);
+            tot += end - beg;
+            ++nseg;
+            zlo += w1 - w0 + 1;
           }
         }
-        zlo += w1 - w0 + 1;
+      }
+    }
+    if (lane < cpr)
+      for (int i = nseg; i < maxseg; ++i) sm.len[slot0 + i] = 0;
+    int inc = tot;  // inclusive warp scan of the per-column candidate counts
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(FULL, inc, off);
+      if (lane >= off) inc += v;
+    }
+    const int total = __shfl_sync(FULL, inc, 31);
+    __syncwarp();
+    if (lane < cpr) {
+      int run = inc - tot;
+      for (int i = 0; i < maxseg; ++i) {
+        const int sl = slot0 + i;
+        sm.start[sl] = run;
+        if (i < nseg) sm.seg[sl].w = ipack(iunpack(sm.seg[sl].w) - run, T());
+        run += sm.len[sl];
+      }
+    }
+    if (lane == 0) sm.start[cpr * maxseg] = total;
+    __syncwarp();
+    // ---- (2) candidates of the flat list, RS_U x 32 per pass
+    int sp = 0;  // this lane's segment (monotone along the list)
+    constexpr int RS_U = RsU<T>::value;
+    for (int b0 = 0; b0 < total; b0 += 32 * RS_U) {
+      int jj[RS_U], sv[RS_U];
+      V4 xv[RS_U];
+      T sx[RS_U], sy[RS_U], sz[RS_U];
+#pragma unroll
+      for (int u = 0; u < RS_U; ++u) {
+        const int f = b0 + 32 * u + lane;
+        sv[u] = -1;
+        if (f < total) {
+          while (sm.start[sp + 1] <= f) ++sp;
+          const V4 sg = sm.seg[sp];
+          sv[u] = sp;
+          jj[u] = iunpack(sg.w) + f;
+          sx[u] = sg.x;
+          sy[u] = sg.y;
+          sz[u] = sg.z;
+          xv[u] = a.xs[jj[u]];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < RS_U; ++u) {
+        bool in = false;
+        if (sv[u] >= 0) {
+          const T r0 = tx - (xv[u].x + sx[u]), r1 = ty - (xv[u].y + sy[u]), r2 = tz - (xv[u].z + sz[u]);
+          in = r0 * r0 + r1 * r1 + r2 * r2 < rcp2;
+        }
+        const unsigned bal = __ballot_sync(FULL, in);
+        if (in) {
+          const int e = (tail + __popc(bal & lt_mask)) & (RS_RING - 1);
+          sm.ring_j[e] = jj[u];
+          sm.ring_pk[e] = sm.pk[sv[u]];
+        }
+        tail += __popc(bal);
+      }
+      // ---- (3) pairs, 32 at a time
+      while (tail - head >= 32u) {
+        flush(32);
+        head += 32;
       }
     }
   }
-  if (qn > 0) flush(qn);
+  if (tail != head) flush((int)(tail - head));
 #pragma unroll
   for (int k = 0; k < 3 * RMAX; ++k) {
     T v = acc[k];
@@ -825,6 +888,19 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
         *o = a.overwrite ? acc[3 * r + qq] : *o + acc[3 * r + qq];
       }
   }
+}
+
+// Segment-table layout of a real-space launch: segments per column (periodic direction 2
+// splits a column at each image boundary) and columns per round.
+template <typename T>
+static se_status real_seg_setup(RealArgs<T>& ra) {
+  const CellGeom& g = ra.cg;
+  int maxseg = 1;
+  if (g.periodic[2]) maxseg = (2 * g.range[2] + 1 + g.nc[2] - 1) / g.nc[2] + 1;
+  if (maxseg > RS_SEGCAP) return SE_ERR_UNSUPPORTED;
+  ra.maxseg = maxseg;
+  ra.cols_per_round = std::min(32, RS_SEGCAP / maxseg);
+  return SE_OK;
 }
 
 // sorted positions (wrapped, plan precision, padded to 4) and cell coordinates
@@ -1021,6 +1097,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   p->window = window;
   p->opts = o;
   p->prec = o.prec;
+  p->flags = o.flags;
   p->stream = (cudaStream_t)o.stream;
   cudaGetDevice(&p->device);
 
@@ -1253,7 +1330,10 @@ void spread_launch_group(se_plan_t* p, const int* tile_start, const int* base, c
 }
 
 template <typename T>
-void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C, T* grid) {
+se_status spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C,
+                        T* grid) {
+  if (sizeof(T) == 4 && (p->flags & SE_FLAG_TC_GRIDDING) && p->geom.P <= 16)
+    return spread_tc_launch(p, tile_start, base, (const float*)w, (const float*)sf, C, (float*)grid);
   // deal the source tiles of each output tile over nslab CTAs so that the grid has enough
   // CTAs to fill the GPU; the partial tiles are then added atomically into a zeroed grid.
   // Components go in groups that fit the registers (24 floats or 12 doubles per grid point).
@@ -1270,6 +1350,7 @@ void spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T
     else if (Cc <= 12) spread_launch_group<T, 12>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
     else spread_launch_group<T, 24>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
   }
+  return SE_OK;
 }
 
 template <typename T, int NC>
@@ -1401,6 +1482,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       ra.tcell = (int*)tcell;
       ra.u = overlap ? ureal : u;
       ra.overwrite = overlap ? 1 : 0;
+      SE_TRY(real_seg_setup(ra));
       if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
       if (n_rhs <= 1) real_launch<T, 1>(p, rs, ra);
       else if (n_rhs <= 4) real_launch<T, 4>(p, rs, ra);
@@ -1444,7 +1526,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
     if (g.n[0] != g.m[0] || g.n[1] != g.m[1] || g.n[2] != g.m[2])
       SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));  // zero padding (D = 0)
-    spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid);
+    SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid));
     SE_CUDA(cudaGetLastError());
     p->last_grid_comps = C;
     stage.mark();  // 2: spread
@@ -1698,6 +1780,7 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   ra.tcell = tcell;
   ra.u = u;
   ra.overwrite = 0;
+  SE_TRY(real_seg_setup(ra));
   const int grid = grid1d(N, RS_WARPS);
   if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
   else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);

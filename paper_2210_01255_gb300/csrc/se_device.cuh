@@ -76,4 +76,43 @@ __device__ __forceinline__ T regular_scalar(int kernel, T kk, T inv4xi2) {
   return T(-8.0 * 3.14159265358979323846) / (kk * kk) * (T(1) + kk * inv4xi2);
 }
 
+// ---------------------------------------------------------------- gridding source lists
+
+constexpr int SP_MAXB = 12;  // max (bin, image) pairs per direction (E <= 16, P <= 32: <= 8)
+
+// The source tiles (TS cells per direction, the bins of the point sort) whose points can
+// reach the output tile starting at o with extent E along one direction, as (wrapped tile
+// index, grid shift) pairs: a point in cell c reaches the tile iff
+// c in [o - P/2, o + E - 2 + P/2]. In a periodic direction that cell range is
+// split at multiples of m into one segment per image; each segment maps to whole tiles of
+// the wrapped grid, so no tile is visited twice for the same image.
+__device__ inline int tile_list(const GridGeom& g, int d, int o, int E, int* bins, int* shift) {
+  const int P = g.P, m = g.m[d];
+  int clo = o - P / 2, chi = o + E - 2 + P / 2;
+  int nb = 0;
+  if (!g.periodic[d]) {
+    clo = max(clo, 0);
+    chi = min(chi, m - 1);
+    for (int b = clo / TS; b <= chi / TS && nb < SP_MAXB; ++b) {
+      bins[nb] = b;
+      shift[nb] = 0;
+      ++nb;
+    }
+    return nb;
+  }
+  int c = clo;
+  while (c <= chi && nb < SP_MAXB) {
+    const int im = fdiv(c, m);
+    const int seg_hi = min(chi, (im + 1) * m - 1);
+    const int a = c - im * m, e = seg_hi - im * m;  // wrapped cells a..e
+    for (int b = a / TS; b <= e / TS && nb < SP_MAXB; ++b) {
+      bins[nb] = b;
+      shift[nb] = im * m;
+      ++nb;
+    }
+    c = seg_hi + 1;
+  }
+  return nb;
+}
+
 }  // namespace se

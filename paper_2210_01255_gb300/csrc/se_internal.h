@@ -64,6 +64,7 @@ struct se_plan_t {
   int window = SE_WIN_PKB;
   se_opts opts{};
   int prec = SE_FP64;
+  int flags = 0;  // se_opts.flags
   cudaStream_t stream = nullptr;
   int device = 0;
 
@@ -123,6 +124,9 @@ struct ScaleTables {
 };
 template <typename T>
 se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const ScaleTables<T>& t);
+// FP32 gridding on the tensor cores (se_spread_tc.cu)
+se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
+                           int C, float* grid);
 se_status free_plan_setup(se_plan_t* p);
 template <typename T>
 se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);
