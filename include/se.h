@@ -78,6 +78,8 @@ typedef struct {
   int kernel_mask;   /* kernels the plan will be used with (for the free-direction rules); 0 = all */
   void* stream;      /* cudaStream_t to issue work on; NULL = the legacy default stream   */
   int flags;         /* SE_FLAG_* bits, 0 = defaults                                        */
+  double n_rc;       /* se_autotune: average neighbours within r_c used to choose xi when
+                        *xi_io <= 0 (Sec. 5.2); 0 = the paper's uniform-case values (Table 5) */
 } se_opts;
 
 /* se_opts.flags: with SE_FLAG_TC_GRIDDING, FP32 gridding (Alg. 1, gridding step) with window

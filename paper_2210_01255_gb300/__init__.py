@@ -36,7 +36,8 @@ class se_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("f_M", ctypes.c_int), ("lambda_", ctypes.c_double),
                 ("Mext", ctypes.c_int * 3), ("s0", ctypes.c_double), ("s_star", ctypes.c_double),
                 ("kbar_star", ctypes.c_int), ("tol_abs", ctypes.c_double), ("Q", ctypes.c_double),
-                ("kernel_mask", ctypes.c_int), ("stream", ctypes.c_void_p), ("flags", ctypes.c_int)]
+                ("kernel_mask", ctypes.c_int), ("stream", ctypes.c_void_p), ("flags", ctypes.c_int),
+                ("n_rc", ctypes.c_double)]
 
 
 class se_info(ctypes.Structure):

@@ -208,6 +208,7 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
     if (N <= 0) return SE_ERR_ARG;
     double nrc = 0;
     for (int i = 0; i < nk; ++i) nrc = std::max(nrc, nrc_uniform(kernels[i], D));
+    if (io->n_rc > 0) nrc = io->n_rc;
     double rc = std::cbrt(3.0 * nrc * vol / (4.0 * M_PI * (double)N));
     xi = 4.0 / rc;
     for (int it = 0; it < 60; ++it) {
