@@ -106,7 +106,7 @@ def tuned(cfg, kernel, f):
 KERNEL_SOURCES = {"real": "se_core.cu", "spread": "se_core.cu", "gather": "se_core.cu"}
 
 
-def kernel_traffic(stage, params):
+def kernel_traffic(stage, params, gridding="cuda"):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the stage's kernel
     from the committed ncu summary profiles/traffic_3p_stresslet_rotlet_n20000.txt, averaged over
     the stresslet and rotlet launches; None when the summary is missing, was taken for other
@@ -117,6 +117,8 @@ def kernel_traffic(stage, params):
         lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     except OSError:
         return None
+    if stage == "spread" and gridding == "tc":
+        return None  # the summary covers the CUDA-core gridding kernel only
     src = os.path.join(ROOT, "paper_2210_01255_gb300", "csrc", KERNEL_SOURCES[stage])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = []
@@ -274,7 +276,7 @@ def main():
     dom = max(work, key=lambda n: per_stage[n])
     ach = work[dom] / (per_stage[dom] * 1e-3) / 1e12
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(dom, params),
+            "frac": ach / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(dom, params, args.gridding),
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived from unit counts and "
                            "the maximum SM clock)"}
     roof["per_stage_tflops"] = {k: work[k] / (per_stage[k] * 1e-3) / 1e12 for k in work if per_stage[k] > 0}

@@ -33,7 +33,6 @@ constexpr int TC_N = 48;              // accumulator columns: Z * CG
 constexpr int TC_K = 32;              // points per operand stage (4 MMAs of K = 8)
 constexpr int TC_THREADS = 256;
 constexpr int TC_PMAX = 16;           // window supports handled here (larger P: CUDA cores)
-constexpr int TC_PF = TC_K * 3 * TC_PMAX / TC_THREADS;  // raw window values per thread
 constexpr uint32_t TC_TMEM_COLS = 128; // two accumulators of TC_N columns, at 0 and 64
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 
@@ -42,7 +41,9 @@ constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 constexpr uint32_t TC_LBO = 128;                 // next core matrix along K
 constexpr uint32_t TC_SBO = 128 * (TC_K / 4);    // next 8-row group
 
-constexpr int TC_WS = TC_K + 4;  // row stride (words) of the transposed window tables
+constexpr int TC_WS = TC_K + 4;          // row stride (words) of the transposed window tables
+constexpr int TC_RWS = 3 * TC_PMAX + 1;   // per-point stride (words) of the raw window values
+constexpr int TC_PEND = 2 * TC_K + TC_THREADS;  // pending reaching points (< 64 + one pass)
 
 template <int Z, int CG>
 struct TcSmem {
@@ -56,10 +57,9 @@ struct TcSmem {
   float w1[TC_Y][TC_WS];
   float w2[Z][TC_WS];
   float f[CG][TC_WS];
-  float r_w[TC_K * 3 * TC_PMAX];  // raw window values of the next chunk's points (as in wts)
-  int r_base[TC_K * 3];
-  float r_f[TC_K * CG];
-  int r_meta[4];                  // points in the chunk, image shifts rel0..2
+  float r_w[TC_K * TC_RWS];  // raw window values of the chunk's points (as in wts), odd stride
+  int4 pend[TC_PEND];        // reaching points: (index, first tap - tile origin, per direction)
+  int wcnt[TC_THREADS / 32];
   uint64_t mbar[2];
   uint32_t tmem_base;
   int bins[3][SP_MAXB], sh[3][SP_MAXB], nb[3];
@@ -125,15 +125,16 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
 
 template <int Z, int CG>
 __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const int* __restrict__ tile_start,
-                                                          const int* __restrict__ base,
-                                                          const float* __restrict__ wts,
-                                                          const float* __restrict__ sf, int Ctot, int c0, int C,
-                                                          int nslab, float* __restrict__ grid,
-                                                          int* __restrict__ status) {
+                                                             const int* __restrict__ base,
+                                                             const float* __restrict__ wts,
+                                                             const float* __restrict__ sf, int Ctot, int c0, int C,
+                                                             int nslab, float* __restrict__ grid,
+                                                             int* __restrict__ status) {
   static_assert(Z * CG == TC_N, "accumulator width");
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   TcSmem<Z, CG>& sm = *reinterpret_cast<TcSmem<Z, CG>*>(tc_smem_raw);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const unsigned FULL = 0xffffffffu;
   const int P = g.P;
   const int slab = blockIdx.x % nslab;
   const int o0 = (int)(blockIdx.x / nslab) * TC_X, o1 = (int)blockIdx.y * TC_Y, o2 = (int)blockIdx.z * Z;
@@ -188,13 +189,42 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
     return true;
   };
 
-  // ---- the CTA's chunks: 32 consecutive points of one source bin at a time
-  int it_ib = slab - nslab, it_p0 = 0, it_end = 0, it_rel0 = 0, it_rel1 = 0, it_rel2 = 0;
-  auto advance = [&]() -> bool {  // to the next chunk; uniform
-    it_p0 += TC_K;
-    while (it_p0 >= it_end) {
-      it_ib += nslab;
-      if (it_ib >= nbins) return false;
+  int chunk = 0;
+  bool ok = true;
+  int npend = 0;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  // raw data of a chunk (pending points 0 .. cnt - 1), warp w holding points w, w + 8, ...:
+  // loaded to registers, stored to shared memory later (all loads of a chunk in flight at once)
+  float pw[TC_K / 8][2], pfv[TC_K / 8];
+  auto fetch = [&](int first, int cnt) {
+#pragma unroll
+    for (int j = 0; j < TC_K / 8; ++j) {
+      const int k = warp + 8 * j;
+      const bool valid = k < cnt;
+      const int gp = valid ? sm.pend[first + k].x : 0;
+      const float* src = wts + (size_t)gp * 3 * P;
+      pw[j][0] = (valid && lane < 3 * P) ? src[lane] : 0.f;
+      pw[j][1] = (valid && lane + 32 < 3 * P) ? src[lane + 32] : 0.f;
+      pfv[j] = (valid && lane < C) ? sf[(size_t)gp * Ctot + c0 + lane] : 0.f;
+    }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int j = 0; j < TC_K / 8; ++j) {
+      const int k = warp + 8 * j;
+      sm.r_w[k * TC_RWS + lane] = pw[j][0];
+      if (lane + 32 < TC_RWS) sm.r_w[k * TC_RWS + lane + 32] = pw[j][1];
+      if (lane < CG) sm.f[lane][k] = pfv[j];
+    }
+  };
+
+  // ---- the source bins streamed through candidate passes: keep the points whose support
+  // meets the tile (exact test on the first taps), appended to the pending list
+  int it_ib = slab, it_p0 = 0, it_end = 0, it_rel0 = 0, it_rel1 = 0, it_rel2 = 0;
+  bool more = it_ib < nbins;
+  auto load_bin = [&]() {  // uniform
+    while (it_ib < nbins) {
       const int ix = it_ib / (nby * nbz), iy = (it_ib / nbz) % nby, iz = it_ib % nbz;
       const int bin = (sm.bins[0][ix] * g.ntile[1] + sm.bins[1][iy]) * g.ntile[2] + sm.bins[2][iz];
       it_p0 = tile_start[bin];
@@ -202,99 +232,92 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
       it_rel0 = sm.sh[0][ix] - o0;
       it_rel1 = sm.sh[1][iy] - o1;
       it_rel2 = sm.sh[2][iz] - o2;
+      if (it_p0 < it_end) return true;
+      it_ib += nslab;
     }
-    return true;
+    return false;
   };
-  // raw data of a chunk: loaded to registers (all loads in flight together), stored to smem later
-  float pw[TC_PF], pf = 0.f;
-  int pb = 0, pcnt = 0;
-  auto fetch = [&]() {
-    pcnt = min(TC_K, it_end - it_p0);
-    const float* wsrc = wts + (size_t)it_p0 * 3 * P;
-    const int nw = pcnt * 3 * P;
+  more = load_bin();
+  auto refill = [&]() {  // until two chunks are pending or the bins are exhausted; uniform
+    while (more && npend < 2 * TC_K) {
+      const int gp = it_p0 + tid;
+      bool reach = false;
+      int s0 = 0, s1 = 0, s2 = 0;
+      if (gp < it_end) {
+        s0 = base[3 * (size_t)gp] + it_rel0;
+        s1 = base[3 * (size_t)gp + 1] + it_rel1;
+        s2 = base[3 * (size_t)gp + 2] + it_rel2;
+        reach = s0 < TC_X && s0 + P > 0 && s1 < TC_Y && s1 + P > 0 && s2 < Z && s2 + P > 0;
+      }
+      const unsigned bal = __ballot_sync(FULL, reach);
+      if (lane == 0) sm.wcnt[warp] = __popc(bal);
+      __syncthreads();
+      int off = npend, tot = 0;
 #pragma unroll
-    for (int j = 0; j < TC_PF; ++j) {
-      const int i = tid + j * TC_THREADS;
-      pw[j] = i < nw ? wsrc[i] : 0.f;
-    }
-    pb = tid < pcnt * 3 ? base[(size_t)it_p0 * 3 + tid] : 0;
-    pf = 0.f;
-    if (tid < pcnt * CG) {
-      const int i = tid / CG, c = tid - i * CG;
-      if (c < C) pf = sf[(size_t)(it_p0 + i) * Ctot + c0 + c];
-    }
-  };
-  auto store = [&]() {
-#pragma unroll
-    for (int j = 0; j < TC_PF; ++j) sm.r_w[tid + j * TC_THREADS] = pw[j];
-    if (tid < TC_K * 3) sm.r_base[tid] = pb;
-    if (tid < TC_K * CG) sm.r_f[tid] = pf;
-    if (tid == 0) {
-      sm.r_meta[0] = pcnt;
-      sm.r_meta[1] = it_rel0;
-      sm.r_meta[2] = it_rel1;
-      sm.r_meta[3] = it_rel2;
+      for (int w = 0; w < TC_THREADS / 32; ++w) {
+        const int c = sm.wcnt[w];
+        off += w < warp ? c : 0;
+        tot += c;
+      }
+      if (reach) sm.pend[off + __popc(bal & lt_mask)] = make_int4(gp, s0, s1, s2);
+      npend += tot;
+      it_p0 += TC_THREADS;
+      if (it_p0 >= it_end) {
+        it_ib += nslab;
+        more = load_bin();
+      }
+      __syncthreads();
     }
   };
 
-  int chunk = 0;
-  bool ok = true;
-  bool has = advance();
-  if (has) {
-    fetch();
+  refill();
+  if (npend > 0) {
+    fetch(0, min(TC_K, npend));
     store();
   }
   __syncthreads();
-  while (has) {
-    // stage and accumulator chunk & 1 were last used by chunk - 2 (drained at chunk - 1); the
-    // raw buffer holds this chunk (stored last iteration) until this chunk's staging is done
+  while (npend > 0 && ok) {
     const int st = chunk & 1;
-    const bool has_next = advance();
-    if (has_next) fetch();
-    // ---- window values aligned to the tile, transposed, from the raw buffer
+    const int cnt = min(TC_K, npend), ncnt = min(TC_K, npend - cnt);
+    if (ncnt > 0) fetch(cnt, ncnt);  // the next chunk's raw data, in flight during this one
+    // ---- window values aligned to the tile, transposed; lane = point of the chunk
     {
-      const int cnt = sm.r_meta[0];
-      const int rel0 = sm.r_meta[1], rel1 = sm.r_meta[2], rel2 = sm.r_meta[3];
-      for (int idx = tid; idx < TC_K * (TC_X + TC_Y + Z + CG); idx += TC_THREADS) {
-        const int k = idx & (TC_K - 1), e = idx / TC_K;  // point k of the chunk, table row e
-        const bool valid = k < cnt;
-        if (e < TC_X + TC_Y + Z) {
-          const int d = e < TC_X ? 0 : (e < TC_X + TC_Y ? 1 : 2);
-          const int l = e - (d == 0 ? 0 : (d == 1 ? TC_X : TC_X + TC_Y));
-          float w = 0.f;
-          if (valid) {
-            const int qq = l - (sm.r_base[3 * k + d] + (d == 0 ? rel0 : (d == 1 ? rel1 : rel2)));
-            if (qq >= 0 && qq < P) w = sm.r_w[(3 * k + d) * P + qq];
-          }
-          if (d == 0) sm.w0[l][k] = w;
-          else if (d == 1) sm.w1[l][k] = w;
-          else sm.w2[l][k] = w;
-        } else {
-          const int c = e - (TC_X + TC_Y + Z);
-          sm.f[c][k] = valid ? sm.r_f[k * CG + c] : 0.f;
+      const int k = lane;
+      const int4 pe = sm.pend[k];
+      const bool valid = k < cnt;
+      const float* rw = sm.r_w + k * TC_RWS;
+      if (warp == 0 || warp == 4) {
+        const int s0 = pe.y;
+        for (int l = (warp == 0 ? 0 : TC_X / 2); l < (warp == 0 ? TC_X / 2 : TC_X); ++l) {
+          const int qq = l - s0;
+          sm.w0[l][k] = (valid && qq >= 0 && qq < P) ? rw[qq] : 0.f;
+        }
+      } else if (warp == 1) {
+        const int s1 = pe.z;
+        for (int l = 0; l < TC_Y; ++l) {
+          const int qq = l - s1;
+          sm.w1[l][k] = (valid && qq >= 0 && qq < P) ? rw[P + qq] : 0.f;
+        }
+      } else if (warp == 2 || warp == 6) {
+        const int s2 = pe.w;
+        const int lb = warp == 2 ? 0 : Z / 2, le = warp == 2 ? Z / 2 : Z;
+        for (int l = lb; l < le; ++l) {
+          const int qq = l - s2;
+          sm.w2[l][k] = (valid && qq >= 0 && qq < P) ? rw[2 * P + qq] : 0.f;
         }
       }
     }
     __syncthreads();
-    // ---- operands. One task = one row of one core matrix: 4 consecutive K (points) of
-    // row m (A) or n (B), built from two 128-bit loads and written as two 128-bit stores
-    // (hi, lo). Lane = (row r, K group kc): 8 lanes of a row group write 128 contiguous bytes.
+    // ---- operands: one task = 4 consecutive K (points) of one row of a core matrix, built
+    // from two 128-bit loads and written as two 128-bit stores (hi, lo); 8 lanes of a row
+    // group write 128 contiguous bytes
     {
-      constexpr int NA = TC_M / 8 * (TC_K / 4) * 8;  // A row tasks: 16 x-groups x 8 kc x 8 rows
-      constexpr int NB = TC_N / 8 * (TC_K / 4) * 8;
-      for (int t = tid; t < NA + NB; t += TC_THREADS) {
-        const int isA = t < NA;
-        const int tt = isA ? t : t - NA;
-        const int r = tt & 7, kc = (tt >> 3) & 7, rg = tt >> 6;  // row, K group, row group
-        float4 u, v;
-        if (isA) {  // row m = 8 x + y with x = rg, y = r
-          u = *reinterpret_cast<const float4*>(&sm.w0[rg][4 * kc]);
-          v = *reinterpret_cast<const float4*>(&sm.w1[r][4 * kc]);
-        } else {    // row n = z CG + c
-          const int n = rg * 8 + r, z = n / CG, c = n - z * CG;
-          u = *reinterpret_cast<const float4*>(&sm.w2[z][4 * kc]);
-          v = *reinterpret_cast<const float4*>(&sm.f[c][4 * kc]);
-        }
+      const int r = tid & 7, kc = (tid >> 3) & 7, rg0 = tid >> 6;  // A: rows m = 8 x + y, x = rg
+      const float4 v = *reinterpret_cast<const float4*>(&sm.w1[r][4 * kc]);
+#pragma unroll
+      for (int j = 0; j < TC_M / 8 / 4; ++j) {
+        const int rg = rg0 + 4 * j;
+        const float4 u = *reinterpret_cast<const float4*>(&sm.w0[rg][4 * kc]);
         const float a0 = u.x * v.x, a1 = u.y * v.y, a2 = u.z * v.z, a3 = u.w * v.w;
         uint4 hi, lo;
         hi.x = f2tf32(a0);
@@ -307,13 +330,27 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
         lo.z = __float_as_uint(a2 - __uint_as_float(hi.z));
         lo.w = __float_as_uint(a3 - __uint_as_float(hi.w));
         const int widx = (rg * (TC_K / 4) + kc) * 32 + r * 4;  // (rg SBO + kc LBO + r 16 B) / 4
-        if (isA) {
-          *reinterpret_cast<uint4*>(&sm.a_hi[st][widx]) = hi;
-          *reinterpret_cast<uint4*>(&sm.a_lo[st][widx]) = lo;
-        } else {
-          *reinterpret_cast<uint4*>(&sm.b_hi[st][widx]) = hi;
-          *reinterpret_cast<uint4*>(&sm.b_lo[st][widx]) = lo;
-        }
+        *reinterpret_cast<uint4*>(&sm.a_hi[st][widx]) = hi;
+        *reinterpret_cast<uint4*>(&sm.a_lo[st][widx]) = lo;
+      }
+      for (int t = tid; t < TC_N * (TC_K / 4); t += TC_THREADS) {  // B: rows n = z CG + c
+        const int rb = t & 7, kcb = (t >> 3) & 7, ng = t >> 6;
+        const int n = ng * 8 + rb, z = n / CG, c = n - z * CG;
+        const float4 u = *reinterpret_cast<const float4*>(&sm.w2[z][4 * kcb]);
+        const float4 fv = *reinterpret_cast<const float4*>(&sm.f[c][4 * kcb]);
+        const float b0 = u.x * fv.x, b1 = u.y * fv.y, b2 = u.z * fv.z, b3 = u.w * fv.w;
+        uint4 hi, lo;
+        hi.x = f2tf32(b0);
+        hi.y = f2tf32(b1);
+        hi.z = f2tf32(b2);
+        hi.w = f2tf32(b3);
+        lo.x = __float_as_uint(b0 - __uint_as_float(hi.x));
+        lo.y = __float_as_uint(b1 - __uint_as_float(hi.y));
+        lo.z = __float_as_uint(b2 - __uint_as_float(hi.z));
+        lo.w = __float_as_uint(b3 - __uint_as_float(hi.w));
+        const int widx = (ng * (TC_K / 4) + kcb) * 32 + rb * 4;
+        *reinterpret_cast<uint4*>(&sm.b_hi[st][widx]) = hi;
+        *reinterpret_cast<uint4*>(&sm.b_lo[st][widx]) = lo;
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -334,18 +371,29 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
       }
       mma_commit(&sm.mbar[st]);
     }
-    if (has_next) store();
-    // ---- add the previous chunk (its MMAs ran while this chunk's operands were built)
+    if (ncnt > 0) store();  // staging and formation of this chunk are done (barrier above)
+    // ---- add the previous chunk (its MMAs ran while this chunk's operands were built); the
+    // stage and accumulator of chunk - 1 are then free for chunk + 1
     if (chunk >= 1 && !drain(chunk - 1)) {
-      if (tid == 0) atomicOr(status, 2);
       ok = false;
-      ++chunk;
       break;
     }
     ++chunk;
-    has = has_next;
-    __syncthreads();
+    // ---- drop this chunk from the pending list, then top it up
+    {
+      const int rest = npend - cnt;
+      int4 v0 = make_int4(0, 0, 0, 0), v1 = v0;
+      if (tid < rest) v0 = sm.pend[cnt + tid];
+      if (tid + TC_THREADS < rest) v1 = sm.pend[cnt + tid + TC_THREADS];
+      __syncthreads();
+      if (tid < rest) sm.pend[tid] = v0;
+      if (tid + TC_THREADS < rest) sm.pend[tid + TC_THREADS] = v1;
+      npend = rest;
+      __syncthreads();
+    }
+    refill();
   }
+  if (!ok && tid == 0) atomicOr(status, 2);
   if (ok && chunk >= 1 && !drain(chunk - 1)) {
     if (tid == 0) atomicOr(status, 2);
     ok = false;
