@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 
@@ -133,10 +134,15 @@ __global__ void k_scatter_perm(const int* __restrict__ key, const int* __restric
 }
 
 // counting sort by key; returns perm (sorted -> original) and start[nk+1]
+// scatter(key, rank, start, perm): a kernel that writes perm and the sorted payload of each
+// point at its slot start[key] + rank in one pass (replaces the plain perm scatter)
+typedef std::function<void(const int*, const int*, const int*, int*)> ScatterFn;
+
 static se_status counting_sort(se_plan_t* p, cudaStream_t st, const char* tag, int n, int nk,
                                void (*keyfun)(se_plan_t*, cudaStream_t, const double*, int, int*, int*, int*,
                                               const void*),
-                               const double* x, const void* geom, int** perm_out, int** start_out) {
+                               const double* x, const void* geom, int** perm_out, int** start_out,
+                               const ScatterFn& scatter = ScatterFn()) {
   std::string t(tag);
   void *key, *rank, *count, *start, *perm;
   SE_TRY(buf(p, (t + ".key").c_str(), sizeof(int) * (size_t)n, &key));
@@ -150,7 +156,8 @@ static se_status counting_sort(se_plan_t* p, cudaStream_t st, const char* tag, i
   k_scan<<<1, 1024, 0, st>>>((int*)count, (int*)start, nk);
   if (n > 0) {
     ++p->launches;
-    k_scatter_perm<<<grid1d(n, 256), 256, 0, st>>>((int*)key, (int*)rank, (int*)start, n, (int*)perm);
+    if (scatter) scatter((const int*)key, (const int*)rank, (const int*)start, (int*)perm);
+    else k_scatter_perm<<<grid1d(n, 256), 256, 0, st>>>((int*)key, (int*)rank, (int*)start, n, (int*)perm);
   }
   SE_CUDA(cudaGetLastError());
   *perm_out = (int*)perm;
@@ -212,14 +219,11 @@ __device__ inline T win_tap(const WinArgs<T>& w, int q, T delta) {
   return dev_i0(w.beta * sqrt(a)) * w.inv_i0beta;
 }
 
-// base tap index (unwrapped) and window values for each point, in sorted order
+// base tap index (unwrapped) and window values of point i, written at sorted slot s
 template <typename T>
-__global__ void k_weights(GridGeom g, WinArgs<T> w, const double* __restrict__ x,
-                          const int* __restrict__ perm, int n, int* __restrict__ base,
-                          T* __restrict__ wts, int* status) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int i = perm ? perm[s] : s;
+__device__ __forceinline__ void put_weights(const GridGeom& g, const WinArgs<T>& w, const double* __restrict__ x,
+                                            int i, int s, int* __restrict__ base, T* __restrict__ wts,
+                                            int* status) {
   const int P = g.P;
   for (int d = 0; d < 3; ++d) {
     double xw = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
@@ -234,15 +238,12 @@ __global__ void k_weights(GridGeom g, WinArgs<T> w, const double* __restrict__ x
   }
 }
 
-// spread components in sorted order: S, Omega: f per RHS; T: the 6 symmetric components
-// (q_l nu_m + q_m nu_l)/2 in the order 11,22,33,12,13,23 (the stresslet operator is fully
-// symmetric, Eq. stokes-kernels, so only the symmetric part of f_lm contributes)
+// spread components of point i at sorted slot s: S, Omega: f per RHS; T: the 6 symmetric
+// components (q_l nu_m + q_m nu_l)/2 in the order 11,22,33,12,13,23 (the stresslet operator is
+// fully symmetric, Eq. stokes-kernels, so only the symmetric part of f_lm contributes)
 template <typename T>
-__global__ void k_sort_strengths(int kernel, const T* __restrict__ f, const int* __restrict__ perm,
-                                 int n, int n_rhs, T* __restrict__ sf) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int i = perm[s];
+__device__ __forceinline__ void put_spread_strengths(int kernel, const T* __restrict__ f, int n, int n_rhs, int i,
+                                                     int s, T* __restrict__ sf) {
   if (kernel == SE_STRESSLET) {
     const int C = 6 * n_rhs;
     for (int r = 0; r < n_rhs; ++r) {
@@ -261,6 +262,22 @@ __global__ void k_sort_strengths(int kernel, const T* __restrict__ f, const int*
     for (int r = 0; r < n_rhs; ++r)
       for (int l = 0; l < 3; ++l) sf[(size_t)s * C + 3 * r + l] = f[((size_t)r * n + i) * 3 + l];
   }
+}
+
+// tile sort, last pass: perm, base taps, window values and (sources) spread components of
+// each point written at its slot s = start[key] + rank
+template <typename T>
+__global__ void k_scatter_tile(GridGeom g, WinArgs<T> w, const int* __restrict__ key,
+                               const int* __restrict__ rank, const int* __restrict__ start, int n,
+                               const double* __restrict__ x, int kernel, const T* __restrict__ f, int n_rhs,
+                               int* __restrict__ perm, int* __restrict__ base, T* __restrict__ wts,
+                               T* __restrict__ sf, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = start[key[i]] + rank[i];
+  perm[s] = i;
+  put_weights(g, w, x, i, s, base, wts, status);
+  if (f) put_spread_strengths(kernel, f, n, n_rhs, i, s, sf);
 }
 
 // ========================================================= gridding, Eq. (SE-gridding-disc)
@@ -903,15 +920,18 @@ static se_status real_seg_setup(RealArgs<T>& ra) {
   return SE_OK;
 }
 
-// sorted positions (wrapped, plan precision, padded to 4) and cell coordinates
+// cell sort, last pass: perm, the wrapped position of point i as hi (+ lo, FP32) parts, its
+// cell coordinates (when cell3 is given) and (sources) its strengths, at slot start[key] + rank
 template <typename T>
-__global__ void k_sort_positions(CellGeom g, const double* __restrict__ x, const int* __restrict__ perm,
-                                 int n, typename Vec4<T>::type* __restrict__ xs,
-                                 typename Vec4<T>::type* __restrict__ xsl, int* __restrict__ cell3,
-                                 int* status) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int i = perm[s];
+__global__ void k_scatter_cell(CellGeom g, const int* __restrict__ key, const int* __restrict__ rank,
+                               const int* __restrict__ start, int n, const double* __restrict__ x, int kernel,
+                               const T* __restrict__ f, int n_rhs, int* __restrict__ perm,
+                               typename Vec4<T>::type* __restrict__ xs, typename Vec4<T>::type* __restrict__ xsl,
+                               int* __restrict__ cell3, T* __restrict__ fs, int* status) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int s = start[key[i]] + rank[i];
+  perm[s] = i;
   double w[3];
   for (int d = 0; d < 3; ++d) w[d] = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
   typename Vec4<T>::type v, lo;
@@ -931,17 +951,11 @@ __global__ void k_sort_positions(CellGeom g, const double* __restrict__ x, const
       cell3[3 * s + d] = min(max(cc, 0), g.nc[d] - 1);
     }
   }
-}
-
-template <typename T>
-__global__ void k_sort_rs_strengths(int kernel, const T* __restrict__ f, const int* __restrict__ perm,
-                                    int n, int n_rhs, T* __restrict__ fs) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  int i = perm[s];
-  const int nc = kernel == SE_STRESSLET ? 6 : 3;
-  for (int r = 0; r < n_rhs; ++r)
-    for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = f[((size_t)r * n + i) * nc + c];
+  if (f) {
+    const int nc = kernel == SE_STRESSLET ? 6 : 3;
+    for (int r = 0; r < n_rhs; ++r)
+      for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = f[((size_t)r * n + i) * nc + c];
+  }
 }
 
 // ================================================================ corrections
@@ -1426,7 +1440,6 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     }
     const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
     int *sperm, *cstart;
-    SE_TRY(counting_sort(p, rs, "cell", N, ncell, cell_keyfun, src, &cg, &sperm, &cstart));
     typedef typename Vec4<T>::type V4;
     void *xs, *fs, *xsl;
     SE_TRY(buf(p, "rs.xs", sizeof(V4) * (size_t)std::max(N, 1), &xs));
@@ -1434,27 +1447,26 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     SE_TRY(buf(p, "rs.fs", sizeof(T) * C * (size_t)std::max(N, 1), &fs));
     void* tcell;
     SE_TRY(buf(p, "rs.tcell", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcell));
-    if (N > 0) {
-      ++p->launches;
-      k_sort_positions<T><<<grid1d(N, 256), 256, 0, rs>>>(cg, src, sperm, N, (V4*)xs, (V4*)xsl,
-                                                          star ? (int*)tcell : nullptr, p->d_status);
-      ++p->launches;
-      k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, rs>>>(kernel, strengths, sperm, N, n_rhs, (T*)fs);
-    }
+    SE_TRY(counting_sort(p, rs, "cell", N, ncell, cell_keyfun, src, &cg, &sperm, &cstart,
+                         [&](const int* key, const int* rank, const int* start, int* perm) {
+                           k_scatter_cell<T><<<grid1d(N, 256), 256, 0, rs>>>(
+                               cg, key, rank, start, N, src, kernel, strengths, n_rhs, perm, (V4*)xs, (V4*)xsl,
+                               star ? (int*)tcell : nullptr, (T*)fs, p->d_status);
+                         }));
     const V4* xt = (V4*)xs;
     const V4* xtl = (V4*)xsl;
     const int* tperm = sperm;
     if (!star) {
       int *tp2, *ts2;
-      SE_TRY(counting_sort(p, rs, "tcellsort", NT, ncell, cell_keyfun, tgt, &cg, &tp2, &ts2));
       void *xt2, *xtl2;
       SE_TRY(buf(p, "rs.xt", sizeof(V4) * (size_t)std::max(NT, 1), &xt2));
       SE_TRY(buf(p, "rs.xtl", sizeof(V4) * (size_t)std::max(NT, 1), &xtl2));
-      if (NT > 0) {
-        ++p->launches;
-        k_sort_positions<T><<<grid1d(NT, 256), 256, 0, rs>>>(cg, tgt, tp2, NT, (V4*)xt2, (V4*)xtl2,
-                                                             (int*)tcell, p->d_status);
-      }
+      SE_TRY(counting_sort(p, rs, "tcellsort", NT, ncell, cell_keyfun, tgt, &cg, &tp2, &ts2,
+                           [&](const int* key, const int* rank, const int* start, int* perm) {
+                             k_scatter_cell<T><<<grid1d(NT, 256), 256, 0, rs>>>(
+                                 cg, key, rank, start, NT, tgt, kernel, (const T*)nullptr, n_rhs, perm, (V4*)xt2,
+                                 (V4*)xtl2, (int*)tcell, (T*)nullptr, p->d_status);
+                           }));
       xt = (V4*)xt2;
       xtl = (V4*)xtl2;
       tperm = tp2;
@@ -1498,7 +1510,6 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   if (parts & SE_PART_FOURIER) {
     const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
     int *perm, *tstart;
-    SE_TRY(counting_sort(p, st, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart));
     void *base, *wts, *sf;
     SE_TRY(buf(p, "base", sizeof(int) * 3 * (size_t)std::max(N, 1), &base));
     SE_TRY(buf(p, "wts", sizeof(T) * 3 * g.P * (size_t)std::max(N, 1), &wts));
@@ -1511,12 +1522,13 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     wa.beta = (T)p->win.beta;
     wa.inv_i0beta = (T)(1.0 / p->win.i0beta);
     wa.pkb = (const T*)p->pkb_coef.p;
-    if (N > 0) {
-      ++p->launches;
-      k_weights<T><<<grid1d(N, 128), 128, 0, st>>>(g, wa, src, perm, N, (int*)base, (T*)wts, p->d_status);
-      ++p->launches;
-      k_sort_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, strengths, perm, N, n_rhs, (T*)sf);
-    }
+    SE_TRY(counting_sort(p, st, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart,
+                         [&](const int* key, const int* rank, const int* start, int* pm) {
+                           k_scatter_tile<T><<<grid1d(N, 128), 128, 0, st>>>(g, wa, key, rank, start, N, src,
+                                                                            kernel, strengths, n_rhs, pm,
+                                                                            (int*)base, (T*)wts, (T*)sf,
+                                                                            p->d_status);
+                         }));
     stage.mark();  // 1: bin + weights
     const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
@@ -1553,15 +1565,15 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     const T* tw = (T*)wts;
     if (!star) {
       int *perm2, *tstart2;
-      SE_TRY(counting_sort(p, st, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2));
       void *base2, *wts2;
       SE_TRY(buf(p, "tbase", sizeof(int) * 3 * (size_t)std::max(NT, 1), &base2));
       SE_TRY(buf(p, "twts", sizeof(T) * 3 * g.P * (size_t)std::max(NT, 1), &wts2));
-      if (NT > 0) {
-        ++p->launches;
-        k_weights<T><<<grid1d(NT, 128), 128, 0, st>>>(g, wa, tgt, perm2, NT, (int*)base2, (T*)wts2,
-                                                      p->d_status);
-      }
+      SE_TRY(counting_sort(p, st, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2,
+                           [&](const int* key, const int* rank, const int* start, int* pm) {
+                             k_scatter_tile<T><<<grid1d(NT, 128), 128, 0, st>>>(
+                                 g, wa, key, rank, start, NT, tgt, kernel, (const T*)nullptr, n_rhs, pm,
+                                 (int*)base2, (T*)wts2, (T*)nullptr, p->d_status);
+                           }));
       tperm = perm2;
       tbase = (int*)base2;
       tw = (T*)wts2;
@@ -1755,9 +1767,8 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   if (N == 0) return SE_OK;
   k_cell_keys<<<grid1d(N, 256), 256, 0, st>>>(cg, src, N, key, rank, count, status);
   k_scan<<<1, 1024, 0, st>>>(count, start, ncell);
-  k_scatter_perm<<<grid1d(N, 256), 256, 0, st>>>(key, rank, start, N, perm);
-  k_sort_positions<T><<<grid1d(N, 256), 256, 0, st>>>(cg, src, perm, N, xs, xsl, tcell, status);
-  k_sort_rs_strengths<T><<<grid1d(N, 256), 256, 0, st>>>(kernel, f, perm, N, 1, fs);
+  k_scatter_cell<T><<<grid1d(N, 256), 256, 0, st>>>(cg, key, rank, start, N, src, kernel, f, 1, perm, xs, xsl,
+                                                     tcell, fs, status);
   RealArgs<T> ra;
   ra.cg = cg;
   for (int d = 0; d < 3; ++d) {
