@@ -481,7 +481,7 @@ template se_status launch_scale3p<double>(se_plan_t*, int, int, double*, const S
 // ====================================================== gathering, Eq. (SE-gathering-disc)
 //
 // One warp per target: lanes cover the P x P (direction 1, 2) taps, each lane runs over the
-// P taps of direction 0; warp-shuffle reduction; u = h^3 * sum.
+// P taps of direction 0; compensated accumulation (FP32), warp-shuffle reduction; u = h^3 sum.
 
 template <typename T, int NCMAX>
 __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restrict__ perm,
@@ -511,6 +511,13 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
   const T* w1 = s_w[warp] + P;
   const T* w2 = s_w[warp] + 2 * P;
   const int* xo = s_xo[warp];
+  // FP32: each lane sums one P-term row along direction 0 in plain FP32 and adds the row sum
+  // to its accumulator with Kahan compensation (err[]); the lanes' totals then meet in a
+  // shuffle tree. FP64 accumulates directly.
+  constexpr bool kahan = sizeof(T) == 4;
+  T err[NCMAX];
+#pragma unroll
+  for (int k = 0; k < NCMAX; ++k) err[k] = T(0);
   for (int l = lane; l < P * P; l += 32) {
     const int b = l / P, c = l - b * P;
     int y = b1 + b, z = b2 + c;
@@ -518,13 +525,29 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
     if (g.periodic[2]) { if (z < 0) z += g.m[2]; else if (z >= g.m[2]) z -= g.m[2]; }
     const T wyz = w1[b] * w2[c];
     const T* Fyz = F + (y * g.n[2] + z);
+    T row[NCMAX];
+#pragma unroll
+    for (int k = 0; k < NCMAX; ++k) row[k] = T(0);
 #pragma unroll 4
     for (int a = 0; a < P; ++a) {
       const T* Fp = Fyz + xo[a];
       const T wv = w0[a] * wyz;
 #pragma unroll
       for (int k = 0; k < NCMAX; ++k)
-        if (k < NC) acc[k] += wv * Fp[(size_t)k * G];
+        if (k < NC) row[k] += wv * Fp[(size_t)k * G];
+    }
+#pragma unroll
+    for (int k = 0; k < NCMAX; ++k) {
+      if (k < NC) {
+        if (kahan) {
+          const T yv = row[k] - err[k];
+          const T t = acc[k] + yv;
+          err[k] = (t - acc[k]) - yv;
+          acc[k] = t;
+        } else {
+          acc[k] += row[k];
+        }
+      }
     }
   }
 #pragma unroll
