@@ -27,8 +27,11 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "3p_stresslet_rotlet_n20000"
-METRIC = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), 3P stresslet+rotlet, N=20000"
+WORKLOAD = "3p_stresslet_rotlet_n20000"   # default (--workload selects another configuration)
+METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
+METRIC = METRIC_FMT % "3P stresslet+rotlet, N=20000"
+METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
+                "2p_stokeslet_n200000_rhs8": "2P stokeslet, N=200000, 8 RHS"}
 UNIT = "targets/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 
@@ -87,12 +90,15 @@ class ClockSampler:
 
 
 def make_inputs():
+    """Positions (N, 3) and per-kernel strengths (n_rhs, N, c) of the selected workload."""
     from paper_2210_01255_gb300 import workloads as W
     cfg = W.CONFIGS[WORKLOAD]
-    N = cfg["N"]
+    N, R = cfg["N"], cfg.get("n_rhs", 1)
     x = W.uniform_points(N, cfg["box"], seed=cfg["seed"])
-    fs = {k: W.strengths(k, N, seed=cfg["seed"] + (0 if k == "stresslet" else 100)).astype(np.float32)
-          for k in cfg["kernels"]}
+    fs = {}
+    for k in cfg["kernels"]:
+        f = W.strengths(k, N, seed=cfg["seed"] + (0 if k == "stresslet" else 100), n_rhs=R if R > 1 else None)
+        fs[k] = np.ascontiguousarray(f.reshape(R, N, -1).astype(np.float32))
     return cfg, x, fs
 
 
@@ -100,7 +106,7 @@ def tuned(cfg, kernel, f):
     import paper_2210_01255_gb300 as se
     from paper_2210_01255_gb300 import workloads as W
     # the selection targets E <= 10 tau (Sec. 4.6); ask for tol/10 so the result meets tol
-    Q = W.source_quantity(kernel, f)
+    Q = W.source_quantity(kernel, f[0])
     o = se.se_opts_default()
     o.n_rc = cfg.get("n_rc", {}).get(kernel, 0.0)
     return se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[kernel], Q, cfg["N"], cfg["tol"] / 10.0, opts=o)
@@ -140,7 +146,7 @@ def oracle_sample(cfg, x, fs, nsample, seed=7):
     idx = np.random.default_rng(seed).choice(cfg["N"], nsample, replace=False)
     out, t0 = {}, time.perf_counter()
     for k in cfg["kernels"]:
-        out[k] = E.potential(cfg["D"], list(cfg["box"]), k, x, fs[k].astype(np.float64), targets=x[idx])
+        out[k] = E.potential(cfg["D"], list(cfg["box"]), k, x, fs[k][0].astype(np.float64), targets=x[idx])
     return idx, out, time.perf_counter() - t0
 
 
@@ -165,7 +171,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": cfg["N"], "box": list(cfg["box"]),
-                       "kernels": list(cfg["kernels"]), "tol_rel": cfg["tol"], "parallelism": "replicas"},
+                       "kernels": list(cfg["kernels"]), "tol_rel": cfg["tol"], "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d sampled targets x %d kernels per step, all N sources" %
                                        (ns, len(cfg["kernels"]))},
@@ -175,6 +181,7 @@ def run_reference(args):
 
 
 def main():
+    global WORKLOAD, METRIC
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -182,9 +189,13 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(METRIC_NAMES),
+                    help="configuration from paper_2210_01255_gb300.workloads.CONFIGS")
     ap.add_argument("--gridding", choices=["cuda", "tc"], default="cuda",
                     help="FP32 gridding on the CUDA cores (default) or the tensor cores (tcgen05)")
     args = ap.parse_args()
+    WORKLOAD = args.workload
+    METRIC = METRIC_FMT % METRIC_NAMES[WORKLOAD]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -202,7 +213,7 @@ def main():
     dev = torch.device("cuda", local)
 
     cfg, x, fs = make_inputs()
-    N = cfg["N"]
+    N, R = cfg["N"], cfg.get("n_rhs", 1)
     stream = torch.cuda.current_stream()
     plans, fdev, params = {}, {}, {}
     for k in cfg["kernels"]:
@@ -213,8 +224,9 @@ def main():
         plans[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp32",
                            opts=o, stream=stream)
         fdev[k] = torch.tensor(fs[k], device=dev)
+    grid_n = {k: list(plans[k].info().n) for k in cfg["kernels"]}
     xdev = torch.tensor(x, device=dev)
-    udev = {k: torch.empty((1, N, 3), dtype=torch.float32, device=dev) for k in cfg["kernels"]}
+    udev = {k: torch.empty((R, N, 3), dtype=torch.float32, device=dev) for k in cfg["kernels"]}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
@@ -249,7 +261,7 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    targets_per_step = N * len(cfg["kernels"])
+    targets_per_step = N * R * len(cfg["kernels"])  # (target, RHS) evaluations per step
     # FP32 batched: both evaluations of a step captured into one CUDA graph (se_batch_*) on a
     # stream of their own and replayed; L2 flushed between replays, timed with events
     graph = None
@@ -262,10 +274,10 @@ def main():
             o.flags = se.FLAG_TC_GRIDDING if args.gridding == "tc" else 0
             gplans[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp32",
                                 opts=o, stream=gstream)
-            gu[k] = torch.empty((1, N, 3), dtype=torch.float32, device=dev)
+            gu[k] = torch.empty((R, N, 3), dtype=torch.float32, device=dev)
         ks = list(cfg["kernels"])
         bh = se.se_batch_create([gplans[k].handle for k in ks], [se.KERNELS[k] for k in ks], [xdev] * len(ks),
-                                [fdev[k] for k in ks], [1] * len(ks), [gu[k] for k in ks])
+                                [fdev[k] for k in ks], [R] * len(ks), [gu[k] for k in ks])
         for _ in range(max(3, args.warmup)):
             se.se_batch_launch(bh)
         gstream.synchronize()
@@ -303,14 +315,22 @@ def main():
     # ---- dominant kernel and its roofline
     names = ["bin", "spread", "fft", "scale", "ifft", "gather", "real", "corr"]
     per_stage = {n: sum(stage_ms[k][i] for k in cfg["kernels"]) / args.steps for i, n in enumerate(names)}
-    work = {}
+    work, hbm = {}, {}
     for k in cfg["kernels"]:
         P = params[k]["P"]
-        C = 6 if k == "stresslet" else 3
+        C = (6 if k == "stresslet" else 3) * R
+        G = float(np.prod(grid_n[k]))
+        H = float(grid_n[k][0] * grid_n[k][1] * (grid_n[k][2] // 2 + 1))
         work.setdefault("spread", 0.0)
         work["spread"] += 2.0 * N * P ** 3 * C        # one FMA per tap per component
         work.setdefault("gather", 0.0)
-        work["gather"] += 2.0 * N * P ** 3 * 3
+        work["gather"] += 2.0 * N * P ** 3 * 3 * R
+        # algorithmic HBM bytes: spread N (24 + 4 C) + 4 G C; gather 4 G 3R + 12 N R;
+        # k-space multiply (3P) (C + 3R) x 8 B per half-spectrum mode
+        hbm["spread"] = hbm.get("spread", 0.0) + N * (24 + 4 * C) + 4 * G * C
+        hbm["gather"] = hbm.get("gather", 0.0) + 4 * G * 3 * R + 12 * N * R
+        if cfg["D"] == 3:
+            hbm["scale"] = hbm.get("scale", 0.0) + (C + 3 * R) * 8 * H
     # real space: pairs within rc for the uniform density of this workload, 60 flops per pair
     vol = float(np.prod(cfg["box"]))
     work["real"] = sum(60.0 * N * (N - 1) / vol * 4.0 / 3.0 * math.pi * params[k]["rc"] ** 3
@@ -323,20 +343,24 @@ def main():
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived from unit counts and "
                            "the maximum SM clock)"}
     roof["per_stage_tflops"] = {k: work[k] / (per_stage[k] * 1e-3) / 1e12 for k in work if per_stage[k] > 0}
+    pk = peaks()
+    roof["per_stage_hbm"] = {k: {"algorithmic_bytes": hbm[k], "achieved_gbs": hbm[k] / (per_stage[k] * 1e-3) / 1e9,
+                                 "frac_of_measured_peak": hbm[k] / (per_stage[k] * 1e-3) / 1e9 / pk["hbm_gbs"]}
+                             for k in hbm if per_stage[k] > 0}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
     e2e = None
     if rank == 0 or True:
         xh = np.ascontiguousarray(x)
-        uh = {k: np.empty((N, 3), dtype=np.float32) for k in cfg["kernels"]}
+        uh = {k: np.empty((R, N, 3), dtype=np.float32) for k in cfg["kernels"]}
         fh = {k: np.ascontiguousarray(fs[k]) for k in cfg["kernels"]}
         for _ in range(2):
             for k in cfg["kernels"]:
-                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], 1, None, uh[k])
+                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], R, None, uh[k])
         t0 = time.perf_counter()
         for _ in range(args.steps):
             for k in cfg["kernels"]:
-                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], 1, None, uh[k])
+                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], R, None, uh[k])
         dt = time.perf_counter() - t0
         h2d = sum(xh.nbytes + fh[k].nbytes for k in cfg["kernels"])
         d2h = sum(uh[k].nbytes for k in cfg["kernels"])
@@ -356,7 +380,8 @@ def main():
 
         def step64():
             for k in cfg["kernels"]:
-                plans64[k].evaluate(k, xdev, f64[k], out=u64[k])
+                for r in range(R):
+                    plans64[k].evaluate(k, xdev, f64[k][r], out=u64[k])
 
         for _ in range(3):
             step64()
@@ -385,7 +410,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": g_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "box": list(cfg["box"]), "kernels": list(cfg["kernels"]),
+            "config": {"workload": WORKLOAD, "N": N, "n_rhs": R, "box": list(cfg["box"]),
+                       "kernels": list(cfg["kernels"]), "periodicity": cfg["D"],
                        "tol_rel": cfg["tol"], "window": cfg["window"], "params": params,
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "gridding": "tcgen05" if args.gridding == "tc" else "cuda cores",
@@ -395,7 +421,7 @@ def main():
 
     # ---- CPU baseline (rank 0, N = 1): the oracle on a bounded sample; also the GPU error there
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = 16
+        ns = 16 if N <= 50000 else 2  # a bounded sample: ~10-30 s of oracle work
         idx, ref, dt = oracle_sample(cfg, x, fs, ns)
         err = {}
         from oracle import ewald as E
@@ -403,7 +429,7 @@ def main():
             err[k] = E.rms_rel(udev[k][0].cpu().numpy()[idx].astype(np.float64), ref[k])
         line["cpu_baseline"] = {"value": ns * len(cfg["kernels"]) / dt, "unit": UNIT, "cores": os.cpu_count(),
                                 "kind": "oracle",
-                                "sample": "%d sampled targets x %d kernels against all %d sources" %
+                                "sample": "%d sampled targets x %d kernels (RHS 0) against all %d sources" %
                                           (ns, len(cfg["kernels"]), N)}
         line["rms_rel_err_vs_oracle"] = err
     if rank == 0:

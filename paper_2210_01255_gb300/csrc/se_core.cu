@@ -1373,19 +1373,19 @@ se_status spread_launch(se_plan_t* p, const int* tile_start, const int* base, co
     return spread_tc_launch(p, tile_start, base, (const float*)w, (const float*)sf, C, (float*)grid);
   // deal the source tiles of each output tile over nslab CTAs so that the grid has enough
   // CTAs to fill the GPU; the partial tiles are then added atomically into a zeroed grid.
-  // Components go in groups that fit the registers (24 floats or 12 doubles per grid point).
+  // Components go in groups that keep the register accumulators small enough for several
+  // CTAs per SM (12 floats or 6 doubles per grid point; 24 halved the rate at 8 RHS).
   const GridGeom& g = p->geom;
   const long long tiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
   int nslab = (int)std::min<long long>(9, std::max<long long>(1, (16LL * 152 + tiles - 1) / tiles));
   const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
   if (nslab > 1) cudaMemsetAsync(grid, 0, sizeof(T) * C * G, p->stream);
-  const int CG = sizeof(T) == 4 ? 24 : 12;
+  const int CG = sizeof(T) == 4 ? 12 : 6;
   for (int c0 = 0; c0 < C; c0 += CG) {
     const int Cc = std::min(CG, C - c0);
     if (Cc <= 3) spread_launch_group<T, 3>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
     else if (Cc <= 6) spread_launch_group<T, 6>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
-    else if (Cc <= 12) spread_launch_group<T, 12>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
-    else spread_launch_group<T, 24>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
+    else spread_launch_group<T, 12>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
   }
   return SE_OK;
 }
@@ -1603,11 +1603,16 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     }
     const T scale = (T)(g.h * g.h * g.h);
     if (NT > 0) {
-      if (NC <= 3) gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
-      else if (NC <= 6) gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
-      else if (NC <= 12) gather_launch<T, 12>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
-      else if (NC <= 24) gather_launch<T, 24>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
-      else gather_launch<T, 48>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      // more than 2 RHS: groups of 6 components (2 RHS) per launch keep the per-lane
+      // accumulators in registers (one launch over all 3 n_rhs components halved the rate)
+      if (NC <= 3) {
+        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+      } else {
+        const size_t GG = (size_t)g.n[0] * g.n[1] * g.n[2];
+        for (int c0 = 0; c0 < NC; c0 += 6)
+          gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), scale,
+                              u + (size_t)(c0 / 3) * NT * 3);
+      }
     }
     SE_CUDA(cudaGetLastError());
     stage.mark();  // 6: gather
