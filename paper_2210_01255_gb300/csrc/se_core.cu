@@ -1324,6 +1324,7 @@ se_status get_fft(se_plan_t* p, bool forward, int batch, cufftHandle* out) {
   auto& mp = forward ? *p->fwd : *p->inv;
   auto it = mp.find(batch);
   if (it != mp.end()) {
+    SE_CUFFT(cufftSetStream(it->second, p->stream));  // the stream the caller issues on now
     *out = it->second;
     return SE_OK;
   }
@@ -1860,7 +1861,16 @@ struct se_batch_t {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int n_cfg = 0;
+  std::vector<cudaStream_t> branch;  // capture branches (kept for the graph's lifetime)
 };
+
+static void batch_free(se_batch_t* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  delete b;
+}
 
 extern "C" se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h* plans, const int* kernel_mask,
                                      const long long* n_src, const double* const* src,
@@ -1887,21 +1897,47 @@ extern "C" se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h
     cudaGetLastError();
     return SE_ERR_CUDA;
   }
+  // The configurations are independent: each is captured on one of up to kMaxBranch branch
+  // streams forked from and joined to the capture stream, so the graph runs them as parallel
+  // branches (configuration i on branch i mod nbr, in order within a branch). Every plan owns
+  // its buffers, cuFFT plans (bound to the plan's current stream at each call) and side
+  // stream, so concurrent branches share no state.
+  constexpr int kMaxBranch = 16;
+  const int nbr = std::min(n_cfg, kMaxBranch);
+  std::vector<cudaStream_t> bs(nbr, nullptr);
+  std::vector<cudaEvent_t> ev(nbr + 1, nullptr);
   se_status s = SE_OK;
-  for (int i = 0; i < n_cfg && s == SE_OK; ++i)
-    s = se_eval(plans[i], kernel_mask[i], n_src[i], src[i], strengths[i], n_rhs[i], 0, nullptr, u[i]);
+  for (int k = 0; k < nbr && s == SE_OK; ++k)
+    if (cudaStreamCreateWithFlags(&bs[k], cudaStreamNonBlocking) != cudaSuccess) s = SE_ERR_CUDA;
+  for (int k = 0; k <= nbr && s == SE_OK; ++k)
+    if (cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) != cudaSuccess) s = SE_ERR_CUDA;
+  if (s == SE_OK && cudaEventRecord(ev[nbr], st) != cudaSuccess) s = SE_ERR_CUDA;
+  for (int k = 0; k < nbr && s == SE_OK; ++k)
+    if (cudaStreamWaitEvent(bs[k], ev[nbr], 0) != cudaSuccess) s = SE_ERR_CUDA;
+  for (int i = 0; i < n_cfg && s == SE_OK; ++i) {
+    se_plan_t* pl = plans[i];
+    const cudaStream_t own = pl->stream;
+    pl->stream = bs[i % nbr];
+    s = se_eval(pl, kernel_mask[i], n_src[i], src[i], strengths[i], n_rhs[i], 0, nullptr, u[i]);
+    pl->stream = own;
+  }
+  for (int k = 0; k < nbr && s == SE_OK; ++k)
+    if (cudaEventRecord(ev[k], bs[k]) != cudaSuccess || cudaStreamWaitEvent(st, ev[k], 0) != cudaSuccess)
+      s = SE_ERR_CUDA;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &g);
+  for (int k = 0; k <= nbr; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  b->branch = bs;
   if (s != SE_OK || e != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
-    delete b;
+    batch_free(b);
     cudaGetLastError();
     return s != SE_OK ? s : SE_ERR_CUDA;
   }
   b->graph = g;
   if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
-    cudaGraphDestroy(g);
-    delete b;
+    batch_free(b);
     cudaGetLastError();
     return SE_ERR_CUDA;
   }
@@ -1917,7 +1953,5 @@ extern "C" se_status se_batch_launch(se_batch_h b) {
 
 extern "C" void se_batch_destroy(se_batch_h b) {
   if (!b) return;
-  if (b->exec) cudaGraphExecDestroy(b->exec);
-  if (b->graph) cudaGraphDestroy(b->graph);
-  delete b;
+  batch_free(b);
 }

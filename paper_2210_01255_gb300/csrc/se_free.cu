@@ -587,6 +587,7 @@ se_status free_fft(se_plan_t* p, int tag, int batch, int rank, const int* n, int
   int key = (tag << 20) ^ batch;
   auto it = p->fwd->find(-1 - key);
   if (it != p->fwd->end()) {
+    SE_CUFFT(cufftSetStream(it->second, p->stream));  // the stream the caller issues on now
     *out = it->second;
     return SE_OK;
   }
