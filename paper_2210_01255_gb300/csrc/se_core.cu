@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
   __shared__ __align__(16) T s_w[CH][3 * TS];
   __shared__ T s_f[CH][CMAX];
   __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
-  __shared__ int s_list[CH], s_wcnt[2];
+  __shared__ int s_list[CH], s_xh[CH], s_wcnt[2];
   const int P = g.P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lz = tid & 7, ly = tid >> 3;
@@ -339,7 +339,13 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
       if (lane == 0) s_wcnt[warp] = __popc(bal);
       __syncthreads();
       const int nreach = s_wcnt[0] + s_wcnt[1];
-      if (reach) s_list[(warp ? s_wcnt[0] : 0) + __popc(bal & ((1u << lane) - 1u))] = p0 + tid;
+      if (reach) {
+        // which halves of the tile's 8 points along direction 0 the support touches
+        const int pos = (warp ? s_wcnt[0] : 0) + __popc(bal & ((1u << lane) - 1u));
+        const int s0 = base[3 * (size_t)(p0 + tid)] + rel0;
+        s_list[pos] = p0 + tid;
+        s_xh[pos] = (s0 < TS / 2 ? 1 : 0) | (s0 + P > TS / 2 ? 2 : 0);
+      }
       __syncthreads();
       for (int idx = tid; idx < nreach * 3 * TS; idx += 64) {
         const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
@@ -357,15 +363,23 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
       for (int pp = 0; pp < nreach; ++pp) {
         const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
         if (wyz != T(0)) {
-          T wx[TS];
+          // many components: skip the half of the x points the support misses (the same for
+          // every thread: no divergence); few components: the test costs more than it saves
+          const int xh = CMAX >= 12 ? s_xh[pp] : 3;
 #pragma unroll
-          for (int xx = 0; xx < TS; ++xx) wx[xx] = s_w[pp][xx] * wyz;
+          for (int hf = 0; hf < 2; ++hf) {
+            if (xh & (1 << hf)) {
+              T wx[TS / 2];
 #pragma unroll
-          for (int c = 0; c < CMAX; ++c) {
-            if (c < C) {
-              const T fv = s_f[pp][c];
+              for (int xx = 0; xx < TS / 2; ++xx) wx[xx] = s_w[pp][hf * (TS / 2) + xx] * wyz;
 #pragma unroll
-              for (int xx = 0; xx < TS; ++xx) acc[xx][c] += wx[xx] * fv;
+              for (int c = 0; c < CMAX; ++c) {
+                if (c < C) {
+                  const T fv = s_f[pp][c];
+#pragma unroll
+                  for (int xx = 0; xx < TS / 2; ++xx) acc[hf * (TS / 2) + xx][c] += wx[xx] * fv;
+                }
+              }
             }
           }
         }
