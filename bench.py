@@ -89,6 +89,22 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (each rank times its own replica; the job ends with the last)."""
+    if dist is None:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(targets_per_step, world, steps, ms_max):
+    """Whole-job throughput of `world` replicas (weak scaling): every rank's targets over the
+    slowest rank's time."""
+    return targets_per_step * world * steps / (ms_max / 1e3)
+
+
 def make_inputs():
     """Positions (N, 3) and per-kernel strengths (n_rhs, N, c) of the selected workload."""
     from paper_2210_01255_gb300 import workloads as W
@@ -305,12 +321,8 @@ def main():
     clocks = sampler.stop()
     for p in plans.values():
         se.se_set_timing(p.handle, False)
-    tot_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist:
-        t = torch.tensor([tot_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = targets_per_step * world * args.steps / (tot_ms / 1e3)
+    tot_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
+    value = replica_value(targets_per_step, world, args.steps, tot_ms)
 
     # ---- dominant kernel and its roofline
     names = ["bin", "spread", "fft", "scale", "ifft", "gather", "real", "corr"]
@@ -402,11 +414,8 @@ def main():
     # eager per-call form, whose per-kernel events give the stage times and the roofline, beside it
     eager = {"value": value, "unit": UNIT, "ms_per_step": tot_ms / args.steps,
              "form": "FP32, one se_eval call per kernel per step"}
-    gtimes = torch.tensor([graph["ms_per_step"] * args.steps], device=dev)
-    if dist:
-        dist.all_reduce(gtimes, op=dist.ReduceOp.MAX)
-    g_ms = float(gtimes.item())
-    value = targets_per_step * world * args.steps / (g_ms / 1e3)
+    g_ms = max_over_ranks(graph["ms_per_step"] * args.steps, dist, dev)
+    value = replica_value(targets_per_step, world, args.steps, g_ms)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": g_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
