@@ -125,6 +125,7 @@ def tuned(cfg, kernel, f):
     Q = W.source_quantity(kernel, f[0])
     o = se.se_opts_default()
     o.n_rc = cfg.get("n_rc", {}).get(kernel, 0.0)
+    o.P_margin = cfg.get("P_margin", -1)
     return se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[kernel], Q, cfg["N"], cfg["tol"] / 10.0, opts=o)
 
 
@@ -172,7 +173,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg, x, fs = make_inputs()
-    ns = 8
+    ns = 512 if cfg["N"] <= 50000 else 32  # targets per step: ~1-2 s of oracle work
     for _ in range(args.warmup):
         oracle_sample(cfg, x, fs, ns, seed=11)
     tot = 0.0
@@ -422,6 +423,8 @@ def main():
             "config": {"workload": WORKLOAD, "N": N, "n_rhs": R, "box": list(cfg["box"]),
                        "kernels": list(cfg["kernels"]), "periodicity": cfg["D"],
                        "tol_rel": cfg["tol"], "window": cfg["window"], "params": params,
+                       "selection": {"n_rc": cfg.get("n_rc"), "P_margin": cfg.get("P_margin", -1),
+                                     "tol_requested": cfg["tol"] / 10.0},
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "gridding": "tcgen05" if args.gridding == "tc" else "cuda cores",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -430,7 +433,9 @@ def main():
 
     # ---- CPU baseline (rank 0, N = 1): the oracle on a bounded sample; also the GPU error there
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ns = 16 if N <= 50000 else 2  # a bounded sample: ~10-30 s of oracle work
+        # a bounded sample (a few seconds of oracle work); the oracle's per-call cost (the
+        # k-space structure factors) is amortised over the sample's targets
+        ns = 1024 if N <= 50000 else 64
         idx, ref, dt = oracle_sample(cfg, x, fs, ns)
         err = {}
         from oracle import ewald as E

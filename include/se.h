@@ -80,6 +80,9 @@ typedef struct {
   int flags;         /* SE_FLAG_* bits, 0 = defaults                                        */
   double n_rc;       /* se_autotune: average neighbours within r_c used to choose xi when
                         *xi_io <= 0 (Sec. 5.2); 0 = the paper's uniform-case values (Table 5) */
+  int P_margin;      /* se_autotune: window points added to the estimate of Eq.
+                        (approximation-estimate) by the error-pollution rule, Eq.
+                        (error-pollution-fix); -1 = the paper's (4, or 2 for D = 0)          */
 } se_opts;
 
 /* se_opts.flags: with SE_FLAG_TC_GRIDDING, FP32 gridding (Alg. 1, gridding step) with window

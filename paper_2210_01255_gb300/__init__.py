@@ -37,7 +37,7 @@ class se_opts(ctypes.Structure):
                 ("Mext", ctypes.c_int * 3), ("s0", ctypes.c_double), ("s_star", ctypes.c_double),
                 ("kbar_star", ctypes.c_int), ("tol_abs", ctypes.c_double), ("Q", ctypes.c_double),
                 ("kernel_mask", ctypes.c_int), ("stream", ctypes.c_void_p), ("flags", ctypes.c_int),
-                ("n_rc", ctypes.c_double)]
+                ("n_rc", ctypes.c_double), ("P_margin", ctypes.c_int)]
 
 
 class se_info(ctypes.Structure):

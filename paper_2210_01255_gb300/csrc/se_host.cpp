@@ -233,7 +233,7 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
   double h_est = M_PI / kinf;
   // step 4: error-pollution rule, Eq. (error-pollution-fix), then Eq. (grid-adjustment)
   double h_t = D == 0 ? h_est / 1.1 : h_est / 1.05;
-  double P_t = D == 0 ? Pest + 2.0 : Pest + 4.0;
+  double P_t = Pest + (io->P_margin >= 0 ? (double)io->P_margin : (D == 0 ? 2.0 : 4.0));
   // isotropic h: the first periodic direction (or direction 0 for D = 0) fixes h
   int M[3] = {0, 0, 0};
   M[0] = fM * (int)std::ceil(box[0] / h_t / fM);
@@ -334,5 +334,6 @@ extern "C" se_status se_opts_default(se_opts* o) {
   o->prec = SE_FP64;
   o->f_M = 4;
   o->kbar_star = -1;
+  o->P_margin = -1;
   return SE_OK;
 }

@@ -70,3 +70,18 @@ def test_autotune_rules():
     Mext = r0["opts"].Mext[0]
     assert Mext == 4 * math.ceil((M + P + 1.2 * max(P, 8)) / 4)
     assert abs(r0["opts"].s0 - math.ceil(10 * (1 + math.sqrt(3))) / 10) < 1e-12
+
+
+def test_window_margin_option():
+    """se_opts.P_margin: -1 (default) is the paper's error-pollution rule (+4 points for D >= 1,
+    +2 for D = 0); 0 keeps the bare estimate of Eq. (approximation-estimate)."""
+    import paper_2210_01255_gb300 as se
+    for D, margin in ((3, 4), (2, 4), (0, 2)):
+        o = se.se_opts_default()
+        assert o.P_margin == -1
+        t_paper = se.se_autotune(D, (1.0, 1.0, 1.0), se.STOKESLET, 3000.0, 1000, 1e-8, opts=o)
+        o0 = se.se_opts_default()
+        o0.P_margin = 0
+        t_bare = se.se_autotune(D, (1.0, 1.0, 1.0), se.STOKESLET, 3000.0, 1000, 1e-8, opts=o0)
+        assert t_paper["P"] - t_bare["P"] in (margin, margin + 2, margin - 2)  # even rounding
+        assert t_paper["P"] > t_bare["P"]
