@@ -303,7 +303,10 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
   __shared__ __align__(16) T s_w[CH][3 * TS];
   __shared__ T s_f[CH][CMAX];
   __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
-  __shared__ int s_list[CH], s_xh[CH], s_wcnt[2];
+  // reaching points not yet spread: (index, first tap - tile origin per direction); < CH
+  // carried over plus one candidate pass of CH
+  __shared__ int4 s_pend[2 * CH];
+  __shared__ int s_wcnt[2];
   const int P = g.P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int lz = tid & 7, ly = tid >> 3;
@@ -319,6 +322,54 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
   __syncthreads();
   const int nbx = s_nb[0], nby = s_nb[1], nbz = s_nb[2];
   const int nbins = nbx * nby * nbz;
+  // spread the first n pending points (n <= CH); uniform
+  auto spread_pending = [&](int n) {
+    for (int idx = tid; idx < n * 3 * TS; idx += 64) {
+      const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
+      const int d = r / TS, l = r - d * TS;
+      const int4 pe = s_pend[pp];
+      const int q = l - (d == 0 ? pe.y : (d == 1 ? pe.z : pe.w));
+      s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)pe.x * 3 + d) * P + q] : T(0);
+    }
+    for (int idx = tid; idx < n * C; idx += 64) {
+      const int pp = idx / C, c = idx - pp * C;
+      s_f[pp][c] = sf[(size_t)s_pend[pp].x * Ctot + c0 + c];
+    }
+    __syncthreads();
+    for (int pp = 0; pp < n; ++pp) {
+      const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
+      if (wyz != T(0)) {
+        // many components: skip the half of the x points the support misses (the same for
+        // every thread: no divergence); few components: the test costs more than it saves
+        int xh = 3;
+        if (CMAX >= 12) {
+          const int s0 = s_pend[pp].y;
+          xh = (s0 < TS / 2 ? 1 : 0) | (s0 + P > TS / 2 ? 2 : 0);
+        }
+#pragma unroll
+        for (int hf = 0; hf < 2; ++hf) {
+          if (xh & (1 << hf)) {
+            T wx[TS / 2];
+#pragma unroll
+            for (int xx = 0; xx < TS / 2; ++xx) wx[xx] = s_w[pp][hf * (TS / 2) + xx] * wyz;
+#pragma unroll
+            for (int c = 0; c < CMAX; ++c) {
+              if (c < C) {
+                const T fv = s_f[pp][c];
+#pragma unroll
+                for (int xx = 0; xx < TS / 2; ++xx) acc[hf * (TS / 2) + xx][c] += wx[xx] * fv;
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  };
+  // stream the source bins: keep the points whose support [base + rel, base + rel + P) meets
+  // the tile [0, TS) in all three directions (a source tile is reached only in part),
+  // collected across bins so that every staged chunk is full
+  int npend = 0;
   for (int ib = slab; ib < nbins; ib += nslab) {
     const int ix = ib / (nby * nbz), iy = (ib / nbz) % nby, iz = ib % nbz;
     const int bin = (s_bin[0][ix] * g.ntile[1] + s_bin[1][iy]) * g.ntile[2] + s_bin[2][iz];
@@ -326,66 +377,34 @@ __global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict
     const int rel0 = s_sh[0][ix] - o[0], rel1 = s_sh[1][iy] - o[1], rel2 = s_sh[2][iz] - o[2];
     for (int p0 = beg; p0 < end; p0 += CH) {
       const int cnt = min(CH, end - p0);
-      __syncthreads();
-      // keep the points of the chunk whose support [base + rel, base + rel + P) meets the
-      // tile [0, TS) in all three directions (a source tile is reached only in part)
       bool reach = false;
+      int s0 = 0, s1 = 0, s2 = 0;
       if (tid < cnt) {
         const int* bp = base + 3 * (size_t)(p0 + tid);
-        const int s0 = bp[0] + rel0, s1 = bp[1] + rel1, s2 = bp[2] + rel2;
+        s0 = bp[0] + rel0;
+        s1 = bp[1] + rel1;
+        s2 = bp[2] + rel2;
         reach = s0 < TS && s0 + P > 0 && s1 < TS && s1 + P > 0 && s2 < TS && s2 + P > 0;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, reach);
       if (lane == 0) s_wcnt[warp] = __popc(bal);
       __syncthreads();
-      const int nreach = s_wcnt[0] + s_wcnt[1];
-      if (reach) {
-        // which halves of the tile's 8 points along direction 0 the support touches
-        const int pos = (warp ? s_wcnt[0] : 0) + __popc(bal & ((1u << lane) - 1u));
-        const int s0 = base[3 * (size_t)(p0 + tid)] + rel0;
-        s_list[pos] = p0 + tid;
-        s_xh[pos] = (s0 < TS / 2 ? 1 : 0) | (s0 + P > TS / 2 ? 2 : 0);
-      }
+      const int w0c = s_wcnt[0], tot = w0c + s_wcnt[1];
+      if (reach) s_pend[npend + (warp ? w0c : 0) + __popc(bal & ((1u << lane) - 1u))] = make_int4(p0 + tid, s0, s1, s2);
+      npend += tot;
       __syncthreads();
-      for (int idx = tid; idx < nreach * 3 * TS; idx += 64) {
-        const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
-        const int d = r / TS, l = r - d * TS;
-        const int rel = d == 0 ? rel0 : (d == 1 ? rel1 : rel2);
-        const int gp = s_list[pp];
-        const int q = l - (base[3 * gp + d] + rel);
-        s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)gp * 3 + d) * P + q] : T(0);
-      }
-      for (int idx = tid; idx < nreach * C; idx += 64) {
-        const int pp = idx / C, c = idx - pp * C;
-        s_f[pp][c] = sf[(size_t)s_list[pp] * Ctot + c0 + c];
-      }
-      __syncthreads();
-      for (int pp = 0; pp < nreach; ++pp) {
-        const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
-        if (wyz != T(0)) {
-          // many components: skip the half of the x points the support misses (the same for
-          // every thread: no divergence); few components: the test costs more than it saves
-          const int xh = CMAX >= 12 ? s_xh[pp] : 3;
-#pragma unroll
-          for (int hf = 0; hf < 2; ++hf) {
-            if (xh & (1 << hf)) {
-              T wx[TS / 2];
-#pragma unroll
-              for (int xx = 0; xx < TS / 2; ++xx) wx[xx] = s_w[pp][hf * (TS / 2) + xx] * wyz;
-#pragma unroll
-              for (int c = 0; c < CMAX; ++c) {
-                if (c < C) {
-                  const T fv = s_f[pp][c];
-#pragma unroll
-                  for (int xx = 0; xx < TS / 2; ++xx) acc[hf * (TS / 2) + xx][c] += wx[xx] * fv;
-                }
-              }
-            }
-          }
-        }
+      if (npend >= CH) {
+        spread_pending(CH);
+        npend -= CH;  // move the rest (< CH) to the front
+        int4 v = make_int4(0, 0, 0, 0);
+        if (tid < npend) v = s_pend[CH + tid];
+        __syncthreads();
+        if (tid < npend) s_pend[tid] = v;
+        __syncthreads();
       }
     }
   }
+  if (npend > 0) spread_pending(npend);
   const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
   const int y = o[1] + ly, z = o[2] + lz;
   if (y < g.m[1] && z < g.m[2]) {
