@@ -429,11 +429,8 @@ se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, con
                        int Ctot, int c0, int C, float* grid) {
   const GridGeom& g = p->geom;
   const size_t smem = sizeof(TcSmem<Z, CG>);
-  static bool attr_set = false;  // per instantiation; the attribute is per function and device
-  if (!attr_set) {
-    SE_CUDA(cudaFuncSetAttribute(k_spread_tc<Z, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr_set = true;
-  }
+  // per function and device; set at every launch (a host-side call, cheap, thread-safe)
+  SE_CUDA(cudaFuncSetAttribute(k_spread_tc<Z, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const int t0 = cdiv(g.m[0], TC_X), t1 = cdiv(g.m[1], TC_Y), t2 = cdiv(g.m[2], Z);
   const long long tiles = (long long)t0 * t1 * t2;
   // two CTAs fit an SM; split the source bins of a tile over nslab CTAs when the tiles
