@@ -724,9 +724,9 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
 //     the cells that can hold sources within rc, split at periodic images into contiguous
 //     source ranges, "segments") are set up one column per lane, all cstart loads in flight
 //     at once; a warp scan lays the segments out as one flat candidate list.
-// (2) Candidates: the warp walks the flat list U x 32 at a time (U = 4 independent loads per
-//     lane in FP32, 2 in FP64), tests them on the hi parts and compacts the ones inside rc (ballot + popc)
-//     into a per-warp ring of pairs.
+// (2) Candidates: the warp walks the flat list U x 32 at a time (U = 2 independent loads per
+//     lane), tests them on the hi parts and compacts the ones inside rc (ballot + popc) into a
+//     per-warp ring of pairs.
 // (3) Pairs: whenever 32 are queued they are evaluated one per lane with the exact hi + lo
 //     separation. Lane partial sums are combined by shuffles.
 // More than 32 columns (or more segments than the table holds) are done in rounds.
@@ -735,7 +735,7 @@ constexpr int RS_SEGCAP = 64;  // column segments per round
 constexpr int RS_RING = 256;   // pair ring entries (power of two, >= 32 (RS_U + 1))
 template <typename T>
 struct RsU {  // candidate chunks of 32 in flight per lane
-  static constexpr int value = sizeof(T) == 4 ? 4 : 2;
+  static constexpr int value = 2;  // 4 in FP32 measured 5 % slower (registers, occupancy)
 };
 
 template <typename T>
