@@ -17,7 +17,8 @@ WIN_GAUSSIAN, WIN_KB, WIN_PKB = 0, 1, 2
 FP64, FP32 = 0, 1
 PART_REAL, PART_FOURIER, PART_CORR, PART_ALL = 1, 2, 4, 7
 FLAG_TC_GRIDDING = 1  # se_opts.flags: FP32 gridding (P <= 16) on the tensor cores (tcgen05)
-KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET}
+KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
+           "stokeslet+stresslet": STOKESLET | STRESSLET}
 WINDOWS = {"gaussian": WIN_GAUSSIAN, "kb": WIN_KB, "pkb": WIN_PKB}
 
 SE_OK = 0

@@ -238,9 +238,21 @@ __device__ __forceinline__ void put_weights(const GridGeom& g, const WinArgs<T>&
   }
 }
 
-// spread components of point i at sorted slot s: S, Omega: f per RHS; T: the 6 symmetric
-// components (q_l nu_m + q_m nu_l)/2 in the order 11,22,33,12,13,23 (the stresslet operator is
-// fully symmetric, Eq. stokes-kernels, so only the symmetric part of f_lm contributes)
+// the 6 symmetric components (q_l nu_m + q_m nu_l)/2 of the stresslet source, in the order
+// 11,22,33,12,13,23 (the stresslet operator is fully symmetric, Eq. stokes-kernels, so only
+// the symmetric part of f_lm contributes)
+template <typename T>
+__device__ __forceinline__ void put_sym6(const T* __restrict__ q, const T* __restrict__ nu, T* __restrict__ o) {
+  o[0] = q[0] * nu[0];
+  o[1] = q[1] * nu[1];
+  o[2] = q[2] * nu[2];
+  o[3] = T(0.5) * (q[0] * nu[1] + q[1] * nu[0]);
+  o[4] = T(0.5) * (q[0] * nu[2] + q[2] * nu[0]);
+  o[5] = T(0.5) * (q[1] * nu[2] + q[2] * nu[1]);
+}
+
+// spread components of point i at sorted slot s, per RHS: S, Omega: f; T: the 6 symmetric
+// components of q nu^T; S|T: f followed by those 6
 template <typename T>
 __device__ __forceinline__ void put_spread_strengths(int kernel, const T* __restrict__ f, int n, int n_rhs, int i,
                                                      int s, T* __restrict__ sf) {
@@ -248,14 +260,17 @@ __device__ __forceinline__ void put_spread_strengths(int kernel, const T* __rest
     const int C = 6 * n_rhs;
     for (int r = 0; r < n_rhs; ++r) {
       const T* q = f + ((size_t)r * n + i) * 6;
-      const T* nu = q + 3;
-      T* o = sf + (size_t)s * C + 6 * r;
-      o[0] = q[0] * nu[0];
-      o[1] = q[1] * nu[1];
-      o[2] = q[2] * nu[2];
-      o[3] = T(0.5) * (q[0] * nu[1] + q[1] * nu[0]);
-      o[4] = T(0.5) * (q[0] * nu[2] + q[2] * nu[0]);
-      o[5] = T(0.5) * (q[1] * nu[2] + q[2] * nu[1]);
+      put_sym6(q, q + 3, sf + (size_t)s * C + 6 * r);
+    }
+  } else if (kernel == SE_KERNEL_ST) {
+    const int C = 9 * n_rhs;
+    for (int r = 0; r < n_rhs; ++r) {
+      const T* fr = f + ((size_t)r * n + i) * 9;
+      T* o = sf + (size_t)s * C + 9 * r;
+      o[0] = fr[0];
+      o[1] = fr[1];
+      o[2] = fr[2];
+      put_sym6(fr + 3, fr + 6, o + 3);
     }
   } else {
     const int C = 3 * n_rhs;
@@ -470,16 +485,27 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
       s = regular_scalar<T>(kernel, kk, a.inv4xi2) * g;
     }
   }
-  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const int cin = kernel_comps(kernel);
   for (int r = 0; r < n_rhs; ++r) {
-    T re[6], im[6];
+    T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
       re[c] = spec[o];
       im[c] = spec[o + 1];
     }
     T ore[3], oim[3];
-    apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
+    if (kernel == SE_KERNEL_ST) {
+      // both are biharmonic (same scalar s): K^S f^ + K^T F^, the stresslet components after f
+      T tre[3], tim[3];
+      apply_regular<T>(SE_STOKESLET, s, k0, k1, k2, re, im, ore, oim);
+      apply_regular<T>(SE_STRESSLET, s, k0, k1, k2, re + 3, im + 3, tre, tim);
+      for (int j = 0; j < 3; ++j) {
+        ore[j] += tre[j];
+        oim[j] += tim[j];
+      }
+    } else {
+      apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
+    }
     for (int j = 0; j < 3; ++j) {
       const size_t o = (((size_t)(3 * r + j)) * H + idx) * 2;
       spec[o] = ore[j];
@@ -654,12 +680,13 @@ template <typename T, int KERNEL, int RMAX>
 __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, T c2pi, const T* __restrict__ f,
                                           int n_rhs, T* acc) {
   if (rr2 == T(0)) {
-    if (KERNEL == SE_STOKESLET) {
+    if (KERNEL == SE_STOKESLET || KERNEL == SE_KERNEL_ST) {
       const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi), Eq. (3p-stokeslet-self-term)
+      constexpr int STRIDE = KERNEL == SE_KERNEL_ST ? 9 : 3;
 #pragma unroll
       for (int r = 0; r < RMAX; ++r)
         if (r < n_rhs)
-          for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[3 * r + q];
+          for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[STRIDE * r + q];
     }
     return;
   }
@@ -698,13 +725,31 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   } else {
     // Eq. (stresslet-real): -2 r_j r_l r_m / r^4 (3 erfc/r + (3 + 2 xi^2 r^2) 2 xi e/sqrt pi)
     //   + (delta_jl r_m + delta_mj r_l + delta_lm r_j) 4 xi^3 e / sqrt pi
+    // (S|T: the stokeslet term of Eq. stokeslet-real on f as above, then this on (q, nu))
+    constexpr int STRIDE = KERNEL == SE_KERNEL_ST ? 9 : 6;
+    constexpr int QOFF = KERNEL == SE_KERNEL_ST ? 3 : 0;
+    if (KERNEL == SE_KERNEL_ST) {
+      const T c1 = ec + c2pi * e;
+      const T c0 = c1 - T(2) * c2pi * e;
+      const T c1i = c1 * inv2;
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) {
+        if (r < n_rhs) {
+          const T* fr = f + STRIDE * r;
+          const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1i;
+          acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
+          acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
+          acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
+        }
+      }
+    }
     const T A = T(3) * ec + (T(3) + T(2) * xi2 * rr2) * c2pi * e;
     const T B = T(2) * xi2 * c2pi * e;
     const T Ai = -T(2) * A * inv2 * inv2;
 #pragma unroll
     for (int r = 0; r < RMAX; ++r) {
       if (r < n_rhs) {
-        const T* q = f + 6 * r;
+        const T* q = f + STRIDE * r + QOFF;
         const T* nu = q + 3;
         const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
         const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
@@ -775,7 +820,7 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   xtl.x = xtl.y = xtl.z = xtl.w = T(0);
   if (sizeof(T) == 4) xtl = a.xtl[s];
   const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
-  const int nc = KERNEL == SE_STRESSLET ? 6 : 3;
+  const int nc = kernel_comps(KERNEL);
   const int C = nc * a.n_rhs;
   T acc[3 * RMAX];
 #pragma unroll
@@ -1008,7 +1053,7 @@ __global__ void k_scatter_cell(CellGeom g, const int* __restrict__ key, const in
     }
   }
   if (f) {
-    const int nc = kernel == SE_STRESSLET ? 6 : 3;
+    const int nc = kernel_comps(kernel);
     for (int r = 0; r < n_rhs; ++r)
       for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = f[((size_t)r * n + i) * nc + c];
   }
@@ -1022,13 +1067,14 @@ __global__ void k_scatter_cell(CellGeom g, const int* __restrict__ key, const in
 
 template <typename T>
 __global__ void k_k0_sums(GridGeom g, const double* __restrict__ x, const T* __restrict__ f, int n,
-                          int n_rhs, double* __restrict__ sums, int* status) {
-  // sums[r*4 + 0] = sum qn, sums[r*4 + 1..3] = sum x_n qn
+                          int n_rhs, int stride, int qoff, double* __restrict__ sums, int* status) {
+  // sums[r*4 + 0] = sum qn, sums[r*4 + 1..3] = sum x_n qn; (q, nu) of point i of RHS r at
+  // f[(r n + i) stride + qoff ...]
   __shared__ double red[4][256];
   for (int r = 0; r < n_rhs; ++r) {
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-      const T* q = f + ((size_t)r * n + i) * 6;
+      const T* q = f + ((size_t)r * n + i) * stride + qoff;
       double qn = (double)q[0] * q[3] + (double)q[1] * q[4] + (double)q[2] * q[5];
       a0 += qn;
       a1 += wrap_coord(x[3 * i], g.L[0], 1, status) * qn;
@@ -1440,7 +1486,8 @@ template <typename T, int R>
 void real_launch(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
   if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, st, a);
   else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, st, a);
-  else real_launch_k<T, SE_STRESSLET, R>(p, st, a);
+  else if (a.kernel == SE_STRESSLET) real_launch_k<T, SE_STRESSLET, R>(p, st, a);
+  else real_launch_k<T, SE_KERNEL_ST, R>(p, st, a);
 }
 
 // u += v elementwise (join of the real-space part computed on the side stream)
@@ -1456,7 +1503,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   const bool star = (tgt == nullptr);
   const int N = (int)n_src;
   const int NT = star ? N : (int)n_tgt;
-  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const int cin = kernel_comps(kernel);
   const int C = cin * n_rhs;    // spread components
   const int NC = 3 * n_rhs;     // output components
   if (C > MAX_COMP || n_rhs > 16) return SE_ERR_UNSUPPORTED;
@@ -1664,21 +1711,21 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   stage.mark();  // 7: real (join)
 
   // ---------------- corrections (self term lives in the real-space pair loop)
-  if ((parts & SE_PART_CORR) && p->D == 3 && kernel == SE_STRESSLET && N > 0 && NT > 0) {
+  if ((parts & SE_PART_CORR) && p->D == 3 && (kernel & SE_STRESSLET) && N > 0 && NT > 0) {
     void* sums;
     SE_TRY(buf(p, "k0sums", sizeof(double) * 4 * n_rhs, &sums));
     SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * n_rhs, st));
     ++p->launches;
-    k_k0_sums<T><<<std::min(grid1d(N, 256), 152), 256, 0, st>>>(g, src, strengths, N, n_rhs, (double*)sums,
-                                                                p->d_status);
+    k_k0_sums<T><<<std::min(grid1d(N, 256), 152), 256, 0, st>>>(g, src, strengths, N, n_rhs, cin, cin - 6,
+                                                                (double*)sums, p->d_status);
     const double vol = p->L[0] * p->L[1] * p->L[2];
     ++p->launches;
     k_k0_apply<T><<<grid1d(NT, 256), 256, 0, st>>>(g, star ? src : tgt, NT, n_rhs, (double*)sums,
                                                   -8.0 * M_PI / vol, u, p->d_status);
     SE_CUDA(cudaGetLastError());
   }
-  if ((parts & SE_PART_CORR) && kernel == SE_STOKESLET)
-    SE_TRY(gauge_correction<T>(p, strengths, N, n_rhs, NT, u));
+  if ((parts & SE_PART_CORR) && (kernel & SE_STOKESLET))
+    SE_TRY(gauge_correction<T>(p, strengths, cin, N, n_rhs, NT, u));
   stage.mark();  // 8: corrections
   p->timed_pending = p->timers.on;
   p->real_timed = p->timers.on && (parts & SE_PART_REAL) && NT > 0;
@@ -1693,10 +1740,8 @@ extern "C" se_status se_eval_parts(se_plan_h p, int kernel, int parts, long long
   if (!p || !u || (n_src > 0 && (!src || !strengths))) return SE_ERR_ARG;
   if (n_src < 0 || n_src > 0x7fffffffLL || n_rhs < 1) return SE_ERR_ARG;
   if (tgt && (n_tgt < 0 || n_tgt > 0x7fffffffLL)) return SE_ERR_ARG;
-  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET) {
-    if (kernel == (SE_STOKESLET | SE_STRESSLET)) return SE_ERR_UNSUPPORTED;
+  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET && kernel != SE_KERNEL_ST)
     return SE_ERR_ARG;
-  }
   if (parts <= 0 || parts > SE_PART_ALL) return SE_ERR_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return SE_ERR_CUDA;
   if (p->prec == SE_FP32)
@@ -1717,7 +1762,7 @@ extern "C" se_status se_eval_host(se_plan_h p, int kernel, long long n_src, cons
   if (!p || !u || !src || !strengths || n_src < 0 || n_rhs < 1) return SE_ERR_ARG;
   const bool star = tgt == nullptr;
   const long long NT = star ? n_src : n_tgt;
-  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const int cin = kernel_comps(kernel);
   const size_t es = p->prec == SE_FP32 ? 4 : 8;
   const size_t bx = sizeof(double) * 3 * (size_t)n_src;
   const size_t bf = es * cin * (size_t)n_rhs * n_src;

@@ -238,11 +238,82 @@ struct FreeScale {
   double inv4xi2;
 };
 
+// One kernel's operator on one mode (Eq. SE-scaling-disc): the regular symbol for
+// k^P != 0 (scalar s), the modified kernels of Eqs. (mod-*-2p) / (mod-*-1p) for the k^P = 0
+// class (scalars mr + i mi, and tb = B^ for D = 1). Writes the 3 output components.
+template <typename T>
+__device__ __forceinline__ void free_mode(const FreeScale& a, int kernel, T s, T k0, T k1, T k2, T mr, T mi, T tb,
+                                          const T* re, const T* im, T* ore, T* oim) {
+  if (a.cls != 0) {
+    apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
+  } else if (a.m.D == 2) {
+    // modified column: scalar (mr + i mi) times D^S, D^Omega or D^T
+    T vr[3], vi[3];
+    if (kernel == SE_STOKESLET) {
+      vr[0] = 2 * re[0]; vi[0] = 2 * im[0];
+      vr[1] = 2 * re[1]; vi[1] = 2 * im[1];
+      vr[2] = 0; vi[2] = 0;
+    } else if (kernel == SE_ROTLET) {
+      vr[0] = re[1]; vi[0] = im[1];
+      vr[1] = -re[0]; vi[1] = -im[0];
+      vr[2] = 0; vi[2] = 0;
+    } else {
+      // D^T_1lm F_lm = -2 (F13 + F31), D^T_2lm F_lm = -2 (F23 + F32), D^T_3lm F_lm = -2 tr F
+      vr[0] = -4 * re[4]; vi[0] = -4 * im[4];
+      vr[1] = -4 * re[5]; vi[1] = -4 * im[5];
+      vr[2] = -2 * (re[0] + re[1] + re[2]); vi[2] = -2 * (im[0] + im[1] + im[2]);
+    }
+    for (int q = 0; q < 3; ++q) {
+      ore[q] = mr * vr[q] - mi * vi[q];
+      oim[q] = mr * vi[q] + mi * vr[q];
+    }
+  } else {
+    // modified plane (D = 1), k = (0, kappa2, kappa3)
+    const T q2 = k1, q3 = k2;
+    if (kernel == SE_ROTLET) {
+      apply_regular<T>(SE_ROTLET, mr, T(0), q2, q3, re, im, ore, oim);
+    } else if (kernel == SE_STOKESLET) {
+      ore[0] = 2 * mr * re[0];
+      oim[0] = 2 * mr * im[0];
+      ore[1] = tb * (-q3 * q3 * re[1] + q2 * q3 * re[2]);
+      oim[1] = tb * (-q3 * q3 * im[1] + q2 * q3 * im[2]);
+      ore[2] = tb * (q2 * q3 * re[1] - q2 * q2 * re[2]);
+      oim[2] = tb * (q2 * q3 * im[1] - q2 * q2 * im[2]);
+    } else {
+      // 2i C^TH H^ - i C^TB B^ with symmetric F: 11,22,33,12,13,23 = 0..5
+      const T kk = q2 * q2 + q3 * q3;
+      T chr[3], chi[3], cbr[3], cbi[3];
+      chr[0] = 2 * q2 * re[3] + 2 * q3 * re[4];
+      chi[0] = 2 * q2 * im[3] + 2 * q3 * im[4];
+      chr[1] = q2 * re[0];
+      chi[1] = q2 * im[0];
+      chr[2] = q3 * re[0];
+      chi[2] = q3 * im[0];
+      cbr[0] = 0;
+      cbi[0] = 0;
+      const T c22 = q2 * (3 * kk - 2 * q2 * q2), c23 = q3 * (kk - 2 * q2 * q2), c33 = q2 * (kk - 2 * q3 * q3);
+      cbr[1] = c22 * re[1] + 2 * c23 * re[5] + c33 * re[2];
+      cbi[1] = c22 * im[1] + 2 * c23 * im[5] + c33 * im[2];
+      const T d22 = q3 * (kk - 2 * q2 * q2), d23 = q2 * (kk - 2 * q3 * q3), d33 = q3 * (3 * kk - 2 * q3 * q3);
+      cbr[2] = d22 * re[1] + 2 * d23 * re[5] + d33 * re[2];
+      cbi[2] = d22 * im[1] + 2 * d23 * im[5] + d33 * im[2];
+      for (int q = 0; q < 3; ++q) {
+        const T vr = 2 * mr * chr[q] - tb * cbr[q];
+        const T vi = 2 * mr * chi[q] - tb * cbi[q];
+        ore[q] = -vi;  // i (vr + i vi)
+        oim[q] = vr;
+      }
+    }
+  }
+}
+
 // Scaling step, Eq. (SE-scaling-disc), on a class buffer [C][ncols][free...] in place:
 // regular kernel for k^P != 0; the modified kernels of Eqs. (mod-*-2p) / (mod-*-1p) for the
 // k^P = 0 class. Tables (plan precision): tp0/tp1 periodic factors, tf0/tf1 free factors
-// (exp(-k^2/4xi^2) / w^2 / n each); for the k^P = 0 class mod0 / mod1 / mod2 hold the
-// modified-kernel scalars.
+// (exp(-k^2/4xi^2) / w^2 / n each); for the k^P = 0 class mod0 / mod1 hold the modified-
+// kernel scalars (D = 2: complex scalar of the kernel, and of the stresslet for S|T in mod1;
+// D = 1: H^ and B^). S|T sums the stokeslet operator on components 0..2 and the stresslet
+// operator on components 3..8.
 template <typename T>
 __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __restrict__ tp0,
                              const T* __restrict__ tp1, const T* __restrict__ tf0, const T* __restrict__ tf1,
@@ -260,7 +331,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
   if (a.cls == 2 && !in_class(a.m, i0, i1, 2)) return;
   int f0 = nf == 1 ? (int)e : (int)(e / a.fn[1]);
   int f1 = nf == 1 ? 0 : (int)(e % a.fn[1]);
-  const int cin = kernel == SE_STRESSLET ? 6 : 3;
+  const int cin = kernel_comps(kernel);
   // wavenumbers
   bool zero = false;
   T k0, k1, k2;
@@ -273,7 +344,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
     if (f1 == a.fn[1] / 2) zero = true;
   }
   T s = 0;
-  T mr = 0, mi = 0, tb = 0;
+  T mr = 0, mi = 0, tb = 0, mr2 = 0, mi2 = 0;  // mr2, mi2: stresslet scalar of S|T
   if (a.m.D == 2) {
     const int kb0 = i0 < a.m.M0 / 2 ? i0 : i0 - a.m.M0;
     if (i0 == a.m.M0 / 2 || i1 == a.m.M1 / 2) zero = true;
@@ -283,6 +354,10 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
     if (a.cls == 0) {
       mr = mod0[2 * f0];
       mi = mod0[2 * f0 + 1];
+      if (kernel == SE_KERNEL_ST) {
+        mr2 = mod1[2 * f0];
+        mi2 = mod1[2 * f0 + 1];
+      }
     } else {
       const T kk = k0 * k0 + k1 * k1 + k2 * k2;
       s = regular_scalar<T>(kernel, kk, (T)a.inv4xi2) * tp0[i0] * tp1[i1] * tf0[f0];
@@ -295,6 +370,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
     if (a.cls == 0) {
       mr = mod0[e];       // H^-type table for this kernel
       tb = mod1 ? mod1[e] : T(0);  // B^ table (stokeslet, stresslet)
+      mr2 = mr;           // the stresslet of S|T uses the same H^ and B^
     } else {
       const T kk = k0 * k0 + k1 * k1 + k2 * k2;
       s = regular_scalar<T>(kernel, kk, (T)a.inv4xi2) * tp0[i0] * tf0[f0] * tf1[f1];
@@ -302,7 +378,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
   }
   const size_t H = (size_t)a.ncols * plane;  // component stride in this buffer
   for (int r = 0; r < n_rhs; ++r) {
-    T re[6], im[6];
+    T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
       re[c] = spec[o];
@@ -310,66 +386,16 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
     }
     T ore[3] = {0, 0, 0}, oim[3] = {0, 0, 0};
     if (!zero) {
-      if (a.cls != 0) {
-        apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
-      } else if (a.m.D == 2) {
-        // modified column: scalar (mr + i mi) times D^S, D^Omega or D^T
-        T vr[3], vi[3];
-        if (kernel == SE_STOKESLET) {
-          vr[0] = 2 * re[0]; vi[0] = 2 * im[0];
-          vr[1] = 2 * re[1]; vi[1] = 2 * im[1];
-          vr[2] = 0; vi[2] = 0;
-        } else if (kernel == SE_ROTLET) {
-          vr[0] = re[1]; vi[0] = im[1];
-          vr[1] = -re[0]; vi[1] = -im[0];
-          vr[2] = 0; vi[2] = 0;
-        } else {
-          // D^T_1lm F_lm = -2 (F13 + F31), D^T_2lm F_lm = -2 (F23 + F32), D^T_3lm F_lm = -2 tr F
-          vr[0] = -4 * re[4]; vi[0] = -4 * im[4];
-          vr[1] = -4 * re[5]; vi[1] = -4 * im[5];
-          vr[2] = -2 * (re[0] + re[1] + re[2]); vi[2] = -2 * (im[0] + im[1] + im[2]);
-        }
+      if (kernel == SE_KERNEL_ST) {
+        T tre[3], tim[3];
+        free_mode<T>(a, SE_STOKESLET, s, k0, k1, k2, mr, mi, tb, re, im, ore, oim);
+        free_mode<T>(a, SE_STRESSLET, s, k0, k1, k2, mr2, mi2, tb, re + 3, im + 3, tre, tim);
         for (int q = 0; q < 3; ++q) {
-          ore[q] = mr * vr[q] - mi * vi[q];
-          oim[q] = mr * vi[q] + mi * vr[q];
+          ore[q] += tre[q];
+          oim[q] += tim[q];
         }
       } else {
-        // modified plane (D = 1), k = (0, kappa2, kappa3)
-        const T q2 = k1, q3 = k2;
-        if (kernel == SE_ROTLET) {
-          apply_regular<T>(SE_ROTLET, mr, T(0), q2, q3, re, im, ore, oim);
-        } else if (kernel == SE_STOKESLET) {
-          ore[0] = 2 * mr * re[0];
-          oim[0] = 2 * mr * im[0];
-          ore[1] = tb * (-q3 * q3 * re[1] + q2 * q3 * re[2]);
-          oim[1] = tb * (-q3 * q3 * im[1] + q2 * q3 * im[2]);
-          ore[2] = tb * (q2 * q3 * re[1] - q2 * q2 * re[2]);
-          oim[2] = tb * (q2 * q3 * im[1] - q2 * q2 * im[2]);
-        } else {
-          // 2i C^TH H^ - i C^TB B^ with symmetric F: 11,22,33,12,13,23 = 0..5
-          const T kk = q2 * q2 + q3 * q3;
-          T chr[3], chi[3], cbr[3], cbi[3];
-          chr[0] = 2 * q2 * re[3] + 2 * q3 * re[4];
-          chi[0] = 2 * q2 * im[3] + 2 * q3 * im[4];
-          chr[1] = q2 * re[0];
-          chi[1] = q2 * im[0];
-          chr[2] = q3 * re[0];
-          chi[2] = q3 * im[0];
-          cbr[0] = 0;
-          cbi[0] = 0;
-          const T c22 = q2 * (3 * kk - 2 * q2 * q2), c23 = q3 * (kk - 2 * q2 * q2), c33 = q2 * (kk - 2 * q3 * q3);
-          cbr[1] = c22 * re[1] + 2 * c23 * re[5] + c33 * re[2];
-          cbi[1] = c22 * im[1] + 2 * c23 * im[5] + c33 * im[2];
-          const T d22 = q3 * (kk - 2 * q2 * q2), d23 = q2 * (kk - 2 * q3 * q3), d33 = q3 * (3 * kk - 2 * q3 * q3);
-          cbr[2] = d22 * re[1] + 2 * d23 * re[5] + d33 * re[2];
-          cbi[2] = d22 * im[1] + 2 * d23 * im[5] + d33 * im[2];
-          for (int q = 0; q < 3; ++q) {
-            const T vr = 2 * mr * chr[q] - tb * cbr[q];
-            const T vi = 2 * mr * chi[q] - tb * cbi[q];
-            ore[q] = -vi;  // i (vr + i vi)
-            oim[q] = vr;
-          }
-        }
+        free_mode<T>(a, kernel, s, k0, k1, k2, mr, mi, tb, re, im, ore, oim);
       }
     }
     for (int q = 0; q < 3; ++q) {
@@ -380,14 +406,14 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
   }
 }
 
-// gauge constants: u[r][i][j] += c_j sum_n f[r][n][j]
+// gauge constants: u[r][i][j] += c_j sum_n f[r][n][j] (f the first 3 of stride components)
 template <typename T>
-__global__ void k_fsum(const T* f, int n, int n_rhs, double* sums) {
+__global__ void k_fsum(const T* f, int stride, int n, int n_rhs, double* sums) {
   __shared__ double red[3][256];
   for (int r = 0; r < n_rhs; ++r) {
     double a[3] = {0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      for (int j = 0; j < 3; ++j) a[j] += (double)f[((size_t)r * n + i) * 3 + j];
+      for (int j = 0; j < 3; ++j) a[j] += (double)f[((size_t)r * n + i) * stride + j];
     for (int j = 0; j < 3; ++j) red[j][threadIdx.x] = a[j];
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -628,7 +654,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   const GridGeom& g = p->geom;
   cudaStream_t st = p->stream;
   const int D = p->D;
-  const int kidx = kernel == SE_STOKESLET ? 0 : (kernel == SE_STRESSLET ? 1 : 2);
+  // k^P = 0 tables of D = 2 per kernel: 0 stokeslet, 1 stresslet, 2 rotlet (S|T: 0 and 1)
+  const int kidx = (kernel & SE_STOKESLET) ? 0 : (kernel == SE_STRESSLET ? 1 : 2);
   if (D == 0) {
     // 3-D R2C on the 2M' grid, scaled by A^_{R,tr} (Sec. 3.5), C2R
     const int biharm = kernel != SE_ROTLET;
@@ -712,8 +739,9 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     fs.cls = 0;
     fs.ncols = 1;
     fs.fn[0] = n0;
-    k_scale_free<T><<<grid1d(n0, 256), 256, 0, st>>>(fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[0][2].p,
-                                                    nullptr, (const T*)p->mod0[kidx].p, nullptr, (T*)b0);
+    k_scale_free<T><<<grid1d(n0, 256), 256, 0, st>>>(
+        fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[0][2].p, nullptr, (const T*)p->mod0[kidx].p,
+        kernel == SE_KERNEL_ST ? (const T*)p->mod0[1].p : nullptr, (T*)b0);
     if (ncolS > 0) {
       fs.m.mode = 1;
       fs.cls = 1;
@@ -831,13 +859,13 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
 // 1p-stokeslet-extra-contribution): 0P adds (2/R) sum f; 1P subtracts
 // diag(4 ln R + 4, 2 ln R + 1, 2 ln R + 1) sum f / L_0.
 template <typename T>
-se_status gauge_correction(se_plan_t* p, const T* f, int n, int n_rhs, int nt, T* u) {
+se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rhs, int nt, T* u) {
   if (!((p->D == 0 || p->D == 1) && n > 0 && nt > 0)) return SE_OK;
   void* sums;
   SE_TRY(buf(p, "gauge.sums", sizeof(double) * 3 * n_rhs, &sums));
   SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 3 * n_rhs, p->stream));
   ++p->launches;
-  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(f, n, n_rhs, (double*)sums);
+  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(f, stride, n, n_rhs, (double*)sums);
   double c[3];
   if (p->D == 0) {
     c[0] = c[1] = c[2] = 2.0 / p->R;
@@ -854,7 +882,7 @@ se_status gauge_correction(se_plan_t* p, const T* f, int n, int n_rhs, int nt, T
 
 template se_status fourier_free<float>(se_plan_t*, int, int, float*, int, float*, int);
 template se_status fourier_free<double>(se_plan_t*, int, int, double*, int, double*, int);
-template se_status gauge_correction<float>(se_plan_t*, const float*, int, int, int, float*);
-template se_status gauge_correction<double>(se_plan_t*, const double*, int, int, int, double*);
+template se_status gauge_correction<float>(se_plan_t*, const float*, int, int, int, int, float*);
+template se_status gauge_correction<double>(se_plan_t*, const double*, int, int, int, int, double*);
 
 }  // namespace se

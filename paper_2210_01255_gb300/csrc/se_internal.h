@@ -19,6 +19,16 @@ constexpr int TS = 8;          // spread/gather tile edge (grid points)
 constexpr int MAX_P = 32;      // largest window support
 constexpr int MAX_COMP = 48;   // largest number of spread components (16 RHS x 3)
 
+// Stokeslet and stresslet in one evaluation: strengths (f, q, nu) per point, one spread of
+// 3 + 6 components, the two k-space operators summed into one velocity.
+constexpr int SE_KERNEL_ST = SE_STOKESLET | SE_STRESSLET;
+
+// strength components per point and right-hand side, which is also the number of spread
+// components: f (3); (q, nu) (6, spread as the 6 symmetric q nu^T entries); (f, q, nu) (9)
+__host__ __device__ inline int kernel_comps(int kernel) {
+  return kernel == SE_STRESSLET ? 6 : (kernel == SE_KERNEL_ST ? 9 : 3);
+}
+
 // Geometry of the grid that gridding writes and gathering reads (Sec. 3.2).
 struct GridGeom {
   int m[3];         // extent of the spread grid per direction (M_i periodic, M'_i free)
@@ -131,7 +141,7 @@ se_status free_plan_setup(se_plan_t* p);
 template <typename T>
 se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);
 template <typename T>
-se_status gauge_correction(se_plan_t* p, const T* f, int n, int n_rhs, int nt, T* u);
+se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rhs, int nt, T* u);
 double pot_mag(int kernel, double L, double Q, double xi);
 double lambda_table(int kernel, int D);
 void upsampling_rule(int D, const double* box, double h, const int* Mext, double lg, double* s_star,

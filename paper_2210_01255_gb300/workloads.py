@@ -31,9 +31,16 @@ def clustered_points(n, seed, sigma=0.05, centre=(0.5, 0.5, 0.5)):
 
 def strengths(kernel, n, seed, n_rhs=None):
     """Stokeslet / rotlet: f ~ N(0,1)^3. Stresslet: (q, nu) with q ~ N(0,1)^3 and nu ~ N(0,1)^3
-    normalised to unit length. Shape (n, c) or (n_rhs, n, c)."""
+    normalised to unit length. Stokeslet + stresslet: (f, q, nu), f drawn first.
+    Shape (n, c) or (n_rhs, n, c)."""
     rng = np.random.default_rng(seed)
     shape = (n,) if n_rhs is None else (n_rhs, n)
+    if kernel in ("stokeslet+stresslet", 5):
+        f = rng.standard_normal(shape + (3,))
+        q = rng.standard_normal(shape + (3,))
+        nu = rng.standard_normal(shape + (3,))
+        nu /= np.linalg.norm(nu, axis=-1, keepdims=True)
+        return np.concatenate([f, q, nu], axis=-1)
     if kernel in ("stresslet", 4):
         q = rng.standard_normal(shape + (3,))
         nu = rng.standard_normal(shape + (3,))
@@ -43,8 +50,11 @@ def strengths(kernel, n, seed, n_rhs=None):
 
 
 def source_quantity(kernel, f):
-    """Q of Eq. (vector-source-quantity) / (tensor-source-quantity) for one RHS."""
+    """Q of Eq. (vector-source-quantity) / (tensor-source-quantity) for one RHS; for the
+    stokeslet + stresslet strengths (f, q, nu) the two quantities added."""
     f = np.asarray(f, dtype=float)
+    if kernel in ("stokeslet+stresslet", 5):
+        return source_quantity("stokeslet", f[..., :3]) + source_quantity("stresslet", f[..., 3:])
     if kernel in ("stresslet", 4):
         t = f[..., :3, None] * f[..., None, 3:]
         return float(np.sum(t * t))
