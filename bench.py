@@ -1,16 +1,22 @@
 """Benchmark of the Spectral Ewald Stokes hot path on GB300.
 
-Workload (N = 1): the triply periodic stresslet and rotlet potentials of N = 20,000 points
-uniform in the unit box (strengths N(0,1), stresslet normals normalised), FP32 path,
+Default workload (N = 1): the triply periodic stresslet and rotlet potentials of N = 20,000
+points uniform in the unit box (strengths N(0,1), stresslet normals normalised), FP32 path,
 parameters from the selection procedure of Sec. 4.6 at 1e-6 RMS relative tolerance (PKB
-window), targets = sources. One step = one full evaluation of both kernels (real-space sum,
-Fourier-space part of Alg. 1, corrections). value = targets per second of the FP32 batched
-form (both evaluations replayed as one CUDA graph through se_batch_launch), counting each
-(kernel, target) evaluation; the eager form (one se_eval per kernel, with per-kernel events
-for the stage times and the roofline), the FP64 plain form and the end-to-end form through
-host buffers are reported beside it.
+window), targets = sources. --workload selects another configuration of
+paper_2210_01255_gb300.workloads.CONFIGS: the 2P stokeslet with 8 RHS, the 0P stokeslet +
+stresslet of 1e6 clustered points (one fused evaluation), or 64 independent 1P stokeslet
+systems with 16 RHS each.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+A workload is a list of evaluations (kernel, points, strengths, plan); one step runs all of
+them (real-space sum, Fourier-space part of Alg. 1, corrections). value = (target, RHS)
+evaluations per second of the FP32 batched form (all evaluations of a step replayed as one
+CUDA graph through se_batch_launch); the eager form (one se_eval per evaluation, with
+per-evaluation events for the stage times and the roofline), the FP64 plain form (one RHS
+and one kernel per evaluation, same parameters) and the end-to-end form through host
+buffers are reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
 Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas, weak
 scaling, no collective in the data path); value = all ranks' targets / the slowest rank's time.
 """
@@ -31,9 +37,18 @@ WORKLOAD = "3p_stresslet_rotlet_n20000"   # default (--workload selects another 
 METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
 METRIC = METRIC_FMT % "3P stresslet+rotlet, N=20000"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
-                "2p_stokeslet_n200000_rhs8": "2P stokeslet, N=200000, 8 RHS"}
+                "2p_stokeslet_n200000_rhs8": "2P stokeslet, N=200000, 8 RHS",
+                "0p_stokeslet_stresslet_n1000000": "0P stokeslet+stresslet, N=1e6 clustered",
+                "1p_stokeslet_64cfg_rhs16": "1P stokeslet, 64 systems x 16 RHS"}
+# oracle targets per sampled evaluation: cpu_baseline (a few seconds of oracle work on the
+# host cores) and one step of the reference arm
+ORACLE_SAMPLE = {"3p_stresslet_rotlet_n20000": (1024, 512), "2p_stokeslet_n200000_rhs8": (64, 32),
+                 "0p_stokeslet_stresslet_n1000000": (256, 128), "1p_stokeslet_64cfg_rhs16": (64, 32)}
 UNIT = "targets/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+COMPS = {"stokeslet": 3, "rotlet": 3, "stresslet": 6, "stokeslet+stresslet": 9}
+# FP32 operations per real-space pair (separation, rsqrt, exp, erfc fit, the kernel's terms)
+PAIR_FLOPS = {"stokeslet": 60, "rotlet": 60, "stresslet": 60, "stokeslet+stresslet": 75}
 
 
 def peaks():
@@ -105,28 +120,69 @@ def replica_value(targets_per_step, world, steps, ms_max):
     return targets_per_step * world * steps / (ms_max / 1e3)
 
 
-def make_inputs():
-    """Positions (N, 3) and per-kernel strengths (n_rhs, N, c) of the selected workload."""
+def make_items(cfg):
+    """The evaluations of one step: name, kernel, positions (N, 3) and strengths (n_rhs, N, c)
+    in the workload's precision."""
     from paper_2210_01255_gb300 import workloads as W
-    cfg = W.CONFIGS[WORKLOAD]
-    N, R = cfg["N"], cfg.get("n_rhs", 1)
-    x = W.uniform_points(N, cfg["box"], seed=cfg["seed"])
-    fs = {}
+    R = cfg.get("n_rhs", 1)
+    dt = np.float32 if cfg["prec"] == "fp32" else np.float64
+    items = []
+    if "n_cfg" in cfg:
+        Ns = W.batch_sizes(cfg["n_cfg"], *cfg["N_range"], seed=cfg["seed"])
+        for i, N in enumerate(Ns):
+            N = int(N)
+            x = W.uniform_points(N, cfg["box"], seed=cfg["seed"] + 1 + i)
+            for k in cfg["kernels"]:
+                f = W.strengths(k, N, seed=cfg["seed"] + 1000 + i, n_rhs=R)
+                items.append(dict(name="cfg%02d" % i, kernel=k, x=x, N=N, R=R,
+                                  f=np.ascontiguousarray(f.reshape(R, N, -1).astype(dt))))
+        return items
+    N = cfg["N"]
+    if cfg.get("points") == "clustered":
+        x = W.clustered_points(N, seed=cfg["seed"])
+    else:
+        x = W.uniform_points(N, cfg["box"], seed=cfg["seed"])
     for k in cfg["kernels"]:
         f = W.strengths(k, N, seed=cfg["seed"] + (0 if k == "stresslet" else 100), n_rhs=R if R > 1 else None)
-        fs[k] = np.ascontiguousarray(f.reshape(R, N, -1).astype(np.float32))
-    return cfg, x, fs
+        items.append(dict(name=k, kernel=k, x=x, N=N, R=R, f=np.ascontiguousarray(f.reshape(R, N, -1).astype(dt))))
+    return items
 
 
-def tuned(cfg, kernel, f):
+def tuned(cfg, item):
     import paper_2210_01255_gb300 as se
     from paper_2210_01255_gb300 import workloads as W
     # the selection targets E <= 10 tau (Sec. 4.6); ask for tol/10 so the result meets tol
-    Q = W.source_quantity(kernel, f[0])
+    k = item["kernel"]
+    Q = W.source_quantity(k, item["f"][0])
     o = se.se_opts_default()
-    o.n_rc = cfg.get("n_rc", {}).get(kernel, 0.0)
+    o.n_rc = cfg.get("n_rc", {}).get(k, 0.0)
     o.P_margin = cfg.get("P_margin", -1)
-    return se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[kernel], Q, cfg["N"], cfg["tol"] / 10.0, opts=o)
+    return se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
+
+
+def make_plan(cfg, item, prec, stream, flags=0):
+    """A plan with the parameters the selection gives for this evaluation (its extended grid,
+    upsampling factors and kbar_* included), for this kernel only."""
+    import paper_2210_01255_gb300 as se
+    t = tuned(cfg, item)
+    o = t["opts"]
+    o.kernel_mask = se.KERNELS[item["kernel"]]
+    o.flags = flags
+    return se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], prec, opts=o,
+                   stream=stream), dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
+
+
+def real_pairs(cfg, item, rc):
+    """Pairs within rc per evaluation (the real-space work): N (N - 1) / |B| 4/3 pi rc^3 for
+    uniform points; counted with a k-d tree on a sample of 4096 targets for clustered ones."""
+    N = item["N"]
+    if cfg.get("points") != "clustered":
+        return N * (N - 1) / float(np.prod(cfg["box"])) * 4.0 / 3.0 * math.pi * rc ** 3
+    from scipy.spatial import cKDTree
+    x = item["x"]
+    s = np.random.default_rng(3).choice(N, 4096, replace=False)
+    cnt = cKDTree(x).query_ball_point(x[s], rc, return_length=True)
+    return N * float(np.mean(cnt - 1))
 
 
 KERNEL_SOURCES = {"real": "se_core.cu", "spread": "se_core.cu", "gather": "se_core.cu"}
@@ -157,41 +213,55 @@ def kernel_traffic(stage, params, gridding="cuda"):
     return sum(vals) / len(vals) if len(vals) == len(params) else None
 
 
-def oracle_sample(cfg, x, fs, nsample, seed=7):
-    """The exact Ewald oracle (FP64, all host cores) at a bounded sample of targets."""
+def oracle_potential(cfg, item, r, targets):
+    """The exact Ewald oracle (FP64, all host cores): RHS r of one evaluation at the targets;
+    for the stokeslet + stresslet strengths the sum of the two potentials."""
     from oracle import ewald as E
-    idx = np.random.default_rng(seed).choice(cfg["N"], nsample, replace=False)
-    out, t0 = {}, time.perf_counter()
-    for k in cfg["kernels"]:
-        out[k] = E.potential(cfg["D"], list(cfg["box"]), k, x, fs[k][0].astype(np.float64), targets=x[idx])
-    return idx, out, time.perf_counter() - t0
+    f = item["f"][r].astype(np.float64)
+    box = list(cfg["box"])
+    if item["kernel"] == "stokeslet+stresslet":
+        return (E.potential(cfg["D"], box, "stokeslet", item["x"], f[:, :3], targets=targets)
+                + E.potential(cfg["D"], box, "stresslet", item["x"], f[:, 3:], targets=targets))
+    return E.potential(cfg["D"], box, item["kernel"], item["x"], f, targets=targets)
+
+
+def oracle_sample(cfg, items, nsample, seed=7):
+    """The oracle at a bounded sample of targets (RHS 0) of the first two evaluations:
+    returns [(item, target indices, potentials)] and the oracle's time."""
+    out, t0 = [], time.perf_counter()
+    for i, it in enumerate(items[:2]):
+        idx = np.random.default_rng(seed + i).choice(it["N"], min(nsample, it["N"]), replace=False)
+        out.append((it, idx, oracle_potential(cfg, it, 0, it["x"][idx])))
+    return out, time.perf_counter() - t0
 
 
 def run_reference(args):
     """Reference arm: the oracle as it stands, timed on the host cores."""
+    from paper_2210_01255_gb300 import workloads as W
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    cfg, x, fs = make_inputs()
-    ns = 512 if cfg["N"] <= 50000 else 32  # targets per step: ~1-2 s of oracle work
+    cfg = W.CONFIGS[WORKLOAD]
+    items = make_items(cfg)
+    ns = ORACLE_SAMPLE[WORKLOAD][1]
     for _ in range(args.warmup):
-        oracle_sample(cfg, x, fs, ns, seed=11)
-    tot = 0.0
+        oracle_sample(cfg, items, ns, seed=11)
+    tot, targets = 0.0, 0
     for s in range(args.steps):
-        _, _, dt = oracle_sample(cfg, x, fs, ns, seed=100 + s)
+        res, dt = oracle_sample(cfg, items, ns, seed=100 + 7 * s)
         tot += dt
-    targets = ns * len(cfg["kernels"]) * args.steps
+        targets += sum(len(idx) for _, idx, _ in res)
     value = targets / tot
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": cfg["N"], "box": list(cfg["box"]),
+            "config": {"workload": WORKLOAD, "N": sum(it["N"] for it in items), "box": list(cfg["box"]),
                        "kernels": list(cfg["kernels"]), "tol_rel": cfg["tol"], "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": "%d sampled targets x %d kernels per step, all N sources" %
-                                       (ns, len(cfg["kernels"]))},
+                             "sample": "%d sampled targets of each of the first %d evaluations per step, all "
+                                       "sources" % (ns, min(2, len(items)))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -218,6 +288,7 @@ def main():
 
     import torch
     import paper_2210_01255_gb300 as se
+    from paper_2210_01255_gb300 import workloads as W
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,35 +300,32 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    cfg, x, fs = make_inputs()
-    N, R = cfg["N"], cfg.get("n_rhs", 1)
+    cfg = W.CONFIGS[WORKLOAD]
+    prec = cfg["prec"]
+    tdt = torch.float32 if prec == "fp32" else torch.float64
+    flags = se.FLAG_TC_GRIDDING if args.gridding == "tc" else 0
+    items = make_items(cfg)
     stream = torch.cuda.current_stream()
-    plans, fdev, params = {}, {}, {}
-    for k in cfg["kernels"]:
-        t = tuned(cfg, k, fs[k])
-        params[k] = dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
-        o = se.se_opts_default()
-        o.flags = se.FLAG_TC_GRIDDING if args.gridding == "tc" else 0
-        plans[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp32",
-                           opts=o, stream=stream)
-        fdev[k] = torch.tensor(fs[k], device=dev)
-    grid_n = {k: list(plans[k].info().n) for k in cfg["kernels"]}
-    xdev = torch.tensor(x, device=dev)
-    udev = {k: torch.empty((R, N, 3), dtype=torch.float32, device=dev) for k in cfg["kernels"]}
+    for it in items:
+        it["plan"], it["params"] = make_plan(cfg, it, prec, stream, flags)
+        it["grid_n"] = list(it["plan"].info().n)
+        it["xdev"] = torch.tensor(it["x"], device=dev)
+        it["fdev"] = torch.tensor(it["f"], device=dev)
+        it["udev"] = torch.empty((it["R"], it["N"], 3), dtype=tdt, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
-        for k in cfg["kernels"]:
-            plans[k].evaluate(k, xdev, fdev[k], out=udev[k])
+        for it in items:
+            it["plan"].evaluate(it["kernel"], it["xdev"], it["fdev"], out=it["udev"])
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
 
     # ---- timed region: K steps, L2 flushed between steps (outside the events)
-    for p in plans.values():
-        se.se_set_timing(p.handle, True)
-    stage_ms = {k: np.zeros(8) for k in cfg["kernels"]}
+    for it in items:
+        se.se_set_timing(it["plan"].handle, True)
+    stage_ms = np.zeros(8)
     launches = 0
     sampler = ClockSampler(local)
     sampler.start()
@@ -271,30 +339,25 @@ def main():
         ev[s][0].record(stream)
         step()
         ev[s][1].record(stream)
-        for k in cfg["kernels"]:
-            info = plans[k].info()       # waits for this step's stage events
-            stage_ms[k] += np.array(list(info.times_ms))
+        for it in items:
+            info = it["plan"].info()       # waits for this step's stage events
+            stage_ms += np.maximum(np.array(list(info.times_ms)), 0.0)
             launches += info.launches
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    targets_per_step = N * R * len(cfg["kernels"])  # (target, RHS) evaluations per step
-    # FP32 batched: both evaluations of a step captured into one CUDA graph (se_batch_*) on a
+    targets_per_step = sum(it["N"] * it["R"] for it in items)  # (target, RHS) evaluations per step
+    # FP32 batched: all evaluations of a step captured into one CUDA graph (se_batch_*) on a
     # stream of their own and replayed; L2 flushed between replays, timed with events
-    graph = None
     gstream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(gstream):
-        gplans, gu = {}, {}
-        for k in cfg["kernels"]:
-            t = params[k]
-            o = se.se_opts_default()
-            o.flags = se.FLAG_TC_GRIDDING if args.gridding == "tc" else 0
-            gplans[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp32",
-                                opts=o, stream=gstream)
-            gu[k] = torch.empty((R, N, 3), dtype=torch.float32, device=dev)
-        ks = list(cfg["kernels"])
-        bh = se.se_batch_create([gplans[k].handle for k in ks], [se.KERNELS[k] for k in ks], [xdev] * len(ks),
-                                [fdev[k] for k in ks], [R] * len(ks), [gu[k] for k in ks])
+        gplans, gu = [], []
+        for it in items:
+            gplans.append(make_plan(cfg, it, prec, gstream, flags)[0])
+            gu.append(torch.empty((it["R"], it["N"], 3), dtype=tdt, device=dev))
+        bh = se.se_batch_create([p.handle for p in gplans], [se.KERNELS[it["kernel"]] for it in items],
+                                [it["xdev"] for it in items], [it["fdev"] for it in items],
+                                [it["R"] for it in items], gu)
         for _ in range(max(3, args.warmup)):
             se.se_batch_launch(bh)
         gstream.synchronize()
@@ -312,49 +375,53 @@ def main():
         if dist:
             dist.barrier()
         tg = sum(a.elapsed_time(b) for a, b in evg)
-        gerr = max(float((gu[k] - udev[k]).abs().max() / udev[k].abs().max()) for k in ks)
+        gerr = max(float((g - it["udev"]).abs().max() / it["udev"].abs().max()) for g, it in zip(gu, items))
         se.se_batch_destroy(bh)
+        del gplans, gu
     graph = {"value": targets_per_step * args.steps / (tg / 1e3), "unit": UNIT, "ms_per_step": tg / args.steps,
              "form": "FP32 batched: the step's evaluations replayed as one CUDA graph (se_batch_launch); "
                      "the headline value",
              "max_rel_diff_vs_eager": gerr}
 
     clocks = sampler.stop()
-    for p in plans.values():
-        se.se_set_timing(p.handle, False)
+    for it in items:
+        se.se_set_timing(it["plan"].handle, False)
     tot_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), dist, dev)
     value = replica_value(targets_per_step, world, args.steps, tot_ms)
 
     # ---- dominant kernel and its roofline
     names = ["bin", "spread", "fft", "scale", "ifft", "gather", "real", "corr"]
-    per_stage = {n: sum(stage_ms[k][i] for k in cfg["kernels"]) / args.steps for i, n in enumerate(names)}
-    work, hbm = {}, {}
-    for k in cfg["kernels"]:
-        P = params[k]["P"]
-        C = (6 if k == "stresslet" else 3) * R
-        G = float(np.prod(grid_n[k]))
-        H = float(grid_n[k][0] * grid_n[k][1] * (grid_n[k][2] // 2 + 1))
-        work.setdefault("spread", 0.0)
+    per_stage = {n: stage_ms[i] / args.steps for i, n in enumerate(names)}
+    work = {"spread": 0.0, "gather": 0.0, "real": 0.0}
+    hbm = {"spread": 0.0, "gather": 0.0}
+    pairs = 0.0
+    for it in items:
+        N, R, P = it["N"], it["R"], it["params"]["P"]
+        C = COMPS[it["kernel"]] * R
+        G = float(np.prod(it["grid_n"]))
+        H = float(it["grid_n"][0] * it["grid_n"][1] * (it["grid_n"][2] // 2 + 1))
         work["spread"] += 2.0 * N * P ** 3 * C        # one FMA per tap per component
-        work.setdefault("gather", 0.0)
         work["gather"] += 2.0 * N * P ** 3 * 3 * R
         # algorithmic HBM bytes: spread N (24 + 4 C) + 4 G C; gather 4 G 3R + 12 N R;
-        # k-space multiply (3P) (C + 3R) x 8 B per half-spectrum mode
-        hbm["spread"] = hbm.get("spread", 0.0) + N * (24 + 4 * C) + 4 * G * C
-        hbm["gather"] = hbm.get("gather", 0.0) + 4 * G * 3 * R + 12 * N * R
+        # k-space multiply (D = 3; for D < 3 it is timed inside the transforms) (C + 3R) x 8 B
+        # per half-spectrum mode
+        hbm["spread"] += N * (24 + 4 * C) + 4 * G * C
+        hbm["gather"] += 4 * G * 3 * R + 12 * N * R
         if cfg["D"] == 3:
             hbm["scale"] = hbm.get("scale", 0.0) + (C + 3 * R) * 8 * H
-    # real space: pairs within rc for the uniform density of this workload, 60 flops per pair
-    vol = float(np.prod(cfg["box"]))
-    work["real"] = sum(60.0 * N * (N - 1) / vol * 4.0 / 3.0 * math.pi * params[k]["rc"] ** 3
-                       for k in cfg["kernels"])
+        np_ = real_pairs(cfg, it, it["params"]["rc"])
+        pairs += np_
+        work["real"] += PAIR_FLOPS[it["kernel"]] * np_
     # the dominant kernel among those with a per-launch algorithmic work figure
     dom = max(work, key=lambda n: per_stage[n])
     ach = work[dom] / (per_stage[dom] * 1e-3) / 1e12
+    tparams = {it["name"]: it["params"] for it in items}
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": ach / FP32_PEAK_TFLOPS, "traffic": kernel_traffic(dom, params, args.gridding),
+            "frac": ach / FP32_PEAK_TFLOPS,
+            "traffic": kernel_traffic(dom, tparams, args.gridding) if len(items) <= 4 else None,
             "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived from unit counts and "
-                           "the maximum SM clock)"}
+                           "the maximum SM clock)",
+            "real_space_pairs_per_step": pairs}
     roof["per_stage_tflops"] = {k: work[k] / (per_stage[k] * 1e-3) / 1e12 for k in work if per_stage[k] > 0}
     pk = peaks()
     roof["per_stage_hbm"] = {k: {"algorithmic_bytes": hbm[k], "achieved_gbs": hbm[k] / (per_stage[k] * 1e-3) / 1e9,
@@ -362,44 +429,52 @@ def main():
                              for k in hbm if per_stage[k] > 0}
 
     # ---- end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e = None
-    if rank == 0 or True:
-        xh = np.ascontiguousarray(x)
-        uh = {k: np.empty((R, N, 3), dtype=np.float32) for k in cfg["kernels"]}
-        fh = {k: np.ascontiguousarray(fs[k]) for k in cfg["kernels"]}
-        for _ in range(2):
-            for k in cfg["kernels"]:
-                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], R, None, uh[k])
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            for k in cfg["kernels"]:
-                se.se_eval_host(plans[k].handle, se.KERNELS[k], xh, fh[k], R, None, uh[k])
-        dt = time.perf_counter() - t0
-        h2d = sum(xh.nbytes + fh[k].nbytes for k in cfg["kernels"])
-        d2h = sum(uh[k].nbytes for k in cfg["kernels"])
-        e2e = {"value": targets_per_step * args.steps / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+    hx = [np.ascontiguousarray(it["x"]) for it in items]
+    hf = [np.ascontiguousarray(it["f"]) for it in items]
+    hu = [np.empty((it["R"], it["N"], 3), dtype=it["f"].dtype) for it in items]
 
-    # the plain FP64 single-RHS form of the same workload and tolerance (comparison of the metric)
+    def step_host():
+        for it, xh, fh, uh in zip(items, hx, hf, hu):
+            se.se_eval_host(it["plan"].handle, se.KERNELS[it["kernel"]], xh, fh, it["R"], None, uh)
+
+    for _ in range(2):
+        step_host()
+    n_e2e = max(3, args.steps // 2) if len(items) > 4 else args.steps
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        step_host()
+    dt = time.perf_counter() - t0
+    e2e = {"value": targets_per_step * n_e2e / dt, "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(a.nbytes + b.nbytes for a, b in zip(hx, hf))),
+           "d2h_bytes_per_step": int(sum(u.nbytes for u in hu))}
+
+    # the plain FP64 form of the same workload and parameters (comparison of the metric): one
+    # RHS and one kernel per evaluation (a stokeslet + stresslet evaluation as two)
     fp64 = None
     if not args.no_fp64:
-        plans64, f64 = {}, {}
-        for k in cfg["kernels"]:
-            t = params[k]
-            plans64[k] = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp64",
-                                 stream=stream)
-            f64[k] = torch.tensor(fs[k].astype(np.float64), device=dev)
-        u64 = {k: torch.empty((1, N, 3), dtype=torch.float64, device=dev) for k in cfg["kernels"]}
+        plain = []
+        for it in items:
+            p64 = make_plan(cfg, it, "fp64", stream)[0] if prec == "fp64" else None
+            if p64 is None:
+                # the FP32 parameters, FP64 arithmetic; every kernel in the plan's tables
+                t = it["params"]
+                p64 = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp64",
+                              stream=stream)
+            f64 = torch.tensor(it["f"].astype(np.float64), device=dev)
+            parts = ([("stokeslet", f64[:, :, :3].contiguous()), ("stresslet", f64[:, :, 3:].contiguous())]
+                     if it["kernel"] == "stokeslet+stresslet" else [(it["kernel"], f64)])
+            plain.append((p64, parts, it["xdev"], torch.empty((it["N"], 3), dtype=torch.float64, device=dev)))
 
         def step64():
-            for k in cfg["kernels"]:
-                for r in range(R):
-                    plans64[k].evaluate(k, xdev, f64[k][r], out=u64[k])
+            for p64, parts, xdev, u64 in plain:
+                for k, f64 in parts:
+                    for r in range(f64.shape[0]):
+                        p64.evaluate(k, xdev, f64[r], out=u64)
 
-        for _ in range(3):
+        for _ in range(3 if len(items) <= 4 else 1):
             step64()
         torch.cuda.synchronize()
-        n64 = max(3, args.steps // 4)
+        n64 = max(3, args.steps // 4) if len(items) <= 4 else 3
         ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
         for s_ in range(n64):
             flush.zero_()
@@ -409,19 +484,30 @@ def main():
         torch.cuda.synchronize()
         t64 = sum(a.elapsed_time(b) for a, b in ev64)
         fp64 = {"value": targets_per_step * n64 / (t64 / 1e3), "unit": UNIT, "ms_per_step": t64 / n64,
-                "form": "FP64, one RHS per evaluation, same parameters"}
+                "form": "FP64, one RHS and one kernel per evaluation, same parameters"}
+        del plain
 
     # headline: the FP32 batched form (the metric compares it with the FP64 plain form); the
-    # eager per-call form, whose per-kernel events give the stage times and the roofline, beside it
+    # eager per-call form, whose per-evaluation events give the stage times and the roofline, beside it
     eager = {"value": value, "unit": UNIT, "ms_per_step": tot_ms / args.steps,
-             "form": "FP32, one se_eval call per kernel per step"}
+             "form": "FP32, one se_eval call per evaluation per step"}
     g_ms = max_over_ranks(graph["ms_per_step"] * args.steps, dist, dev)
     value = replica_value(targets_per_step, world, args.steps, g_ms)
+    if len(items) <= 4:
+        params = tparams
+    else:
+        params = {"evaluations": len(items),
+                  "N": [int(min(it["N"] for it in items)), int(max(it["N"] for it in items))],
+                  "M0": [min(it["params"]["M"][0] for it in items), max(it["params"]["M"][0] for it in items)],
+                  "P": sorted({it["params"]["P"] for it in items})}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": g_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": N, "n_rhs": R, "box": list(cfg["box"]),
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": int(sum(it["N"] for it in items if it["kernel"] == items[0]["kernel"])),
+                       "n_rhs": cfg.get("n_rhs", 1), "box": list(cfg["box"]),
                        "kernels": list(cfg["kernels"]), "periodicity": cfg["D"],
+                       "points": cfg.get("points", "uniform"),
                        "tol_rel": cfg["tol"], "window": cfg["window"], "params": params,
                        "selection": {"n_rc": cfg.get("n_rc"), "P_margin": cfg.get("P_margin", -1),
                                      "tol_requested": cfg["tol"] / 10.0},
@@ -433,18 +519,16 @@ def main():
 
     # ---- CPU baseline (rank 0, N = 1): the oracle on a bounded sample; also the GPU error there
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # a bounded sample (a few seconds of oracle work); the oracle's per-call cost (the
-        # k-space structure factors) is amortised over the sample's targets
-        ns = 1024 if N <= 50000 else 64
-        idx, ref, dt = oracle_sample(cfg, x, fs, ns)
-        err = {}
         from oracle import ewald as E
-        for k in cfg["kernels"]:
-            err[k] = E.rms_rel(udev[k][0].cpu().numpy()[idx].astype(np.float64), ref[k])
-        line["cpu_baseline"] = {"value": ns * len(cfg["kernels"]) / dt, "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": "%d sampled targets x %d kernels (RHS 0) against all %d sources" %
-                                          (ns, len(cfg["kernels"]), N)}
+        ns = ORACLE_SAMPLE[WORKLOAD][0]
+        res, dt = oracle_sample(cfg, items, ns)
+        err = {}
+        for it, idx, ref in res:
+            err[it["name"]] = E.rms_rel(it["udev"][0].cpu().numpy()[idx].astype(np.float64), ref)
+        nt = sum(len(idx) for _, idx, _ in res)
+        line["cpu_baseline"] = {"value": nt / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": "%d sampled targets of each of the first %d evaluations (RHS 0) "
+                                          "against all their sources" % (ns, len(res))}
         line["rms_rel_err_vs_oracle"] = err
     if rank == 0:
         print(json.dumps(line))

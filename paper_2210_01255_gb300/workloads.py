@@ -49,6 +49,12 @@ def strengths(kernel, n, seed, n_rhs=None):
     return rng.standard_normal(shape + (3,))
 
 
+def batch_sizes(n_cfg, lo, hi, seed):
+    """Point counts of n_cfg independent systems, log-uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    return np.round(np.exp(rng.uniform(np.log(lo), np.log(hi), n_cfg))).astype(int)
+
+
 def source_quantity(kernel, f):
     """Q of Eq. (vector-source-quantity) / (tensor-source-quantity) for one RHS; for the
     stokeslet + stresslet strengths (f, q, nu) the two quantities added."""
@@ -79,4 +85,13 @@ CONFIGS = {
                                        n_rc={"stresslet": 280.0, "rotlet": 140.0}, P_margin=0),
     "2p_stokeslet_n200000_rhs8": dict(D=2, box=(1.0, 1.0, 0.5), N=200000, kernels=("stokeslet",),
                                       tol=1e-6, prec="fp32", window="pkb", seed=2, n_rhs=8),
+    # free space, half the points uniform and half in a Gaussian cluster (sigma 0.05) at the
+    # centre; stokeslet and stresslet strengths (f, q, nu) evaluated together
+    "0p_stokeslet_stresslet_n1000000": dict(D=0, box=(1.0, 1.0, 1.0), N=1000000, points="clustered",
+                                            kernels=("stokeslet+stresslet",), tol=1e-6, prec="fp32",
+                                            window="pkb", seed=4, n_rhs=1),
+    # 64 independent singly periodic systems, N log-uniform in [2e3, 5e4], 16 RHS each
+    "1p_stokeslet_64cfg_rhs16": dict(D=1, box=(4.0, 1.0, 1.0), n_cfg=64, N_range=(2000, 50000),
+                                     kernels=("stokeslet",), tol=1e-6, prec="fp32", window="pkb", seed=5,
+                                     n_rhs=16),
 }
