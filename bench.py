@@ -148,25 +148,40 @@ def make_items(cfg):
     return items
 
 
-def tuned(cfg, item):
+def tuned(cfg, item, prec, stream, flags=0):
+    """The evaluation's parameters, chosen once and cached in the item: by the rules of
+    Sec. 4.6 (se_autotune), or by timing candidate plans on the evaluation's own device
+    arrays (se_autotune_timed) for workloads whose point distribution the uniform-case
+    neighbour count does not describe."""
+    import ctypes
     import paper_2210_01255_gb300 as se
     from paper_2210_01255_gb300 import workloads as W
-    # the selection targets E <= 10 tau (Sec. 4.6); ask for tol/10 so the result meets tol
-    k = item["kernel"]
-    Q = W.source_quantity(k, item["f"][0])
-    o = se.se_opts_default()
-    o.n_rc = cfg.get("n_rc", {}).get(k, 0.0)
-    o.P_margin = cfg.get("P_margin", -1)
-    return se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
+    if "tune" not in item:
+        # the selection targets E <= 10 tau (Sec. 4.6); ask for tol/10 so the result meets tol
+        k = item["kernel"]
+        Q = W.source_quantity(k, item["f"][0])
+        o = se.se_opts_default()
+        o.n_rc = cfg.get("n_rc", {}).get(k, 0.0)
+        o.P_margin = cfg.get("P_margin", -1)
+        if cfg.get("autotune") == "timed":
+            o.flags = flags
+            t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
+                                     cfg["tol"] / 10.0, cfg["window"], opts=o, prec=prec, stream=stream)
+        else:
+            t = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
+        t["opts"].kernel_mask = se.KERNELS[k]
+        item["tune"] = t
+    t = item["tune"]
+    o = se.se_opts()
+    ctypes.memmove(ctypes.byref(o), ctypes.byref(t["opts"]), ctypes.sizeof(o))
+    return t, o
 
 
 def make_plan(cfg, item, prec, stream, flags=0):
-    """A plan with the parameters the selection gives for this evaluation (its extended grid,
-    upsampling factors and kbar_* included), for this kernel only."""
+    """A plan with the evaluation's parameters (extended grid, upsampling factors and kbar_*
+    included), for its kernel only."""
     import paper_2210_01255_gb300 as se
-    t = tuned(cfg, item)
-    o = t["opts"]
-    o.kernel_mask = se.KERNELS[item["kernel"]]
+    t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
     o.flags = flags
     return se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], prec, opts=o,
                    stream=stream), dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
@@ -307,11 +322,11 @@ def main():
     items = make_items(cfg)
     stream = torch.cuda.current_stream()
     for it in items:
-        it["plan"], it["params"] = make_plan(cfg, it, prec, stream, flags)
-        it["grid_n"] = list(it["plan"].info().n)
         it["xdev"] = torch.tensor(it["x"], device=dev)
         it["fdev"] = torch.tensor(it["f"], device=dev)
         it["udev"] = torch.empty((it["R"], it["N"], 3), dtype=tdt, device=dev)
+        it["plan"], it["params"] = make_plan(cfg, it, prec, stream, flags)
+        it["grid_n"] = list(it["plan"].info().n)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
@@ -454,12 +469,8 @@ def main():
     if not args.no_fp64:
         plain = []
         for it in items:
-            p64 = make_plan(cfg, it, "fp64", stream)[0] if prec == "fp64" else None
-            if p64 is None:
-                # the FP32 parameters, FP64 arithmetic; every kernel in the plan's tables
-                t = it["params"]
-                p64 = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], "fp64",
-                              stream=stream)
+            # the same parameters in FP64 arithmetic
+            p64 = make_plan(cfg, it, "fp64", stream)[0]
             f64 = torch.tensor(it["f"].astype(np.float64), device=dev)
             parts = ([("stokeslet", f64[:, :, :3].contiguous()), ("stresslet", f64[:, :, 3:].contiguous())]
                      if it["kernel"] == "stokeslet+stresslet" else [(it["kernel"], f64)])
@@ -510,7 +521,9 @@ def main():
                        "points": cfg.get("points", "uniform"),
                        "tol_rel": cfg["tol"], "window": cfg["window"], "params": params,
                        "selection": {"n_rc": cfg.get("n_rc"), "P_margin": cfg.get("P_margin", -1),
-                                     "tol_requested": cfg["tol"] / 10.0},
+                                     "tol_requested": cfg["tol"] / 10.0,
+                                     "autotune": cfg.get("autotune", "rules"),
+                                     "timed_ms": [it["tune"].get("ms") for it in items[:4]]},
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "gridding": "tcgen05" if args.gridding == "tc" else "cuda cores",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -134,6 +134,34 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
                       int M[3], int* P);
 
 /*
+ * Parameter selection with measured costs. The rules of Sec. 4.6 fix r_c, M and P for a
+ * given xi at the tolerance; se_autotune takes xi from an average neighbour count n_rc that
+ * holds for uniform systems (Table 5, Sec. 5.2). For other point distributions (a dense
+ * cluster multiplies the real-space pairs) and for this GPU's cost balance, this function
+ * chooses the split by timing instead: n_rc is scaled by f^3 (r_c by f) over a geometric
+ * ladder f = 0.8^k around 1 (starting from io_opts->n_rc, or from the uniform rule when it is
+ * 0), se_autotune gives each candidate's parameters, and a plan of each candidate evaluates
+ * the caller's own sources and strengths (star form) once untimed and twice timed with CUDA
+ * events; the walk continues in the improving direction until two candidates are more than
+ * 10 % slower than the best, a candidate's grids would use more than half of the free device
+ * memory, or its grid is unsupported.
+ *   periodicity, box, kernel_mask, Q, tol_rel   as se_autotune (kernel_mask: one kernel or
+ *                SE_STOKESLET|SE_STRESSLET, as for se_eval).
+ *   n_src, src, strengths, n_rhs   the evaluation to time, as se_eval (device arrays).
+ *   window       the window of the plans (SE_WIN_*).
+ *   io_opts      in: as se_autotune, plus prec, stream and flags for the trial plans;
+ *                out: the chosen candidate's options (n_rc, Mext, s0, s_star, kbar_star, ...).
+ *   xi, rc, M, P out: the chosen parameters.
+ *   ms           out (may be NULL): the chosen candidate's measured time per evaluation.
+ * Synchronous: returns when the trials are done. Temporary device memory: one output array
+ * and the trial plans (one at a time).
+ */
+se_status se_autotune_timed(int periodicity, const double box[3], int kernel_mask, double Q,
+                            long long n_src, const double* src, const void* strengths, int n_rhs,
+                            double tol_rel, int window, se_opts* io_opts, double* xi, double* rc,
+                            int M[3], int* P, double* ms);
+
+/*
  * Evaluate the potential (Eqs. Dp-ewald-decomp / Dp-ewald-decomp-self).
  *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET or SE_STOKESLET|SE_STRESSLET.
  *   n_src, src   device double [n_src][3].

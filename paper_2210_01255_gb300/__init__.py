@@ -59,6 +59,9 @@ SIGNATURES = {
                                       ctypes.POINTER(se_opts)]),
     "se_autotune": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
                                    ctypes.c_double, ctypes.POINTER(se_opts), _D3, _D3, _I3, _I3]),
+    "se_autotune_timed": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                                         _P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                         ctypes.POINTER(se_opts), _D3, _D3, _I3, _I3, _D3]),
     "se_eval": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_longlong, _P, _P, ctypes.c_int,
                                ctypes.c_longlong, _P, _P]),
     "se_eval_parts": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_longlong, _P, _P,
@@ -139,6 +142,34 @@ def se_autotune(periodicity, box, kernel_mask, Q, N, tol_rel, opts=None, xi=0.0)
                             ctypes.byref(o), ctypes.byref(x), ctypes.byref(rc), M, ctypes.byref(P)),
           "se_autotune")
     return dict(xi=x.value, rc=rc.value, M=list(M), P=P.value, opts=o)
+
+
+def se_autotune_timed(periodicity, box, kernel_mask, Q, src, strengths, n_rhs, tol_rel, window="pkb",
+                      opts=None, prec="fp32", stream=None):
+    """Parameters chosen by timing candidate plans on the given device arrays (src (N, 3)
+    float64, strengths (n_rhs, N, c) in the precision prec); returns se_autotune's dict plus
+    the measured time per evaluation "ms"."""
+    import torch
+    o = opts if opts is not None else se_opts_default()
+    o.prec = FP32 if prec in ("fp32", FP32) else FP64
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    o.stream = ctypes.c_void_p(stream.cuda_stream)
+    b = (ctypes.c_double * 3)(*[float(v) for v in box])
+    x = ctypes.c_double()
+    rc = ctypes.c_double()
+    M = (ctypes.c_int * 3)()
+    P = ctypes.c_int()
+    ms = ctypes.c_double()
+    k = KERNELS.get(kernel_mask, kernel_mask)
+    src = src.contiguous()
+    strengths = strengths.contiguous()  # kept alive by this name until the call returns
+    check(lib().se_autotune_timed(int(periodicity), b, int(k), float(Q), src.shape[0], _ptr(src),
+                                  _ptr(strengths), int(n_rhs), float(tol_rel),
+                                  WINDOWS.get(window, window), ctypes.byref(o), ctypes.byref(x),
+                                  ctypes.byref(rc), M, ctypes.byref(P), ctypes.byref(ms)),
+          "se_autotune_timed")
+    return dict(xi=x.value, rc=rc.value, M=list(M), P=P.value, opts=o, ms=ms.value)
 
 
 def se_eval_parts(plan, kernel_mask, parts_mask, src, strengths, n_rhs, tgt, u):

@@ -1781,6 +1781,150 @@ extern "C" se_status se_eval_host(se_plan_h p, int kernel, long long n_src, cons
   return se_sync(p);
 }
 
+// ====================================================== parameter selection by measured cost
+//
+// se_autotune picks xi from an average neighbour count n_rc that holds for uniform systems
+// (Table 5). For other distributions the real-space work at that r_c can be orders of
+// magnitude off (a dense cluster multiplies the pairs), and on a GPU the balance between the
+// real-space and the Fourier-space work is not the one of the paper's CPU code either. For
+// any xi the tolerance rules of Sec. 4.6 fix r_c, M and P; what is left free is the split.
+// This chooses it by timing: n_rc is scaled by f^3 (r_c by f) over a geometric ladder of f
+// around 1, se_autotune gives each candidate's parameters, a plan is built and the caller's
+// own evaluation is run once untimed (it sizes the plan's buffers) and twice timed with
+// events on the plan's stream; the fastest candidate wins.
+
+namespace {
+
+struct TimedCand {
+  double f = 0, ms = 1e300, xi = 0, rc = 0;
+  int M[3] = {0, 0, 0}, P = 0;
+  se_opts o;
+};
+
+se_status timed_trial(int D, const double* box, int kernel, double Q, long long n_src, const double* src,
+                      const void* strengths, int n_rhs, double tol_rel, int window, const se_opts& io,
+                      double nrc, size_t mem_cap, void* u, cudaEvent_t e0, cudaEvent_t e1, TimedCand* c) {
+  se_opts o = io;
+  o.n_rc = nrc;
+  double xi = 0, rc = 0;
+  int M[3], P;
+  SE_TRY(se_autotune(D, box, kernel, Q, n_src, tol_rel, &o, &xi, &rc, M, &P));
+  o.kernel_mask = kernel;
+  o.Q = Q;
+  se_plan_h p = nullptr;
+  SE_TRY(se_plan_create(&p, D, box, xi, rc, M, P, window, &o));
+  // device memory of the Fourier part: spread grid, spectrum and output grid
+  const size_t G = (size_t)p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
+  const size_t es = p->prec == SE_FP32 ? 4 : 8;
+  const size_t C = (size_t)kernel_comps(kernel) * n_rhs, NC = 3 * (size_t)n_rhs;
+  if (G * (2 * C + NC) * es > mem_cap) {
+    se_destroy(p);
+    return SE_ERR_NOMEM;
+  }
+  cudaStream_t st = p->stream;
+  se_status s = se_eval(p, kernel, n_src, src, strengths, n_rhs, 0, nullptr, u);
+  if (s == SE_OK) s = se_sync(p);
+  float best = 3e38f;
+  for (int r = 0; r < 2 && s == SE_OK; ++r) {
+    if (cudaEventRecord(e0, st) != cudaSuccess) s = SE_ERR_CUDA;
+    if (s == SE_OK) s = se_eval(p, kernel, n_src, src, strengths, n_rhs, 0, nullptr, u);
+    if (s == SE_OK && cudaEventRecord(e1, st) != cudaSuccess) s = SE_ERR_CUDA;
+    if (s == SE_OK) s = se_sync(p);
+    float ms = 0;
+    if (s == SE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = SE_ERR_CUDA;
+    if (s == SE_OK) best = std::min(best, ms);
+  }
+  se_destroy(p);
+  if (s != SE_OK) return s;
+  c->ms = best;
+  c->xi = xi;
+  c->rc = rc;
+  for (int d = 0; d < 3; ++d) c->M[d] = M[d];
+  c->P = P;
+  c->o = o;
+  return SE_OK;
+}
+
+}  // namespace
+
+extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_mask, double Q, long long n_src,
+                                       const double* src, const void* strengths, int n_rhs, double tol_rel,
+                                       int window, se_opts* io, double* xi_out, double* rc_out, int M_out[3],
+                                       int* P_out, double* ms_out) {
+  if (!box || !io || !xi_out || !rc_out || !M_out || !P_out || !src || !strengths) return SE_ERR_ARG;
+  if (n_src < 1 || n_src > 0x7fffffffLL || n_rhs < 1 || !(tol_rel > 0)) return SE_ERR_ARG;
+  if (kernel_mask != SE_STOKESLET && kernel_mask != SE_ROTLET && kernel_mask != SE_STRESSLET &&
+      kernel_mask != SE_KERNEL_ST)
+    return SE_ERR_ARG;
+  // the reference point: the caller's n_rc, or the uniform-case rule's, recovered from its r_c
+  double nrc0 = io->n_rc;
+  if (!(nrc0 > 0)) {
+    se_opts o = *io;
+    double xi = 0, rc = 0;
+    int M[3], P;
+    SE_TRY(se_autotune(D, box, kernel_mask, Q, n_src, tol_rel, &o, &xi, &rc, M, &P));
+    nrc0 = 4.0 / 3.0 * M_PI * rc * rc * rc * (double)n_src / (box[0] * box[1] * box[2]);
+  }
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return SE_ERR_CUDA;
+  const size_t mem_cap = free_b / 2;
+  const size_t es = io->prec == SE_FP32 ? 4 : 8;
+  void* u = nullptr;
+  if (cudaMalloc(&u, es * 3 * (size_t)n_rhs * n_src) != cudaSuccess) return SE_ERR_NOMEM;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  se_status st = SE_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SE_ERR_CUDA;
+  TimedCand best;
+  const double step = 0.8;  // ratio of successive r_c candidates
+  auto run = [&](double f, TimedCand* c) {
+    c->f = f;
+    return timed_trial(D, box, kernel_mask, Q, n_src, src, strengths, n_rhs, tol_rel, window, *io,
+                       nrc0 * f * f * f, mem_cap, u, e0, e1, c);
+  };
+  // f = 1, then one step down; walk in the better direction while the time keeps improving
+  // (two candidates more than 10 % slower than the best, a candidate that does not fit in
+  // memory or an unsupported grid end the walk)
+  if (st == SE_OK) {
+    TimedCand c1, c2;
+    st = run(1.0, &c1);
+    if (st == SE_OK) {
+      best = c1;
+      se_status s2 = run(step, &c2);
+      const bool down = s2 == SE_OK && c2.ms < c1.ms;
+      if (s2 == SE_OK && c2.ms < best.ms) best = c2;
+      if (s2 != SE_OK && s2 != SE_ERR_NOMEM && s2 != SE_ERR_UNSUPPORTED) st = s2;
+      double f = down ? step * step : 1.0 / step;
+      int worse = 0;
+      for (int k = 0; k < 14 && st == SE_OK && worse < 2; ++k, f = down ? f * step : f / step) {
+        TimedCand c;
+        se_status s = run(f, &c);
+        if (s == SE_ERR_NOMEM || s == SE_ERR_UNSUPPORTED) break;
+        if (s != SE_OK) {
+          st = s;
+          break;
+        }
+        if (c.ms < best.ms) {
+          best = c;
+          worse = 0;
+        } else if (c.ms > 1.1 * best.ms) {
+          ++worse;
+        }
+      }
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(u);
+  if (st != SE_OK) return st;
+  *io = best.o;
+  *xi_out = best.xi;
+  *rc_out = best.rc;
+  for (int d = 0; d < 3; ++d) M_out[d] = best.M[d];
+  *P_out = best.P;
+  if (ms_out) *ms_out = best.ms;
+  return SE_OK;
+}
+
 // ====================================================== allocation-free real-space sum
 //
 // Some callers cannot allocate device memory while they run: code embedded in a framework

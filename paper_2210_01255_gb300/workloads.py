@@ -86,10 +86,11 @@ CONFIGS = {
     "2p_stokeslet_n200000_rhs8": dict(D=2, box=(1.0, 1.0, 0.5), N=200000, kernels=("stokeslet",),
                                       tol=1e-6, prec="fp32", window="pkb", seed=2, n_rhs=8),
     # free space, half the points uniform and half in a Gaussian cluster (sigma 0.05) at the
-    # centre; stokeslet and stresslet strengths (f, q, nu) evaluated together
+    # centre; stokeslet and stresslet strengths (f, q, nu) evaluated together. The uniform-case
+    # neighbour count puts ~1.4e11 pairs inside r_c here, so the split is chosen by timing.
     "0p_stokeslet_stresslet_n1000000": dict(D=0, box=(1.0, 1.0, 1.0), N=1000000, points="clustered",
                                             kernels=("stokeslet+stresslet",), tol=1e-6, prec="fp32",
-                                            window="pkb", seed=4, n_rhs=1),
+                                            window="pkb", seed=4, n_rhs=1, autotune="timed"),
     # 64 independent singly periodic systems, N log-uniform in [2e3, 5e4], 16 RHS each
     "1p_stokeslet_64cfg_rhs16": dict(D=1, box=(4.0, 1.0, 1.0), n_cfg=64, N_range=(2000, 50000),
                                      kernels=("stokeslet",), tol=1e-6, prec="fp32", window="pkb", seed=5,

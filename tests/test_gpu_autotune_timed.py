@@ -1,0 +1,71 @@
+"""Parameter selection by measured cost (se_autotune_timed), through the C ABI.
+
+The tolerance rules of Sec. 4.6 still fix r_c, M and P for every candidate xi, so whatever
+split the timing picks, the result must meet the tolerance: checked against the oracle on a
+clustered free-space system (where the uniform-case neighbour count of Table 5 overestimates
+the useful r_c by far) and on a uniform triply periodic one."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_2210_01255_gb300 as se  # noqa: E402
+from paper_2210_01255_gb300 import workloads as W  # noqa: E402
+from oracle import ewald as E  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+ST = "stokeslet+stresslet"
+
+
+def timed_plan(D, box, kernel, x, f, tol, prec):
+    xt = torch.tensor(x, device="cuda")
+    ft = torch.tensor(f, dtype=torch.float32 if prec == "fp32" else torch.float64, device="cuda")
+    Q = W.source_quantity(kernel, f[0] if f.ndim == 3 else f)
+    t = se.se_autotune_timed(D, box, kernel, Q, xt, ft, 1, tol, "pkb", prec=prec)
+    plan = se.Plan(D, box, t["xi"], t["rc"], t["M"], t["P"], "pkb", prec, opts=t["opts"])
+    u = plan.evaluate(kernel, xt, ft)
+    plan.sync()
+    return t, u.cpu().numpy().astype(np.float64)
+
+
+def test_clustered_free_space_fused():
+    """0P stokeslet + stresslet, N = 2e5 (half in a Gaussian cluster of width 0.05), FP32 at
+    1e-6: the timed choice has a smaller r_c than the uniform-case rule and meets the
+    tolerance at 64 sampled targets."""
+    box = (1.0, 1.0, 1.0)
+    N = 200000
+    x = W.clustered_points(N, seed=21)
+    f = W.strengths(ST, N, seed=22)
+    t, u = timed_plan(0, box, ST, x, f, 1e-7, "fp32")
+    rule = se.se_autotune(0, box, se.KERNELS[ST], W.source_quantity(ST, f), N, 1e-7)
+    assert t["rc"] < rule["rc"] and t["ms"] > 0
+    idx = np.random.default_rng(23).choice(N, 64, replace=False)
+    ref = (E.potential(0, box, "stokeslet", x, f[:, :3], targets=x[idx])
+           + E.potential(0, box, "stresslet", x, f[:, 3:], targets=x[idx]))
+    assert E.rms_rel(u[idx], ref) < 1e-5
+
+
+@pytest.mark.parametrize("prec,tol,bar", [("fp32", 1e-7, 1e-5), ("fp64", 1e-10, 1e-9)])
+def test_uniform_periodic_meets_tolerance(prec, tol, bar):
+    """3P stresslet, N = 20000 uniform: the timed choice meets the tolerance at 128 targets."""
+    box = (1.0, 1.0, 1.0)
+    N = 20000
+    x = W.uniform_points(N, box, seed=24)
+    f = W.strengths("stresslet", N, seed=25)
+    t, u = timed_plan(3, box, "stresslet", x, f, tol, prec)
+    idx = np.random.default_rng(26).choice(N, 128, replace=False)
+    ref = E.potential(3, box, "stresslet", x, f, targets=x[idx])
+    assert E.rms_rel(u[idx], ref) < bar
+
+
+def test_invalid_kernel_mask():
+    box = (1.0, 1.0, 1.0)
+    x = torch.tensor(W.uniform_points(100, box, seed=27), device="cuda")
+    f = torch.zeros((1, 100, 3), dtype=torch.float32, device="cuda")
+    with pytest.raises(se.SeError) as e:
+        se.se_autotune_timed(3, box, se.STOKESLET | se.ROTLET, 1.0, x, f, 1, 1e-6, "pkb", prec="fp32")
+    assert e.value.code == -1
