@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "3p_stresslet_rotlet_n20000"   # default (--workload selects another configuration)
+P_MARGIN = None   # --p-margin: overrides the workload's window margin of the selection
 METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
 METRIC = METRIC_FMT % "3P stresslet+rotlet, N=20000"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
@@ -47,8 +48,10 @@ ORACLE_SAMPLE = {"3p_stresslet_rotlet_n20000": (1024, 512), "2p_stokeslet_n20000
 UNIT = "targets/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
 COMPS = {"stokeslet": 3, "rotlet": 3, "stresslet": 6, "stokeslet+stresslet": 9}
-# FP32 operations per real-space pair (separation, rsqrt, exp, erfc fit, the kernel's terms)
+# FP32 operations per real-space pair: 60 with one RHS (separation, rsqrt, exp, erfc fit,
+# the kernel's terms), plus the kernel's terms for every further RHS
 PAIR_FLOPS = {"stokeslet": 60, "rotlet": 60, "stresslet": 60, "stokeslet+stresslet": 75}
+PAIR_FLOPS_RHS = {"stokeslet": 18, "rotlet": 15, "stresslet": 38, "stokeslet+stresslet": 56}
 
 
 def peaks():
@@ -163,6 +166,8 @@ def tuned(cfg, item, prec, stream, flags=0):
         o = se.se_opts_default()
         o.n_rc = cfg.get("n_rc", {}).get(k, 0.0)
         o.P_margin = cfg.get("P_margin", -1)
+        if P_MARGIN is not None:
+            o.P_margin = P_MARGIN
         if cfg.get("autotune") == "timed":
             o.flags = flags
             t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
@@ -283,7 +288,7 @@ def run_reference(args):
 
 
 def main():
-    global WORKLOAD, METRIC
+    global WORKLOAD, METRIC, P_MARGIN
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -295,9 +300,12 @@ def main():
                     help="configuration from paper_2210_01255_gb300.workloads.CONFIGS")
     ap.add_argument("--gridding", choices=["cuda", "tc"], default="cuda",
                     help="FP32 gridding on the CUDA cores (default) or the tensor cores (tcgen05)")
+    ap.add_argument("--p-margin", type=int, default=None,
+                    help="window points added by the error-pollution rule (default: the workload's)")
     args = ap.parse_args()
     WORKLOAD = args.workload
     METRIC = METRIC_FMT % METRIC_NAMES[WORKLOAD]
+    P_MARGIN = args.p_margin
     if args.impl == "reference":
         return run_reference(args)
 
@@ -426,7 +434,7 @@ def main():
             hbm["scale"] = hbm.get("scale", 0.0) + (C + 3 * R) * 8 * H
         np_ = real_pairs(cfg, it, it["params"]["rc"])
         pairs += np_
-        work["real"] += PAIR_FLOPS[it["kernel"]] * np_
+        work["real"] += (PAIR_FLOPS[it["kernel"]] + PAIR_FLOPS_RHS[it["kernel"]] * (R - 1)) * np_
     # the dominant kernel among those with a per-launch algorithmic work figure
     dom = max(work, key=lambda n: per_stage[n])
     ach = work[dom] / (per_stage[dom] * 1e-3) / 1e12
@@ -520,7 +528,8 @@ def main():
                        "kernels": list(cfg["kernels"]), "periodicity": cfg["D"],
                        "points": cfg.get("points", "uniform"),
                        "tol_rel": cfg["tol"], "window": cfg["window"], "params": params,
-                       "selection": {"n_rc": cfg.get("n_rc"), "P_margin": cfg.get("P_margin", -1),
+                       "selection": {"n_rc": cfg.get("n_rc"),
+                                     "P_margin": P_MARGIN if P_MARGIN is not None else cfg.get("P_margin", -1),
                                      "tol_requested": cfg["tol"] / 10.0,
                                      "autotune": cfg.get("autotune", "rules"),
                                      "timed_ms": [it["tune"].get("ms") for it in items[:4]]},
