@@ -287,6 +287,105 @@ def run_reference(args):
     return 0
 
 
+# Neighbour counts N_rc of the timing experiments (Sec. 5.2), per system, kernel and D
+NRC_TABLE = {"uniform": {"stokeslet": (2500, 950, 450, 400), "rotlet": (2500, 950, 450, 400),
+                         "stresslet": (6000, 1600, 800, 800)},
+             "clustered": {"stokeslet": (800, 300, 170, 120), "rotlet": (800, 300, 170, 120),
+                           "stresslet": (3000, 1200, 370, 300)}}
+
+
+def unit_q_strengths(kernel, n, seed):
+    """Strengths N(0,1) (stresslet: q N(0,1), nu unit) scaled so that the source quantity is
+    Q = 1, as in the timing experiments (L = 1, Q = 1)."""
+    from paper_2210_01255_gb300 import workloads as W
+    f = W.strengths(kernel, n, seed)
+    f[:, :3] /= math.sqrt(W.source_quantity(kernel, f))
+    return f
+
+
+def timed_eval(plan, kernel, xdev, fdev, reps=3):
+    """Median of reps evaluations (CUDA events on the plan's stream) after one untimed one."""
+    import torch
+    plan.evaluate(kernel, xdev, fdev)
+    plan.sync()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(plan.stream)
+        u = plan.evaluate(kernel, xdev, fdev)
+        b.record(plan.stream)
+        plan.sync()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts)), u
+
+
+def experiment_plan(D, kernel, N, tol_abs, prec, stream, n_rc=0.0, xi=0.0):
+    import paper_2210_01255_gb300 as se
+    o = se.se_opts_default()
+    o.tol_abs = tol_abs
+    o.n_rc = n_rc
+    t = se.se_autotune(D, (1.0, 1.0, 1.0), se.KERNELS[kernel], 1.0, N, 0.0, opts=o, xi=xi)
+    t["opts"].kernel_mask = se.KERNELS[kernel]
+    plan = se.Plan(D, (1.0, 1.0, 1.0), t["xi"], t["rc"], t["M"], t["P"], "pkb", prec, opts=t["opts"], stream=stream)
+    return plan, t
+
+
+def run_experiment(args):
+    """The timing experiments of Sec. 5.2 on this GPU (FP64, PKB, L = 1, Q = 1, targets =
+    sources, precomputation excluded). One JSON line per data point.
+    complexity: tol_abs = 1e-8, N = 12,500 x 2^j, N_rc fixed per system, kernel and D (the
+    table of Sec. 5.2), xi from the real-space estimate, the rest by the selection procedure.
+    time_vs_error: N = 1e5, uniform, xi fixed at its complexity-test value for N = 1e5, tol_abs
+    = 1e-2 ... 1e-12; the relative rms error against the same method at tol_abs = 1e-14."""
+    import torch
+    from paper_2210_01255_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    Ds = [int(d) for d in args.exp_d.split(",")]
+    kernels = args.exp_kernels.split(",")
+    if args.experiment == "complexity":
+        for system in args.exp_systems.split(","):
+            for D in Ds:
+                for k in kernels:
+                    for j in range(args.exp_jmax + 1):
+                        N = 12500 * 2 ** j
+                        x = (W.uniform_points(N, (1, 1, 1), seed=100 + j) if system == "uniform"
+                             else W.two_cube_points(N, seed=100 + j))
+                        f = unit_q_strengths(k, N, seed=200 + j)
+                        plan, t = experiment_plan(D, k, N, 1e-8, "fp64", stream, n_rc=NRC_TABLE[system][k][D])
+                        xd = torch.tensor(x, device="cuda")
+                        fd = torch.tensor(f, device="cuda")
+                        ms, _ = timed_eval(plan, k, xd, fd, reps=args.exp_reps)
+                        print(json.dumps({"experiment": "complexity", "system": system, "D": D, "kernel": k, "N": N,
+                                          "xi": t["xi"], "rc": t["rc"], "M": t["M"], "P": t["P"], "ms": ms,
+                                          "us_per_point": 1e3 * ms / N}), flush=True)
+                        del plan, xd, fd
+                        torch.cuda.empty_cache()
+        return 0
+    N = 100000
+    x = W.uniform_points(N, (1, 1, 1), seed=300)
+    xd = torch.tensor(x, device="cuda")
+    for D in Ds:
+        for k in kernels:
+            f = unit_q_strengths(k, N, seed=301)
+            fd = torch.tensor(f, device="cuda")
+            _, t8 = experiment_plan(D, k, N, 1e-8, "fp64", stream, n_rc=NRC_TABLE["uniform"][k][D])
+            ref_plan, _ = experiment_plan(D, k, N, 1e-14, "fp64", stream, xi=t8["xi"])
+            _, uref = timed_eval(ref_plan, k, xd, fd, reps=1)
+            uref = uref.cpu().numpy()
+            del ref_plan
+            for p in range(2, 13):
+                plan, t = experiment_plan(D, k, N, 10.0 ** -p, "fp64", stream, xi=t8["xi"])
+                ms, u = timed_eval(plan, k, xd, fd, reps=args.exp_reps)
+                err = float(np.sqrt(((u.cpu().numpy() - uref) ** 2).sum() / (uref ** 2).sum()))
+                print(json.dumps({"experiment": "time_vs_error", "D": D, "kernel": k, "N": N, "xi": t["xi"],
+                                  "tol_abs": 10.0 ** -p, "rc": t["rc"], "M": t["M"], "P": t["P"], "ms": ms,
+                                  "rms_rel_err": err}), flush=True)
+                del plan
+                torch.cuda.empty_cache()
+    return 0
+
+
 def main():
     global WORKLOAD, METRIC, P_MARGIN
     ap = argparse.ArgumentParser()
@@ -302,7 +401,16 @@ def main():
                     help="FP32 gridding on the CUDA cores (default) or the tensor cores (tcgen05)")
     ap.add_argument("--p-margin", type=int, default=None,
                     help="window points added by the error-pollution rule (default: the workload's)")
+    ap.add_argument("--experiment", choices=["complexity", "time_vs_error"], default=None,
+                    help="the timing experiments of Sec. 5.2 instead of the benchmark line")
+    ap.add_argument("--exp-d", default="3,2,1,0")
+    ap.add_argument("--exp-kernels", default="stokeslet,stresslet")
+    ap.add_argument("--exp-systems", default="uniform,clustered")
+    ap.add_argument("--exp-jmax", type=int, default=6)
+    ap.add_argument("--exp-reps", type=int, default=3, help="timed evaluations per data point (median)")
     args = ap.parse_args()
+    if args.experiment:
+        return run_experiment(args)
     WORKLOAD = args.workload
     METRIC = METRIC_FMT % METRIC_NAMES[WORKLOAD]
     P_MARGIN = args.p_margin

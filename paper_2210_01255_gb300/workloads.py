@@ -29,6 +29,15 @@ def clustered_points(n, seed, sigma=0.05, centre=(0.5, 0.5, 0.5)):
     return out
 
 
+def two_cube_points(n, seed):
+    """The clustered system of the timing experiments (Sec. 5.2): n points uniform in the two
+    subdomains [0,1/3)^3 and [2/3,1)^3 of the unit cube, half in each."""
+    rng = np.random.default_rng(seed)
+    out = rng.random((n, 3)) / 3.0
+    out[n // 2:] += 2.0 / 3.0
+    return out
+
+
 def strengths(kernel, n, seed, n_rhs=None):
     """Stokeslet / rotlet: f ~ N(0,1)^3. Stresslet: (q, nu) with q ~ N(0,1)^3 and nu ~ N(0,1)^3
     normalised to unit length. Stokeslet + stresslet: (f, q, nu), f drawn first.

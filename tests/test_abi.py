@@ -58,6 +58,28 @@ def test_autotune_reproduces_table6_xi(key):
     assert abs(r["xi"] - TABLE6[key]) < 5e-5
 
 
+# The clustered-system columns of the same two tables: the neighbour counts N_rc (points only
+# in [0,1/3)^3 and [2/3,1)^3; N_rc still counts the mean concentration N / L^3) and the xi
+# they give at N = 1e5, tol_abs = 1e-8; passed to the selection through se_opts.n_rc.
+NRC_CLUSTERED = {("stokeslet", 0): 800, ("stokeslet", 1): 300, ("stokeslet", 2): 170, ("stokeslet", 3): 120,
+                 ("rotlet", 0): 800, ("rotlet", 1): 300, ("rotlet", 2): 170, ("rotlet", 3): 120,
+                 ("stresslet", 0): 3000, ("stresslet", 1): 1200, ("stresslet", 2): 370, ("stresslet", 3): 300}
+XI_CLUSTERED = {("stokeslet", 0): 34.2623, ("stokeslet", 1): 47.2969, ("stokeslet", 2): 57.0041,
+                ("stokeslet", 3): 63.9175, ("stresslet", 0): 25.2392, ("stresslet", 1): 34.3700,
+                ("stresslet", 2): 51.0933, ("stresslet", 3): 54.8344, ("rotlet", 0): 36.0043,
+                ("rotlet", 1): 50.1320, ("rotlet", 2): 60.7237, ("rotlet", 3): 68.2974}
+
+
+@pytest.mark.parametrize("key", sorted(XI_CLUSTERED))
+def test_autotune_reproduces_clustered_xi_from_n_rc(key):
+    kernel, D = key
+    o = se.se_opts_default()
+    o.tol_abs = 1e-8
+    o.n_rc = NRC_CLUSTERED[key]
+    r = se.se_autotune(D, (1, 1, 1), se.KERNELS[kernel], 1.0, 100000, 0.0, opts=o, xi=0.0)
+    assert abs(r["xi"] - XI_CLUSTERED[key]) < 5e-5
+
+
 def test_autotune_rules():
     # Sec. 4.6 steps on a case of Sec. 4.6 (N=1000, L=1, Q=1, xi=10)
     o = se.se_opts_default()
