@@ -11,7 +11,7 @@ Steps, in the paper's order and notation (Sec. 3.2-3.4, Alg. 1):
 followed by the self term (Eq. self-term) and, for the 3P stresslet, the k = 0 term
 (Eq. k0-stresslet-3p).
 
-Readings (also listed in the design doc):
+Readings of the paper taken here:
   * window taps: for a coordinate u = (x - o)/h in grid units, the P taps are
     j = floor(u) - P/2 + 1, ..., floor(u) + P/2 (so |jh - x| <= a_w = Ph/2);
   * FFT normalisation: the continuous transforms are replaced by the trapezoidal rule,
