@@ -146,7 +146,8 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * 10 % slower than the best, a candidate's grids would use more than half of the free device
  * memory, or its grid is unsupported.
  *   periodicity, box, kernel_mask, Q, tol_rel   as se_autotune (kernel_mask: one kernel or
- *                SE_STOKESLET|SE_STRESSLET, as for se_eval).
+ *                SE_STOKESLET|SE_STRESSLET, as for se_eval; tol_rel > 0, the absolute-tolerance
+ *                mode of se_autotune is not offered here). Invalid arguments: SE_ERR_ARG.
  *   n_src, src, strengths, n_rhs   the evaluation to time, as se_eval (device arrays).
  *   window       the window of the plans (SE_WIN_*).
  *   io_opts      in: as se_autotune, plus prec, stream and flags for the trial plans;
