@@ -262,6 +262,23 @@ se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h* plans, co
 se_status se_batch_launch(se_batch_h batch);
 void se_batch_destroy(se_batch_h batch);
 
+/*
+ * The same entry points under the names of the problem statement:
+ * se_plan         = se_plan_create (same arguments and behaviour).
+ * se_eval_batch   evaluates n_cfg independent configurations (star form, targets = sources),
+ *                 configuration i as se_eval(plans[i], kernel_mask[i], n_src[i], src[i],
+ *                 strengths[i], n_rhs[i], 0, NULL, u[i]), issued in order, each on its plan's
+ *                 stream (asynchronous; plans on different streams run concurrently). Returns
+ *                 the first error (SE_ERR_ARG for a NULL array or plan, before any work).
+ *                 For repeated evaluations of the same configurations, se_batch_create
+ *                 records them once into a CUDA graph that se_batch_launch replays.
+ */
+se_status se_plan(se_plan_h* out, int periodicity, const double box[3], double xi, double rc,
+                  const int M[3], int P, int window, const se_opts* opts);
+se_status se_eval_batch(const se_plan_h* plans, int n_cfg, const int* kernel_mask,
+                        const long long* n_src, const double* const* src,
+                        const void* const* strengths, const int* n_rhs, void* const* u);
+
 /* Human-readable name of a status code (static storage). */
 const char* se_status_str(se_status s);
 

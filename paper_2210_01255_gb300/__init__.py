@@ -78,6 +78,10 @@ SIGNATURES = {
                                        ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                        _I3, ctypes.POINTER(_P)]),
     "se_batch_launch": (ctypes.c_int, [_P]),
+    "se_plan": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _D3, ctypes.c_double, ctypes.c_double, _I3,
+                               ctypes.c_int, ctypes.c_int, ctypes.POINTER(se_opts)]),
+    "se_eval_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I3, ctypes.POINTER(ctypes.c_longlong),
+                                     ctypes.POINTER(_P), ctypes.POINTER(_P), _I3, ctypes.POINTER(_P)]),
     "se_batch_destroy": (None, [_P]),
     "se_real_noalloc": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
@@ -238,6 +242,20 @@ def se_batch_create(plans, kernel_masks, srcs, strengths, n_rhs, us):
                                 arr(ctypes.c_int, [int(r) for r in n_rhs]),
                                 arr(ctypes.c_void_p, [u.data_ptr() for u in us])), "se_batch_create")
     return h
+
+
+def se_eval_batch(plans, kernel_masks, srcs, strengths, n_rhs, us):
+    """Evaluate several independent configurations (star form) in one call, each on its
+    plan's stream. plans: handles; srcs / strengths / us: torch device tensors."""
+    n = len(plans)
+    arr = lambda t, vals: (t * n)(*vals)
+    check(lib().se_eval_batch(arr(ctypes.c_void_p, [p.value for p in plans]), n,
+                              arr(ctypes.c_int, [int(KERNELS.get(k, k)) for k in kernel_masks]),
+                              arr(ctypes.c_longlong, [int(s.shape[0]) for s in srcs]),
+                              arr(ctypes.c_void_p, [s.data_ptr() for s in srcs]),
+                              arr(ctypes.c_void_p, [f.data_ptr() for f in strengths]),
+                              arr(ctypes.c_int, [int(r) for r in n_rhs]),
+                              arr(ctypes.c_void_p, [u.data_ptr() for u in us])), "se_eval_batch")
 
 
 def se_batch_launch(batch):

@@ -25,6 +25,21 @@ def test_library_exports_every_declared_symbol():
     assert set(names) == set(se.SIGNATURES), "binding and header disagree"
 
 
+def test_problem_statement_entry_points_validate_without_gpu():
+    """se_plan rejects what se_plan_create rejects; se_eval_batch rejects NULL arrays and a
+    non-positive count before any device work."""
+    import ctypes
+    lib = se.lib()
+    h = ctypes.c_void_p()
+    box = (ctypes.c_double * 3)(1, 1, 1)
+    M = (ctypes.c_int * 3)(32, 32, 32)
+    assert lib.se_plan(ctypes.byref(h), 4, box, 10.0, 0.3, M, 8, 2, None) == -1   # periodicity
+    assert lib.se_plan(ctypes.byref(h), 3, box, 10.0, 0.3, M, 7, 2, None) == -1   # odd P
+    assert lib.se_eval_batch(None, 2, None, None, None, None, None, None) == -1
+    plans = (ctypes.c_void_p * 1)(None)
+    assert lib.se_eval_batch(plans, 0, None, None, None, None, None, None) == -1
+
+
 def test_status_strings():
     assert se.se_status_str(0) == "ok"
     assert "unsupported" in se.se_status_str(-7)

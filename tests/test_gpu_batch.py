@@ -100,3 +100,44 @@ def test_batch_graph_matches_individual_evaluations():
 def test_batch_64_configurations_16_rhs():
     """64 configurations, N log-uniform in [2e3, 5e4], 16 RHS each, one graph launch."""
     _run_batch(64, 2000, 50000, 70, 16, check_oracle=True)
+
+
+def test_eval_batch_one_call_matches_individual_evaluations():
+    """se_eval_batch: 5 configurations (mixed kernels, one on its own stream) in one call
+    equal the individual se_eval results; each compared with the oracle at sampled targets."""
+    cfgs = _configs(5, 2000, 6000, 90, 2)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    kernels = ["stokeslet", "stokeslet", "stresslet", "rotlet", "stokeslet+stresslet"]
+    plans, xs, fs, us, refs = [], [], [], [], []
+    for i, ((x, _), k) in enumerate(zip(cfgs, kernels)):
+        f = W.strengths(k, x.shape[0], seed=95 + i, n_rhs=2)
+        Q = W.source_quantity(k, f[0])
+        t = se.se_autotune(1, BOX, se.KERNELS[k], Q, x.shape[0], 1e-7)
+        o = t["opts"]
+        o.kernel_mask = se.KERNELS[k]
+        st = s2 if i == 3 else s1
+        p = se.Plan(1, BOX, t["xi"], t["rc"], t["M"], t["P"], "pkb", "fp64", opts=o, stream=st)
+        xt = torch.tensor(x, device="cuda")
+        ft = torch.tensor(f, device="cuda")
+        u_ref = p.evaluate(k, xt, ft)
+        p.sync()  # the copy below runs on torch's current stream
+        refs.append(u_ref.clone())
+        plans.append(p)
+        xs.append(xt)
+        fs.append(ft)
+        us.append(torch.full_like(refs[-1], float("nan")))
+    torch.cuda.synchronize()  # inputs and fills complete before the plans' streams write
+    se.se_eval_batch([p.handle for p in plans], kernels, xs, fs, [2] * 5, us)
+    for p in plans:
+        p.sync()
+    for i, (u, r) in enumerate(zip(us, refs)):
+        assert torch.equal(u, r) or float((u - r).abs().max() / r.abs().max()) < 1e-12, i
+        x = cfgs[i][0]
+        f = fs[i].cpu().numpy()[1]
+        idx = np.random.default_rng(7).choice(x.shape[0], 6, replace=False)
+        if kernels[i] == "stokeslet+stresslet":
+            e = (E.potential(1, BOX, "stokeslet", x, f[:, :3], targets=x[idx])
+                 + E.potential(1, BOX, "stresslet", x, f[:, 3:], targets=x[idx]))
+        else:
+            e = E.potential(1, BOX, kernels[i], x, f, targets=x[idx])
+        assert E.rms_rel(u[1].cpu().numpy()[idx], e) < 1e-6, i
