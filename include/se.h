@@ -23,6 +23,12 @@
  *       potential u:       [n_rhs][N_t][3], overwritten.
  *     With kernel_mask = STOKESLET|STRESSLET the strengths are [n_rhs][N][9] = (f, q, nu)
  *     and u is the sum of both flows.
+ *       harmonic field:    strengths [n_rhs][N][1] = q; u_j = sum q (x - y)_j / |x - y|^3, the
+ *                          field -grad H q of the harmonic kernel H = 1/r (electrostatics: the
+ *                          field of point charges). It is split and computed like the rotlet
+ *                          (both are first derivatives of H: the rotlet is the curl, this the
+ *                          gradient), with the same zero-mode convention (3P k = 0 term dropped,
+ *                          i.e. tin-foil boundary conditions) and no self or gauge term.
  *   - targets == NULL selects the star form (targets = sources, the self interaction
  *     omitted, Eq. periodic-potential-star). With explicit targets, a target that
  *     coincides exactly with a source is treated the same way for that source.
@@ -59,7 +65,7 @@ typedef enum {
   SE_ERR_CAPACITY = -8     /* the request exceeds a fixed capacity (see se_real_noalloc)    */
 } se_status;
 
-enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4 };
+enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4, SE_HARMONIC_FIELD = 8 };
 enum { SE_WIN_GAUSSIAN = 0, SE_WIN_KB = 1, SE_WIN_PKB = 2 };
 enum { SE_FP64 = 0, SE_FP32 = 1 };
 /* parts of the decomposition returned by se_eval_parts (bit mask) */
@@ -164,9 +170,11 @@ se_status se_autotune_timed(int periodicity, const double box[3], int kernel_mas
 
 /*
  * Evaluate the potential (Eqs. Dp-ewald-decomp / Dp-ewald-decomp-self).
- *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET or SE_STOKESLET|SE_STRESSLET.
+ *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET, SE_STOKESLET|SE_STRESSLET or
+ *                SE_HARMONIC_FIELD.
  *   n_src, src   device double [n_src][3].
- *   strengths    device [n_rhs][n_src][c], c = 3 (S, Omega), 6 (T) or 9 (S|T); float in an
+ *   strengths    device [n_rhs][n_src][c], c = 3 (S, Omega), 6 (T), 9 (S|T) or 1 (harmonic
+ *                field); float in an
  *                SE_FP32 plan, double in an SE_FP64 plan.
  *   n_rhs        number of right-hand sides (strength vectors at the same points), >= 1.
  *   n_tgt, tgt   device double [n_tgt][3], or tgt = NULL for the star form (n_tgt ignored).

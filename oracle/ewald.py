@@ -129,10 +129,32 @@ def parts(D, L, kernel, x, f, targets=None, xi=None, rc=None, kmax=None):
 
 def potential(D, L, kernel, x, f, targets=None, xi=None):
     """The D-periodic potential u^{DP} (star form when targets is None), FP64, (Nt,3)."""
+    if kernel in ("harmonic_field", 8):
+        return harmonic_field(D, L, x, f, targets, xi)
     p = parts(D, L, kernel, x, f, targets, xi)
     if D == 0:
         return p["direct"]
     return p["real"] + p["fourier"] + p["k0"] + p["self"]
+
+
+def harmonic_field(D, L, x, q, targets=None, xi=None):
+    """The D-periodic field E_j = sum q (x - y)_j / |x - y|^3 of charges q ((N,) or (N,1)).
+
+    With H = 1/r the rotlet is Omega_jl = -eps_jlm d_m H and the field is E_j = -d_j H q, so
+    E_1 = (Omega (q e_3))_2, E_2 = (Omega (q e_1))_3, E_3 = (Omega (q e_2))_1: the field is
+    three rotlet sums with torques along the axes. Periodisation is linear, so the identity
+    holds for the D-periodic sums with the rotlet's conventions (3P zero mode dropped; no self
+    term in the star form)."""
+    q = np.asarray(q, dtype=float).reshape(-1)
+    out = None
+    for comp, axis, row in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
+        f = np.zeros((q.shape[0], 3))
+        f[:, axis] = q
+        u = potential(D, L, "rotlet", x, f, targets, xi)
+        if out is None:
+            out = np.zeros_like(u)
+        out[:, comp] = u[:, row]
+    return out
 
 
 def Knu(nu, a, b):

@@ -12,13 +12,13 @@ import os
 
 from . import build as _build
 
-STOKESLET, ROTLET, STRESSLET = 1, 2, 4
+STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD = 1, 2, 4, 8
 WIN_GAUSSIAN, WIN_KB, WIN_PKB = 0, 1, 2
 FP64, FP32 = 0, 1
 PART_REAL, PART_FOURIER, PART_CORR, PART_ALL = 1, 2, 4, 7
 FLAG_TC_GRIDDING = 1  # se_opts.flags: FP32 gridding (P <= 16) on the tensor cores (tcgen05)
 KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
-           "stokeslet+stresslet": STOKESLET | STRESSLET}
+           "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD}
 WINDOWS = {"gaussian": WIN_GAUSSIAN, "kb": WIN_KB, "pkb": WIN_PKB}
 
 SE_OK = 0

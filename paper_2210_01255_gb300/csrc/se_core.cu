@@ -251,8 +251,8 @@ __device__ __forceinline__ void put_sym6(const T* __restrict__ q, const T* __res
   o[5] = T(0.5) * (q[1] * nu[2] + q[2] * nu[1]);
 }
 
-// spread components of point i at sorted slot s, per RHS: S, Omega: f; T: the 6 symmetric
-// components of q nu^T; S|T: f followed by those 6
+// spread components of point i at sorted slot s, per RHS: S, Omega: f; harmonic field: q;
+// T: the 6 symmetric components of q nu^T; S|T: f followed by those 6
 template <typename T>
 __device__ __forceinline__ void put_spread_strengths(int kernel, const T* __restrict__ f, int n, int n_rhs, int i,
                                                      int s, T* __restrict__ sf) {
@@ -273,9 +273,9 @@ __device__ __forceinline__ void put_spread_strengths(int kernel, const T* __rest
       put_sym6(fr + 3, fr + 6, o + 3);
     }
   } else {
-    const int C = 3 * n_rhs;
+    const int c = kernel_comps(kernel), C = c * n_rhs;
     for (int r = 0; r < n_rhs; ++r)
-      for (int l = 0; l < 3; ++l) sf[(size_t)s * C + 3 * r + l] = f[((size_t)r * n + i) * 3 + l];
+      for (int l = 0; l < c; ++l) sf[(size_t)s * C + c * r + l] = f[((size_t)r * n + i) * c + l];
   }
 }
 
@@ -480,13 +480,17 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
     const T g = a.t.g0[i0] * a.t.g1[i1] * a.t.g2[i2];
     if (a.t.atab) {
       s = a.t.atab[idx] * g;
-      if (kernel != SE_ROTLET) s *= T(1) + kk * a.inv4xi2;
+      if (!harmonic_family(kernel)) s *= T(1) + kk * a.inv4xi2;
     } else {
       s = regular_scalar<T>(kernel, kk, a.inv4xi2) * g;
     }
   }
   const int cin = kernel_comps(kernel);
-  for (int r = 0; r < n_rhs; ++r) {
+  // in place: the 3 outputs of RHS r go to components 3r..3r+2, its inputs are cin r ..;
+  // with cin >= 3 ascending r never overwrites an input still to be read, with cin = 1
+  // descending r does (the buffer holds max(cin, 3) n_rhs components)
+  for (int rr = 0; rr < n_rhs; ++rr) {
+    const int r = cin >= 3 ? rr : n_rhs - 1 - rr;
     T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
@@ -708,6 +712,19 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
         acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
         acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
         acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
+      }
+    }
+  } else if (KERNEL == SE_HARMONIC_FIELD) {
+    // -grad of the screened harmonic kernel erfc(xi r)/r: r_j / r^2 (erfc/r + 2 xi e/sqrt pi) q
+    // (the rotlet's radial factor, Eq. rotlet-real, with the gradient in place of the curl)
+    const T c1 = (ec + c2pi * e) * inv2;
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T cq = c1 * f[r];
+        acc[3 * r + 0] += cq * r0;
+        acc[3 * r + 1] += cq * r1;
+        acc[3 * r + 2] += cq * r2;
       }
     }
   } else if (KERNEL == SE_ROTLET) {
@@ -1223,7 +1240,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   g.inv_h = 1.0 / h;
   g.P = P;
   const int fM = o.f_M > 0 ? o.f_M : 4;
-  const int kmask = o.kernel_mask ? o.kernel_mask : 7;
+  const int kmask = rule_mask(o.kernel_mask ? o.kernel_mask : 7);
   for (int d = 0; d < 3; ++d) {
     g.L[d] = box[d];
     g.periodic[d] = d < D;
@@ -1487,6 +1504,7 @@ void real_launch(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
   if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, st, a);
   else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, st, a);
   else if (a.kernel == SE_STRESSLET) real_launch_k<T, SE_STRESSLET, R>(p, st, a);
+  else if (a.kernel == SE_HARMONIC_FIELD) real_launch_k<T, SE_HARMONIC_FIELD, R>(p, st, a);
   else real_launch_k<T, SE_KERNEL_ST, R>(p, st, a);
 }
 
@@ -1638,7 +1656,8 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
     void *grid, *spec = nullptr, *ugrid;
     SE_TRY(buf(p, "grid", sizeof(T) * C * G, &grid));
-    if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
+    // the scaling step writes NC components in place over C (the harmonic field: C < NC)
+    if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * std::max(C, NC) * H, &spec));
     SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
     if (g.n[0] != g.m[0] || g.n[1] != g.m[1] || g.n[2] != g.m[2])
       SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));  // zero padding (D = 0)
@@ -1740,7 +1759,8 @@ extern "C" se_status se_eval_parts(se_plan_h p, int kernel, int parts, long long
   if (!p || !u || (n_src > 0 && (!src || !strengths))) return SE_ERR_ARG;
   if (n_src < 0 || n_src > 0x7fffffffLL || n_rhs < 1) return SE_ERR_ARG;
   if (tgt && (n_tgt < 0 || n_tgt > 0x7fffffffLL)) return SE_ERR_ARG;
-  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET && kernel != SE_KERNEL_ST)
+  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET && kernel != SE_KERNEL_ST &&
+      kernel != SE_HARMONIC_FIELD)
     return SE_ERR_ARG;
   if (parts <= 0 || parts > SE_PART_ALL) return SE_ERR_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return SE_ERR_CUDA;
@@ -1854,7 +1874,7 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   if (!box || !io || !xi_out || !rc_out || !M_out || !P_out || !src || !strengths) return SE_ERR_ARG;
   if (n_src < 1 || n_src > 0x7fffffffLL || n_rhs < 1 || !(tol_rel > 0)) return SE_ERR_ARG;
   if (kernel_mask != SE_STOKESLET && kernel_mask != SE_ROTLET && kernel_mask != SE_STRESSLET &&
-      kernel_mask != SE_KERNEL_ST)
+      kernel_mask != SE_KERNEL_ST && kernel_mask != SE_HARMONIC_FIELD)
     return SE_ERR_ARG;
   // the reference point: the caller's n_rc, or the uniform-case rule's, recovered from its r_c
   double nrc0 = io->n_rc;

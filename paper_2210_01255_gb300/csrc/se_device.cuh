@@ -37,6 +37,12 @@ __device__ __forceinline__ void apply_regular(int kernel, T s, T k0, T k1, T k2,
       ore[j] = s * (-kk * re[j] + kv[j] * kfr);
       oim[j] = s * (-kk * im[j] + kv[j] * kfi);
     }
+  } else if (kernel == SE_HARMONIC_FIELD) {
+    // gradient of the harmonic kernel: -i k_j q (one input component)
+    for (int j = 0; j < 3; ++j) {
+      ore[j] = s * kv[j] * im[0];
+      oim[j] = -s * kv[j] * re[0];
+    }
   } else if (kernel == SE_ROTLET) {
     // -i eps_jlm k_m F_l = -i (F x k)_j
     const T cr[3] = {re[1] * k2 - re[2] * k1, re[2] * k0 - re[0] * k2, re[0] * k1 - re[1] * k0};
@@ -67,12 +73,13 @@ __device__ __forceinline__ void apply_regular(int kernel, T s, T k0, T k1, T k2,
 }
 
 // Scalar of the regular (unmodified) kernel without the separable factors:
-// H^ = 4 pi / k^2 (rotlet, Ewald screening) or B^ (1 + k^2/4xi^2) = -8 pi/k^4 (1 + k^2/4xi^2)
+// H^ = 4 pi / k^2 (rotlet and harmonic field, Ewald screening) or
+// B^ (1 + k^2/4xi^2) = -8 pi/k^4 (1 + k^2/4xi^2)
 // (stokeslet, stresslet, Hasimoto screening); the exp(-k^2/4xi^2) and 1/w^2 factors are
 // separable and come from the per-direction tables.
 template <typename T>
 __device__ __forceinline__ T regular_scalar(int kernel, T kk, T inv4xi2) {
-  if (kernel == SE_ROTLET) return T(4.0 * 3.14159265358979323846) / kk;
+  if (harmonic_family(kernel)) return T(4.0 * 3.14159265358979323846) / kk;
   return T(-8.0 * 3.14159265358979323846) / (kk * kk) * (T(1) + kk * inv4xi2);
 }
 

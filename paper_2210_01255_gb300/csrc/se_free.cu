@@ -247,9 +247,15 @@ __device__ __forceinline__ void free_mode(const FreeScale& a, int kernel, T s, T
   if (a.cls != 0) {
     apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
   } else if (a.m.D == 2) {
-    // modified column: scalar (mr + i mi) times D^S, D^Omega or D^T
+    // modified column: scalar (mr + i mi) times D^S, D^Omega or D^T; the harmonic field's
+    // column has only the direction-2 derivative: the rotlet's scalar (the same derivative of
+    // the modified harmonic kernel) times (0, 0, q)
     T vr[3], vi[3];
-    if (kernel == SE_STOKESLET) {
+    if (kernel == SE_HARMONIC_FIELD) {
+      vr[0] = 0; vi[0] = 0;
+      vr[1] = 0; vi[1] = 0;
+      vr[2] = re[0]; vi[2] = im[0];
+    } else if (kernel == SE_STOKESLET) {
       vr[0] = 2 * re[0]; vi[0] = 2 * im[0];
       vr[1] = 2 * re[1]; vi[1] = 2 * im[1];
       vr[2] = 0; vi[2] = 0;
@@ -270,8 +276,8 @@ __device__ __forceinline__ void free_mode(const FreeScale& a, int kernel, T s, T
   } else {
     // modified plane (D = 1), k = (0, kappa2, kappa3)
     const T q2 = k1, q3 = k2;
-    if (kernel == SE_ROTLET) {
-      apply_regular<T>(SE_ROTLET, mr, T(0), q2, q3, re, im, ore, oim);
+    if (harmonic_family(kernel)) {
+      apply_regular<T>(kernel, mr, T(0), q2, q3, re, im, ore, oim);
     } else if (kernel == SE_STOKESLET) {
       ore[0] = 2 * mr * re[0];
       oim[0] = 2 * mr * im[0];
@@ -377,7 +383,9 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
     }
   }
   const size_t H = (size_t)a.ncols * plane;  // component stride in this buffer
-  for (int r = 0; r < n_rhs; ++r) {
+  // in place, in the order that never overwrites an input still to be read (see k_scale3p)
+  for (int rr = 0; rr < n_rhs; ++rr) {
+    const int r = cin >= 3 ? rr : n_rhs - 1 - rr;
     T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
@@ -536,7 +544,7 @@ se_status free_plan_setup(se_plan_t* p) {
       int n = g.n[d];
       SE_TRY(upload_any(p, sep_table(p, n, d == 2 ? n / 2 + 1 : n), &p->ptab[d]));
     }
-    int mask = p->opts.kernel_mask ? p->opts.kernel_mask : 7;
+    int mask = rule_mask(p->opts.kernel_mask ? p->opts.kernel_mask : 7);
     if (mask & SE_ROTLET) SE_TRY(precompute_0p(p, 0, &p->atr[0]));
     if (mask & (SE_STOKESLET | SE_STRESSLET)) SE_TRY(precompute_0p(p, 1, &p->atr[1]));
     return SE_OK;
@@ -656,14 +664,17 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   const int D = p->D;
   // k^P = 0 tables of D = 2 per kernel: 0 stokeslet, 1 stresslet, 2 rotlet (S|T: 0 and 1)
   const int kidx = (kernel & SE_STOKESLET) ? 0 : (kernel == SE_STRESSLET ? 1 : 2);
+  // spectrum and class buffers hold the C inputs and, after the in-place scaling, the NC
+  // outputs (C < NC for the harmonic field)
+  const int CS = std::max(C, NC);
   if (D == 0) {
     // 3-D R2C on the 2M' grid, scaled by A^_{R,tr} (Sec. 3.5), C2R
-    const int biharm = kernel != SE_ROTLET;
+    const int biharm = !harmonic_family(kernel);
     if (!p->atr[biharm].p) return SE_ERR_UNSUPPORTED;  // kernel not in the plan's kernel_mask
     const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
     void* spec;
-    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * H, &spec));
+    SE_TRY(buf(p, "spec", sizeof(T) * 2 * CS * H, &spec));
     int n[3] = {g.n[0], g.n[1], g.n[2]};
     cufftHandle hf, hi;
     SE_TRY(free_fft(p, 1, C, 3, n, nullptr, 1, (int)G, nullptr, 1, (int)H, FT<T>::R2C, &hf));
@@ -682,7 +693,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     const size_t G = (size_t)M0 * M1 * Mz;
     const size_t S = (size_t)M0 * H1 * Mz;  // complex elements per component
     void* spec;
-    SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * S, &spec));
+    SE_TRY(buf(p, "spec", sizeof(T) * 2 * CS * S, &spec));
     // (ii-a) 2-D R2C over (0, 1) for every z, one execution per component
     int n2[2] = {M0, M1};
     int in2[2] = {M0, M1}, on2[2] = {M0, H1};
@@ -695,8 +706,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     const int ncolS = (2 * p->kbar_star + 1) * (p->kbar_star + 1) - 1;
     const int n0 = p->ncls[0][2], nS = p->ncls[1][2];
     void *b0, *bS;
-    SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * C * (size_t)n0, &b0));
-    SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * C * (size_t)std::max(ncolS, 1) * nS, &bS));
+    SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * CS * (size_t)n0, &b0));
+    SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * CS * (size_t)std::max(ncolS, 1) * nS, &bS));
     const Ext2 em{{Mz, 0}}, e0{{n0, 0}}, eS{{nS, 0}};
     cm.mode = 0;
     k_aft_copy<T><<<grid1d((long long)C * n0, 256), 256, 0, st>>>(cm, C, 1, em, e0, true, (T*)spec, (T*)b0);
@@ -772,7 +783,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   const size_t G = (size_t)M0 * PL;
   const size_t S = (size_t)H0 * PL;
   void* spec;
-  SE_TRY(buf(p, "spec", sizeof(T) * 2 * C * S, &spec));
+  SE_TRY(buf(p, "spec", sizeof(T) * 2 * CS * S, &spec));
   int n1[1] = {M0}, in1[1] = {M0}, on1[1] = {H0};
   cufftHandle h1f, h1i;
   SE_TRY(free_fft(p, 20, (int)PL, 1, n1, in1, (int)PL, 1, on1, (int)PL, 1, FT<T>::R2C, &h1f));
@@ -782,8 +793,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   const int kst = std::max(0, cm.kstar);
   const int n0y = p->ncls[0][1], n0z = p->ncls[0][2], nSy = p->ncls[1][1], nSz = p->ncls[1][2];
   void *b0, *bS;
-  SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * C * (size_t)n0y * n0z, &b0));
-  SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * C * (size_t)std::max(kst, 1) * nSy * nSz, &bS));
+  SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * CS * (size_t)n0y * n0z, &b0));
+  SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * CS * (size_t)std::max(kst, 1) * nSy * nSz, &bS));
   const Ext2 em{{My, Mz}}, e0{{n0y, n0z}}, eS{{nSy, nSz}};
   cm.mode = 0;
   k_aft_copy<T><<<grid1d((long long)C * n0y * n0z, 256), 256, 0, st>>>(cm, C, 1, em, e0, true, (T*)spec, (T*)b0);
@@ -825,8 +836,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   fs.ncols = 1;
   fs.fn[0] = n0y;
   fs.fn[1] = n0z;
-  const T* modH = (const T*)(kernel == SE_ROTLET ? p->mod0[2].p : p->mod0[0].p);
-  const T* modB = (const T*)(kernel == SE_ROTLET ? nullptr : p->mod0[1].p);
+  const T* modH = (const T*)(harmonic_family(kernel) ? p->mod0[2].p : p->mod0[0].p);
+  const T* modB = (const T*)(harmonic_family(kernel) ? nullptr : p->mod0[1].p);
   k_scale_free<T><<<grid1d((long long)n0y * n0z, 256), 256, 0, st>>>(fs, kernel, n_rhs, tp0, nullptr, nullptr,
                                                                      nullptr, modH, modB, (T*)b0);
   if (kst > 0) {

@@ -183,10 +183,13 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
   for (int i = 0; i < 3; ++i)
     if (!(box[i] > 0) || !std::isfinite(box[i])) return SE_ERR_ARG;
   if (!(Q > 0)) return SE_ERR_ARG;
+  if (kernel_mask & ~15) return SE_ERR_ARG;
+  // the harmonic field takes the rotlet's rules (both are first derivatives of H)
+  const int rmask = rule_mask(kernel_mask);
   int kernels[3], nk = 0;
   for (int k : {SE_STOKESLET, SE_ROTLET, SE_STRESSLET})
-    if (kernel_mask & k) kernels[nk++] = k;
-  if (nk == 0 || (kernel_mask & ~7)) return SE_ERR_ARG;
+    if (rmask & k) kernels[nk++] = k;
+  if (nk == 0) return SE_ERR_ARG;
   const int fM = io->f_M > 0 ? io->f_M : 4;
   // In the estimates a cube of side L is assumed; for a cuboid L^3 -> |B|, L -> |B|^(1/3).
   const double vol = box[0] * box[1] * box[2];

@@ -26,7 +26,18 @@ constexpr int SE_KERNEL_ST = SE_STOKESLET | SE_STRESSLET;
 // strength components per point and right-hand side, which is also the number of spread
 // components: f (3); (q, nu) (6, spread as the 6 symmetric q nu^T entries); (f, q, nu) (9)
 __host__ __device__ inline int kernel_comps(int kernel) {
-  return kernel == SE_STRESSLET ? 6 : (kernel == SE_KERNEL_ST ? 9 : 3);
+  return kernel == SE_STRESSLET ? 6 : (kernel == SE_KERNEL_ST ? 9 : (kernel == SE_HARMONIC_FIELD ? 1 : 3));
+}
+
+// the harmonic field is a first derivative of the harmonic kernel like the rotlet: it takes
+// the rotlet's parameter rules (Sec. 4), screening (Ewald) and modified-kernel tables
+__host__ __device__ inline bool harmonic_family(int kernel) {
+  return kernel == SE_ROTLET || kernel == SE_HARMONIC_FIELD;
+}
+
+// a kernel mask with the harmonic field's rules entered as the rotlet's
+__host__ __device__ inline int rule_mask(int mask) {
+  return (mask & 7) | ((mask & SE_HARMONIC_FIELD) ? SE_ROTLET : 0);
 }
 
 // Geometry of the grid that gridding writes and gathering reads (Sec. 3.2).

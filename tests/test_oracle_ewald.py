@@ -267,3 +267,33 @@ def test_3p_self_term_and_magnitudes():
             assert np.allclose(p["self"], -4 * 10.0 / math.sqrt(math.pi) * f, atol=1e-15)
         else:
             assert np.abs(p["self"]).max() == 0.0
+
+
+# ------------------------------------------------------------- harmonic field
+
+def test_harmonic_field_free_space_is_the_direct_sum():
+    """E_j = sum_n q_n (x - x_n)_j / |x - x_n|^3 (star form: n != m), from the rotlet identity,
+    against a direct numpy sum; also at explicit targets."""
+    rng = np.random.default_rng(11)
+    x = rng.random((40, 3))
+    q = rng.standard_normal(40)
+    e = E.harmonic_field(0, [1, 1, 1], x, q)
+    r = x[:, None, :] - x[None, :, :]
+    d = np.linalg.norm(r, axis=-1)
+    np.fill_diagonal(d, np.inf)
+    ref = np.einsum("mnj,n->mj", r / d[..., None] ** 3, q)
+    assert np.abs(e - ref).max() < 1e-12 * np.abs(ref).max()
+    t = rng.random((7, 3))
+    r = t[:, None, :] - x[None, :, :]
+    ref_t = np.einsum("mnj,n->mj", r / np.linalg.norm(r, axis=-1)[..., None] ** 3, q)
+    assert np.abs(E.harmonic_field(0, [1, 1, 1], x, q, targets=t) - ref_t).max() < 1e-12 * np.abs(ref_t).max()
+
+
+@pytest.mark.parametrize("D", [1, 2, 3])
+def test_harmonic_field_periodic_is_xi_independent(D):
+    rng = np.random.default_rng(12 + D)
+    x = rng.random((30, 3))
+    q = rng.standard_normal(30)
+    a = E.harmonic_field(D, [1, 1, 1], x, q, xi=4.0)
+    b = E.harmonic_field(D, [1, 1, 1], x, q, xi=7.0)
+    assert np.abs(a - b).max() < 1e-11 * np.abs(a).max()
