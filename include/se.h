@@ -81,7 +81,8 @@ typedef struct {
   int kbar_star;     /* threshold kbar_* of Eq. (estimate-kbarstar); -1 = rule            */
   double tol_abs;    /* absolute tolerance used by the s_*, kbar_* rules (0 = 1e-10)     */
   double Q;          /* source quantity Q of Eqs. (vector/tensor-source-quantity) for the rules (0 = 1) */
-  int kernel_mask;   /* kernels the plan will be used with (for the free-direction rules); 0 = all */
+  int kernel_mask;   /* kernels the plan will be used with (for the free-direction rules); 0 = all.
+                        SE_HARMONIC_FIELD uses the rotlet's rules and tables             */
   void* stream;      /* cudaStream_t to issue work on; NULL = the legacy default stream   */
   int flags;         /* SE_FLAG_* bits, 0 = defaults                                        */
   double n_rc;       /* se_autotune: average neighbours within r_c used to choose xi when
