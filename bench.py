@@ -40,18 +40,20 @@ METRIC = METRIC_FMT % "3P stresslet+rotlet, N=20000"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
                 "2p_stokeslet_n200000_rhs8": "2P stokeslet, N=200000, 8 RHS",
                 "0p_stokeslet_stresslet_n1000000": "0P stokeslet+stresslet, N=1e6 clustered",
-                "1p_stokeslet_64cfg_rhs16": "1P stokeslet, 64 systems x 16 RHS"}
+                "1p_stokeslet_64cfg_rhs16": "1P stokeslet, 64 systems x 16 RHS",
+                "3p_harmonic_field_n100000": "3P harmonic field, N=100000"}
 # oracle targets per sampled evaluation: cpu_baseline (a few seconds of oracle work on the
 # host cores) and one step of the reference arm
 ORACLE_SAMPLE = {"3p_stresslet_rotlet_n20000": (1024, 512), "2p_stokeslet_n200000_rhs8": (64, 32),
-                 "0p_stokeslet_stresslet_n1000000": (256, 128), "1p_stokeslet_64cfg_rhs16": (64, 32)}
+                 "0p_stokeslet_stresslet_n1000000": (256, 128), "1p_stokeslet_64cfg_rhs16": (64, 32),
+                 "3p_harmonic_field_n100000": (128, 64)}
 UNIT = "targets/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
-COMPS = {"stokeslet": 3, "rotlet": 3, "stresslet": 6, "stokeslet+stresslet": 9}
+COMPS = {"stokeslet": 3, "rotlet": 3, "stresslet": 6, "stokeslet+stresslet": 9, "harmonic_field": 1}
 # FP32 operations per real-space pair: 60 with one RHS (separation, rsqrt, exp, erfc fit,
 # the kernel's terms), plus the kernel's terms for every further RHS
-PAIR_FLOPS = {"stokeslet": 60, "rotlet": 60, "stresslet": 60, "stokeslet+stresslet": 75}
-PAIR_FLOPS_RHS = {"stokeslet": 18, "rotlet": 15, "stresslet": 38, "stokeslet+stresslet": 56}
+PAIR_FLOPS = {"stokeslet": 60, "rotlet": 60, "stresslet": 60, "stokeslet+stresslet": 75, "harmonic_field": 50}
+PAIR_FLOPS_RHS = {"stokeslet": 18, "rotlet": 15, "stresslet": 38, "stokeslet+stresslet": 56, "harmonic_field": 8}
 
 
 def peaks():
