@@ -5,8 +5,9 @@ points uniform in the unit box (strengths N(0,1), stresslet normals normalised),
 parameters from the selection procedure of Sec. 4.6 at 1e-6 RMS relative tolerance (PKB
 window), targets = sources. --workload selects another configuration of
 paper_2210_01255_gb300.workloads.CONFIGS: the 2P stokeslet with 8 RHS, the 0P stokeslet +
-stresslet of 1e6 clustered points (one fused evaluation), or 64 independent 1P stokeslet
-systems with 16 RHS each.
+stresslet of 1e6 clustered points (one fused evaluation), 64 independent 1P stokeslet
+systems with 16 RHS each, or the 3P harmonic field of 1e5 charges. --experiment runs the
+timing experiments of Sec. 5.2 instead (one JSON line per data point).
 
 A workload is a list of evaluations (kernel, points, strengths, plan); one step runs all of
 them (real-space sum, Fourier-space part of Alg. 1, corrections). value = (target, RHS)
@@ -17,6 +18,7 @@ and one kernel per evaluation, same parameters) and the end-to-end form through 
 buffers are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
+       python bench.py --experiment complexity|time_vs_error [--exp-d 3,0] [--exp-jmax 5]
 Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas, weak
 scaling, no collective in the data path); value = all ranks' targets / the slowest rank's time.
 """
