@@ -31,8 +31,11 @@ import math
 import numpy as np
 import scipy.special as sp
 
-STOKESLET, ROTLET, STRESSLET = 1, 2, 4
-_NAMES = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET}
+STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD = 1, 2, 4, 8
+_NAMES = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET, "harmonic_field": HARMONIC_FIELD}
+# the harmonic field E = -grad H q (H = 1/r) is a first derivative of H like the rotlet
+# (Omega_jl = -eps_jlm d_m H): Ewald screening and the harmonic modified kernels
+_HARMONIC = (ROTLET, HARMONIC_FIELD)
 
 
 def kernel_id(kernel):
@@ -111,9 +114,12 @@ def taps(u, P):
 # ---------------------------------------------------------------- Fourier kernels
 
 def _Khat(kernel, k):
-    """Operator symbols K^(k) of Eqs. (diffop-rel-fourier-1..3), shape (..., 3, 3[, 3])."""
+    """Operator symbols K^(k) of Eqs. (diffop-rel-fourier-1..3), shape (..., 3, 3[, 3]);
+    the harmonic field's gradient -i k, shape (..., 3, 1)."""
     d = np.eye(3)
     k2 = np.sum(k * k, axis=-1)
+    if kernel == HARMONIC_FIELD:
+        return (-1j * k)[..., :, None]
     if kernel == STOKESLET:
         return (-d * k2[..., None, None] + k[..., :, None] * k[..., None, :]).astype(complex)
     if kernel == ROTLET:
@@ -128,14 +134,14 @@ def _Khat(kernel, k):
 
 def _screen(kernel, k2, xi):
     gE = np.exp(-k2 / (4 * xi * xi))                                  # Eq. (ewald-screening)
-    return gE if kernel == ROTLET else gE * (1 + k2 / (4 * xi * xi))   # Eq. (hasimoto-screening)
+    return gE if kernel in _HARMONIC else gE * (1 + k2 / (4 * xi * xi))   # Eq. (hasimoto-screening)
 
 
 def kernel_3p(kernel, k, xi):
     """G_R^{3P}(k) gamma^(k; xi), Eq. (mod-kernel-3p) times the screening; zero at k = 0."""
     k2 = np.sum(k * k, axis=-1)
     safe = np.where(k2 > 0, k2, 1.0)
-    A = np.where(k2 > 0, (-8 * np.pi / safe ** 2) if kernel != ROTLET else (4 * np.pi / safe), 0.0)
+    A = np.where(k2 > 0, (-8 * np.pi / safe ** 2) if kernel not in _HARMONIC else (4 * np.pi / safe), 0.0)
     s = A * _screen(kernel, k2, xi)
     K = _Khat(kernel, k)
     return K * s.reshape(s.shape + (1,) * (K.ndim - s.ndim))
@@ -456,6 +462,12 @@ def modified_2p_column(kernel, kap, xi, R):
         D = np.array([[0, 1.0, 0], [-1.0, 0, 0], [0, 0, 0]])
         s = hat_Z2p(kap, R) * _screen(kernel, k2, xi)
         return s[:, None, None] * D
+    if kernel == HARMONIC_FIELD:
+        # only the direction-3 derivative survives at k^P = 0: the rotlet's scalar (the same
+        # derivative of the modified harmonic kernel) on (0, 0, q)
+        D = np.array([[0.0], [0.0], [1.0]])
+        s = hat_Z2p(kap, R) * _screen(kernel, k2, xi)
+        return s[:, None, None] * D
     D = np.zeros((3, 3, 3))
     D[0, 0, 2] = D[0, 2, 0] = -2
     D[1, 1, 2] = D[1, 2, 1] = -2
@@ -471,9 +483,9 @@ def modified_1p_plane(kernel, k2v, k3v, xi, R):
     B = hat_B1p(kap, R)
     scr = _screen(kernel, kap ** 2, xi)
     z = np.zeros_like(kap)
-    if kernel == ROTLET:
+    if kernel in _HARMONIC:
         K = np.stack([np.zeros_like(k2v), k2v, k3v], axis=-1)
-        return _Khat(ROTLET, K) * (H * scr)[..., None, None]
+        return _Khat(kernel, K) * (H * scr)[..., None, None]
     if kernel == STOKESLET:
         G = np.zeros(kap.shape + (3, 3), dtype=complex)
         G[..., 0, 0] = 2 * H
@@ -507,7 +519,7 @@ def scaling_aft(D, kernel, grid, fg, xi, win, s0, s_star, kbar_star, fM):
     per = tuple(range(1, D + 1))                  # periodic axes of the [C, x, y, z] array
     free = tuple(range(D + 1, 4))
     Fp = np.fft.fftn(grid, axes=per)              # FFT in the periodic directions
-    out = np.zeros_like(Fp)
+    out = np.zeros((max(Fp.shape[0], 3),) + Fp.shape[1:], dtype=complex)  # 3 outputs
     kbs = [np.fft.fftfreq(M[d]) * M[d] for d in range(D)]
     for idx in np.ndindex(*[M[d] for d in range(D)]):
         kb = [kbs[d][idx[d]] for d in range(D)]
@@ -566,13 +578,13 @@ def precompute_0p(kernel, fg, s0, fM):
     kv = [_kvec(np.fft.fftfreq(nup[d]) * nup[d], nup[d], h) for d in range(3)]
     K0, K1, K2 = np.meshgrid(*kv, indexing="ij")
     kap = np.sqrt(K0 ** 2 + K1 ** 2 + K2 ** 2)
-    Ahat = hat_H0p(kap, fg.R) if kernel == ROTLET else hat_B0p(kap, fg.R)
+    Ahat = hat_H0p(kap, fg.R) if kernel in _HARMONIC else hat_B0p(kap, fg.R)
     A = np.fft.ifftn(Ahat).real                              # (ii) A_R on the grid (times 1/h^3)
     # (iii) truncate to the 2M' offsets -M' .. M'-1 around the origin, in FFT order
     At = np.zeros((2 * M[0], 2 * M[1], 2 * M[2]))
     offs = [np.concatenate([np.arange(0, M[d]), np.arange(-M[d], 0)]) for d in range(3)]
     At[...] = A[np.ix_(np.mod(offs[0], nup[0]), np.mod(offs[1], nup[1]), np.mod(offs[2], nup[2]))]
-    if kernel != ROTLET:
+    if kernel not in _HARMONIC:
         # mollifier in natural order (origin at index M'), mapped to FFT order
         for d in range(3):
             mu = mollifier(2 * M[d])

@@ -135,3 +135,54 @@ def test_alg1_0p_with_precomputation_reproduces_direct_sum(kernel):
     tot = u + ur + S.self_term(kernel, xi, f)
     ref = E.potential(0, L, kernel, x, f)
     assert E.rms_rel(tot, ref) < 1e-9
+
+
+# ----------------------------------------------------------------- harmonic field
+
+def _field_real(D, L, xi, x, q):
+    """Real-space part of the harmonic field with splitting xi: the rotlet's real-space sums
+    with torques along the axes (E_1 = (Omega q e_3)_2, E_2 = (Omega q e_1)_3,
+    E_3 = (Omega q e_2)_1; the identity holds term by term, both real-space kernels being
+    derivatives of erfc(xi r)/r)."""
+    N = x.shape[0]
+    out = np.zeros((N, 3))
+    for comp, axis, row in ((0, 2, 1), (1, 0, 2), (2, 1, 0)):
+        f = np.zeros((N, 3))
+        f[:, axis] = q
+        ur = np.zeros((N, 3))
+        E.lib().orc_real(D, E._p(np.asarray(L, dtype=float)), xi, 7.0 / xi, E.kernel_id("rotlet"), N,
+                         E._p(np.ascontiguousarray(x)), E._p(f), N, None, E._p(ur))
+        out[:, comp] = ur[:, row]
+    return out
+
+
+def test_alg1_harmonic_field_3p():
+    rng = np.random.default_rng(31)
+    N = 40
+    x = rng.random((N, 3))
+    q = rng.standard_normal(N)
+    xi = 8.0
+    u = S.fourier_part_3p("harmonic_field", x, q[:, None], [1, 1, 1], (48, 48, 48), xi, "pkb", 16)
+    tot = u + _field_real(3, [1, 1, 1], xi, x, q)
+    assert E.rms_rel(tot, E.harmonic_field(3, [1, 1, 1], x, q)) < 1e-11
+
+
+@pytest.mark.parametrize("D", [2, 1, 0])
+def test_alg1_harmonic_field_free_directions(D):
+    """D = 2, 1: the harmonic modified kernels on the k^P = 0 class with the adaptive FFT;
+    D = 0: the precomputed truncated harmonic kernel (no mollifier); vs the exact field."""
+    rng = np.random.default_rng(40 + D)
+    L = np.array([1.0, 1.0, 1.0])
+    N = 24
+    x = rng.random((N, 3))
+    q = rng.standard_normal(N)
+    xi, M, P = 6.0, 40, 16
+    lam = 2.4 if D > 0 else 1.5          # Table 4, rotlet column (the field takes its rules)
+    me = 4 * math.ceil((M + P + (lam - 1) * P) / 4)
+    Mext = [0, 0, 0]
+    for d in range(D, 3):
+        Mext[d] = me
+    u = S.fourier_part(D, "harmonic_field", x, q[:, None], L, 1.0 / M, P, xi, "pkb", Mext=Mext, s_star=3.0,
+                       kbar_star=6)
+    tot = u + _field_real(D, L, xi, x, q)
+    assert E.rms_rel(tot, E.harmonic_field(D, L, x, q)) < 1e-9
