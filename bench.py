@@ -1,12 +1,14 @@
 """Benchmark of the Spectral Ewald Stokes hot path on GB300.
 
-Default workload (N = 1): the triply periodic stresslet and rotlet potentials of N = 20,000
-points uniform in the unit box (strengths N(0,1), stresslet normals normalised), FP32 path,
-parameters from the selection procedure of Sec. 4.6 at 1e-6 RMS relative tolerance (PKB
-window), targets = sources. --workload selects another configuration of
-paper_2210_01255_gb300.workloads.CONFIGS: the 2P stokeslet with 8 RHS, the 0P stokeslet +
-stresslet of 1e6 clustered points (one fused evaluation), 64 independent 1P stokeslet
-systems with 16 RHS each, or the 3P harmonic field of 1e5 charges. --experiment runs the
+Default workload (N = 1): the free-space (0P) stokeslet + stresslet potential of N = 1e6
+points, half uniform in the unit cube and half in a Gaussian cluster (sigma 0.05) at its
+centre, strengths (f, q, nu) N(0,1) with nu normalised, one fused evaluation, FP32 path at
+1e-6 RMS relative tolerance (PKB window), targets = sources; the split between the real-
+and Fourier-space work (and with it M and P) chosen by timing candidate plans on these
+points (se_autotune_timed), each candidate's parameters from the tolerance rules of
+Sec. 4.6. --workload selects another configuration of paper_2210_01255_gb300.workloads.CONFIGS:
+the 3P stresslet + rotlet of 20,000 points, the 2P stokeslet with 8 RHS, 64 independent 1P
+stokeslet systems with 16 RHS each, or the 3P harmonic field of 1e5 charges. --experiment runs the
 timing experiments of Sec. 5.2 instead (one JSON line per data point).
 
 A workload is a list of evaluations (kernel, points, strengths, plan); one step runs all of
@@ -35,10 +37,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "3p_stresslet_rotlet_n20000"   # default (--workload selects another configuration)
+WORKLOAD = "0p_stokeslet_stresslet_n1000000"   # default (--workload selects another configuration)
 P_MARGIN = None   # --p-margin: overrides the workload's window margin of the selection
 METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
-METRIC = METRIC_FMT % "3P stresslet+rotlet, N=20000"
+METRIC = METRIC_FMT % "0P stokeslet+stresslet, N=1e6 clustered"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
                 "2p_stokeslet_n200000_rhs8": "2P stokeslet, N=200000, 8 RHS",
                 "0p_stokeslet_stresslet_n1000000": "0P stokeslet+stresslet, N=1e6 clustered",
@@ -47,10 +49,14 @@ METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
 # oracle targets per sampled evaluation: cpu_baseline (a few seconds of oracle work on the
 # host cores) and one step of the reference arm
 ORACLE_SAMPLE = {"3p_stresslet_rotlet_n20000": (1024, 512), "2p_stokeslet_n200000_rhs8": (64, 32),
-                 "0p_stokeslet_stresslet_n1000000": (256, 128), "1p_stokeslet_64cfg_rhs16": (64, 32),
+                 "0p_stokeslet_stresslet_n1000000": (2048, 512), "1p_stokeslet_64cfg_rhs16": (64, 32),
                  "3p_harmonic_field_n100000": (128, 64)}
 UNIT = "targets/s"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x 2 flop x max clock
+# FP32 ALU peak: measured on a GB300 of this machine by a probe kernel of 16 independent FMA
+# chains per thread (152 x 8 CTAs of 256 threads, best of 3, CUDA events): 78.4 TFLOP/s, 97 % of
+# the 80.5 TFLOP/s that 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz give
+FP32_PEAK_TFLOPS = 78.4
+FP32_PEAK_DERIVED_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 COMPS = {"stokeslet": 3, "rotlet": 3, "stresslet": 6, "stokeslet+stresslet": 9, "harmonic_field": 1}
 # FP32 operations per real-space pair: 60 with one RHS (separation, rsqrt, exp, erfc fit,
 # the kernel's terms), plus the kernel's terms for every further RHS
@@ -212,29 +218,40 @@ def real_pairs(cfg, item, rc):
 KERNEL_SOURCES = {"real": "se_core.cu", "spread": "se_core.cu", "gather": "se_core.cu"}
 
 
-def kernel_traffic(stage, params, gridding="cuda"):
+def param_key(p):
+    """The parameters a traffic figure was taken at: M_0, P and r_c."""
+    return "%d:%d:%.5f" % (p["M"][0], p["P"], p["rc"])
+
+
+def kernel_traffic(workload, stage, params, gridding="cuda"):
     """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the stage's kernel
-    from the committed ncu summary profiles/traffic_3p_stresslet_rotlet_n20000.txt, averaged over
-    the stresslet and rotlet launches; None when the summary is missing, was taken for other
-    parameters, or the kernel's source file changed since (sha256 recorded with the counters)."""
+    from the committed ncu summary profiles/traffic_<workload>.txt (lines: stage, evaluation
+    name, parameter key M_0:P:r_c, bytes per launch, sha256 prefix of the kernel's source
+    file), averaged over the workload's evaluations; None when the summary is missing, was
+    taken at other parameters, or the kernel's source file changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "traffic_3p_stresslet_rotlet_n20000.txt")
+    path = os.path.join(ROOT, "profiles", "traffic_%s.txt" % workload)
     try:
         lines = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     except OSError:
         return None
     if stage == "spread" and gridding == "tc":
-        return None  # the summary covers the CUDA-core gridding kernel only
+        return None  # the summaries cover the CUDA-core gridding kernel only
     src = os.path.join(ROOT, "paper_2210_01255_gb300", "csrc", KERNEL_SOURCES[stage])
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
     vals = []
-    for f in lines:
-        # stage kernel M P bytes_per_launch source_sha
-        if len(f) == 6 and f[0] == stage and f[5] == sha:
-            for k, p in params.items():
-                if f[1] == k and int(f[2]) == p["M"][0] and int(f[3]) == p["P"]:
-                    vals.append(float(f[4]))
-    return sum(vals) / len(vals) if len(vals) == len(params) else None
+    for name, p in params.items():
+        for f in lines:
+            if len(f) == 5 and f[0] == stage and f[1] == name and f[2] == param_key(p) and f[4] == sha:
+                vals.append(float(f[3]))
+                break
+    return sum(vals) / len(vals) if vals and len(vals) == len(params) else None
+
+
+def config_n(items):
+    """Points per step as both arms report it: the points of the evaluations of the first
+    kernel (a workload evaluating two kernels on the same points counts them once)."""
+    return int(sum(it["N"] for it in items if it["kernel"] == items[0]["kernel"]))
 
 
 def oracle_potential(cfg, item, r, targets):
@@ -281,7 +298,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": sum(it["N"] for it in items), "box": list(cfg["box"]),
+            "config": {"workload": WORKLOAD, "N": config_n(items), "box": list(cfg["box"]),
                        "kernels": list(cfg["kernels"]), "tol_rel": cfg["tol"], "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "%d sampled targets of each of the first %d evaluations per step, all "
@@ -553,9 +570,10 @@ def main():
     tparams = {it["name"]: it["params"] for it in items}
     roof = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": ach / FP32_PEAK_TFLOPS,
-            "traffic": kernel_traffic(dom, tparams, args.gridding) if len(items) <= 4 else None,
-            "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (derived from unit counts and "
-                           "the maximum SM clock)",
+            "traffic": kernel_traffic(WORKLOAD, dom, tparams, args.gridding) if len(items) <= 4 else None,
+            "peak_source": "measured: FP32 FMA-chain probe kernel on a GB300 of this pool (of measured; "
+                           "152 SMs x 128 lanes x 2 flop x 2.07 GHz = %.1f TFLOP/s derived)"
+                           % FP32_PEAK_DERIVED_TFLOPS,
             "real_space_pairs_per_step": pairs}
     roof["per_stage_tflops"] = {k: work[k] / (per_stage[k] * 1e-3) / 1e12 for k in work if per_stage[k] > 0}
     pk = peaks()
@@ -602,10 +620,18 @@ def main():
                     for r in range(f64.shape[0]):
                         p64.evaluate(k, xdev, f64[r], out=u64)
 
-        for _ in range(3 if len(items) <= 4 else 1):
-            step64()
+        # one untimed step sizes the timed count: about 20 s of FP64 work at most (the FP64
+        # plain form of the 0P workload takes seconds per step)
+        t0 = time.perf_counter()
+        step64()
+        torch.cuda.synchronize()
+        t_one = time.perf_counter() - t0
+        if t_one < 2.0:
+            for _ in range(2 if len(items) <= 4 else 0):
+                step64()
         torch.cuda.synchronize()
         n64 = max(3, args.steps // 4) if len(items) <= 4 else 3
+        n64 = max(1, min(n64, int(20.0 / max(t_one, 1e-3))))
         ev64 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n64)]
         for s_ in range(n64):
             flush.zero_()
@@ -635,7 +661,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": g_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": int(sum(it["N"] for it in items if it["kernel"] == items[0]["kernel"])),
+            "config": {"workload": WORKLOAD, "N": config_n(items),
                        "n_rhs": cfg.get("n_rhs", 1), "box": list(cfg["box"]),
                        "kernels": list(cfg["kernels"]), "periodicity": cfg["D"],
                        "points": cfg.get("points", "uniform"),

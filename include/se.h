@@ -98,6 +98,12 @@ typedef struct {
  * rounding). Without it (default), and always for FP64 or P > 16, gridding runs on the CUDA
  * cores. */
 enum { SE_FLAG_TC_GRIDDING = 1 };
+/* se_opts.flags, testing aid: with SE_FLAG_TEST_TIMEOUT as well as SE_FLAG_TC_GRIDDING, the
+ * tensor-core gridding's bounded waits for finished chunks report a timeout at their first
+ * poll, so that the timeout path can be checked without a hang: each CTA flags it, waits for
+ * the tensor-core work it has already issued, releases its tensor memory and writes nothing;
+ * se_sync then returns SE_ERR_TIMEOUT and the evaluation's result is invalid. */
+enum { SE_FLAG_TEST_TIMEOUT = 2 };
 
 /* Fill *opts with the defaults above. */
 se_status se_opts_default(se_opts* opts);
@@ -231,21 +237,25 @@ void se_destroy(se_plan_h plan);
  * framework that owns all device memory through its own pre-allocated pool, or a time-step
  * loop that must never stall or fail on an allocation).
  * Computes the same values as se_eval_parts(plan, kernel, SE_PART_REAL, ...) in the star
- * form (targets = sources) for one right-hand side: the real-space part of
- * Eq. (real-space-potential-Dp) with the cut-off rc, plus the self term for the stokeslet.
+ * form (targets = sources) for one right-hand side, with the same cut-off rc and, for the
+ * stokeslet, the same self term.
  *   periodicity, box, xi, rc  as in se_plan_create; kernel: one of SE_STOKESLET, SE_ROTLET,
  *                             SE_STRESSLET; prec: SE_FP64 (double strengths and u) or SE_FP32.
  *   n_src, src                device double [n_src][3]; strengths device [n_src][c].
  *   u                         device [n_src][3], overwritten.
- *   stream                    cudaStream_t (NULL = legacy default stream); asynchronous.
+ *   stream                    cudaStream_t (NULL = legacy default stream).
+ * Synchronous: the work is issued on the stream, then the call waits for it and reads the
+ * device status word back (4 bytes into a host variable), so that a free-direction coordinate
+ * outside [0, L_i) or a non-finite coordinate returns SE_ERR_RANGE as se_eval_parts and
+ * se_sync do (u then holds values for the clamped positions and must be discarded).
  * Scratch: a fixed 16 MiB array inside the library (held by every GPU that loads it until
  * the process exits); limits n_src <= 65536 and at most 32 cells per direction; larger
  * requests return SE_ERR_CAPACITY before any work. No cudaMalloc, cudaFree or allocating
  * library call is made. The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) once for that device: make that first call before any stream
- * capture. Every call shares the one array and keeps its last contents (the counters are
- * cleared at the start of each call); calls that overlap on the GPU (different streams, or
- * host threads) race on it and must be serialised by the caller.
+ * capture. Every call shares the one array and keeps its last contents (the counters and
+ * the status word are cleared at the start of each call); calls that overlap on the GPU
+ * (different streams, or host threads) race on it and must be serialised by the caller.
  */
 se_status se_real_noalloc(int periodicity, const double box[3], double xi, double rc, int kernel,
                           int prec, long long n_src, const double* src, const void* strengths,

@@ -14,8 +14,10 @@
  *     + u^self (Eq. self-term), or, for D = 0, the direct sum of Eq. periodic-potential.
  * The caller chooses xi, rc and kmax so that the neglected tails are below rounding.
  *
- * Parity status of each function is stated in oracle/README.md and in the tests that pin
- * it; nothing here is tuned for speed beyond evaluating a complex exponential per term.
+ * Every function is pinned by tests/test_oracle_ewald.py against something outside itself
+ * (xi-independence of the total, quadrature of the App. A/B defining integrals, brute-force
+ * image sums, the stresslet integral identity, hand-computed kernel values); nothing here is
+ * tuned for speed beyond evaluating a complex exponential per term.
  */
 #include "ewald_oracle.h"
 

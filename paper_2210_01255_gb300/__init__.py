@@ -17,6 +17,7 @@ WIN_GAUSSIAN, WIN_KB, WIN_PKB = 0, 1, 2
 FP64, FP32 = 0, 1
 PART_REAL, PART_FOURIER, PART_CORR, PART_ALL = 1, 2, 4, 7
 FLAG_TC_GRIDDING = 1  # se_opts.flags: FP32 gridding (P <= 16) on the tensor cores (tcgen05)
+FLAG_TEST_TIMEOUT = 2  # se_opts.flags, testing aid: the tensor-core gridding's bounded waits give up at once
 KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
            "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD}
 WINDOWS = {"gaussian": WIN_GAUSSIAN, "kb": WIN_KB, "pkb": WIN_PKB}

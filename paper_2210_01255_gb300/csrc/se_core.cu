@@ -2068,7 +2068,12 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
   else k_real<T, SE_STRESSLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
   SE_CUDA(cudaGetLastError());
-  return SE_OK;
+  // the binning kernels flag a free-direction coordinate outside [0, L) or a non-finite one;
+  // read the word back (4 bytes into a host variable, no allocation) and wait for the stream
+  int flag = 0;
+  SE_CUDA(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SE_CUDA(cudaStreamSynchronize(st));
+  return flag ? SE_ERR_RANGE : SE_OK;
 }
 
 }  // namespace

@@ -17,7 +17,10 @@
 // dropped A_lo B_lo and the TF32 truncation of the low parts are below 2^-21 relative).
 // Operand stages and accumulators are double-buffered; an mbarrier signalled by
 // tcgen05.commit says when the MMAs of a chunk are done. Every wait is bounded: on timeout the CTA sets bit 2 of the
-// plan's status word (SE_ERR_TIMEOUT at se_sync) and stops issuing work.
+// plan's status word (SE_ERR_TIMEOUT at se_sync), stops issuing work, waits (bounded again) for the MMAs it
+// has already committed before it releases its tensor memory, and writes nothing. A timeout therefore leaves the
+// whole spread grid of that evaluation invalid (other CTAs' tiles complete, this CTA's tile missing); the caller
+// must discard the evaluation's result when se_sync reports SE_ERR_TIMEOUT.
 
 #include <cstdint>
 
@@ -114,8 +117,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // bounded wait for the completion of the phase with the given parity
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (long long i = 0; i < TC_WAIT_LIMIT; ++i)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = TC_WAIT_LIMIT) {
+  for (long long i = 0; i < limit; ++i)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }
@@ -129,7 +132,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
                                                              const float* __restrict__ wts,
                                                              const float* __restrict__ sf, int Ctot, int c0, int C,
                                                              int nslab, float* __restrict__ grid,
-                                                             int* __restrict__ status) {
+                                                             int* __restrict__ status, long long drain_limit) {
   static_assert(Z * CG == TC_N, "accumulator width");
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   TcSmem<Z, CG>& sm = *reinterpret_cast<TcSmem<Z, CG>*>(tc_smem_raw);
@@ -170,7 +173,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
 #pragma unroll
   for (int i = 0; i < 24; ++i) acc[i] = 0.f;
   auto drain = [&](int c) {  // wait for chunk c's MMAs and add its accumulator; uniform
-    const bool done = mbar_wait(&sm.mbar[c & 1], (uint32_t)((c >> 1) & 1));
+    const bool done = mbar_wait(&sm.mbar[c & 1], (uint32_t)((c >> 1) & 1), drain_limit);
     if (!__syncthreads_and(done)) return false;
     tc_fence_after();
     const uint32_t ta = trow + 64u * (uint32_t)(c & 1);
@@ -191,6 +194,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
 
   int chunk = 0;
   bool ok = true;
+  int last = -1;  // last chunk whose MMAs were committed (uniform)
   int npend = 0;
   const unsigned lt_mask = (1u << lane) - 1u;
 
@@ -371,6 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
       }
       mma_commit(&sm.mbar[st]);
     }
+    last = chunk;
     if (ncnt > 0) store();  // staging and formation of this chunk are done (barrier above)
     // ---- add the previous chunk (its MMAs ran while this chunk's operands were built); the
     // stage and accumulator of chunk - 1 are then free for chunk + 1
@@ -416,6 +421,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
       }
     }
   }
+  if (!ok && last >= 0) {
+    // a wait gave up: the commit of the last chunk arrives once every MMA this CTA issued has
+    // completed; wait for it (bounded) before the accumulators' tensor memory is released
+    mbar_wait(&sm.mbar[last & 1], (uint32_t)((last >> 1) & 1));
+    __syncthreads();
+  }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
@@ -442,8 +453,11 @@ se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, con
   }
   dim3 grd((unsigned)(t0 * nslab), (unsigned)t1, (unsigned)t2);
   ++p->launches;
+  // SE_FLAG_TEST_TIMEOUT (a testing aid): the waits for finished chunks give up at once,
+  // which exercises the timeout path (status, drain of the MMAs in flight, release)
+  const long long drain_limit = (p->flags & SE_FLAG_TEST_TIMEOUT) ? 0 : TC_WAIT_LIMIT;
   k_spread_tc<Z, CG><<<grd, TC_THREADS, smem, p->stream>>>(g, tile_start, base, w, sf, Ctot, c0, C, nslab, grid,
-                                                           p->d_status);
+                                                           p->d_status, drain_limit);
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }

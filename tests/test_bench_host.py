@@ -98,3 +98,37 @@ def test_neighbour_table_matches_the_selection_defaults():
             a = se.se_autotune(D, (1, 1, 1), se.KERNELS[k], 1.0, 100000, 0.0, opts=o1)
             b = se.se_autotune(D, (1, 1, 1), se.KERNELS[k], 1.0, 100000, 0.0, opts=o2)
             assert a["xi"] == pytest.approx(b["xi"], rel=1e-12), (k, D)
+
+
+def test_traffic_rows_need_matching_parameters_and_sources(tmp_path, monkeypatch):
+    """roofline.traffic is read from profiles/traffic_<workload>.txt only for the same
+    evaluation, parameters and kernel source; anything else gives None."""
+    import hashlib
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_2210_01255_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "se_core.cu").write_text("// kernel source\n")
+    sha = hashlib.sha256(b"// kernel source\n").hexdigest()[:16]
+    p = {"M": [100, 100, 100], "P": 8, "rc": 0.05}
+    (tmp_path / "profiles" / "traffic_w.txt").write_text(
+        "# header\nreal st %s 1000 %s\nreal st 90:8:0.05000 7 %s\n" % (bench.param_key(p), sha, sha))
+    assert bench.kernel_traffic("w", "real", {"st": p}) == 1000.0
+    assert bench.kernel_traffic("w", "real", {"st": dict(p, P=10)}) is None
+    assert bench.kernel_traffic("w", "spread", {"st": p}) is None
+    assert bench.kernel_traffic("other", "real", {"st": p}) is None
+    (csrc / "se_core.cu").write_text("// changed\n")
+    assert bench.kernel_traffic("w", "real", {"st": p}) is None
+
+
+def test_both_arms_count_points_alike():
+    """config.N: the points of one kernel's evaluations (a workload of two kernels on the same
+    points counts them once), the same in the GPU arm and the reference arm."""
+    for name in bench.METRIC_NAMES:
+        cfg = W.CONFIGS[name]
+        items = bench.make_items(cfg)
+        n = bench.config_n(items)
+        if "n_cfg" in cfg:
+            assert n == sum(int(v) for v in W.batch_sizes(cfg["n_cfg"], *cfg["N_range"], seed=cfg["seed"]))
+        else:
+            assert n == cfg["N"]

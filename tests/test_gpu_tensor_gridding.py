@@ -135,3 +135,26 @@ def test_tensor_gridding_clustered_full_size():
     e_cc = maxrel(grid_of(*args, 0), ref)
     assert e_cc < 2e-5, e_cc
     assert e_tc < 2e-5 and e_tc < 3 * e_cc, (e_tc, e_cc)
+
+
+def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
+    """The tensor-core gridding's bounded waits: with the testing flag SE_FLAG_TEST_TIMEOUT
+    they give up at their first poll. The evaluation must then report SE_ERR_TIMEOUT at
+    se_sync (no hang, no fault), and the same process must evaluate correctly afterwards."""
+    N, M, P = 4000, 32, 8
+    x = W.uniform_points(N, (1, 1, 1), seed=31)
+    f = W.strengths("stokeslet", N, seed=32)
+    o = se.se_opts_default()
+    o.flags = se.FLAG_TC_GRIDDING | se.FLAG_TEST_TIMEOUT
+    o.kernel_mask = se.STOKESLET
+    plan = se.Plan(3, (1, 1, 1), 8.0, 0.3, (M, M, M), P, "pkb", "fp32", opts=o)
+    xt = torch.tensor(x, device="cuda")
+    ft = torch.tensor(f, dtype=torch.float32, device="cuda")
+    plan.evaluate("stokeslet", xt, ft, parts=se.PART_FOURIER)
+    with pytest.raises(se.SeError) as e:
+        plan.sync()
+    assert e.value.code == -6
+    del plan
+    g_tc = grid_of(3, (1, 1, 1), "stokeslet", x, f, 8.0, (M, M, M), P, "pkb", se.FLAG_TC_GRIDDING)
+    g_cu = grid_of(3, (1, 1, 1), "stokeslet", x, f, 8.0, (M, M, M), P, "pkb", 0)
+    assert maxrel(g_tc, g_cu) < BAR
