@@ -104,6 +104,20 @@ enum { SE_FLAG_TC_GRIDDING = 1 };
  * the tensor-core work it has already issued, releases its tensor memory and writes nothing;
  * se_sync then returns SE_ERR_TIMEOUT and the evaluation's result is invalid. */
 enum { SE_FLAG_TEST_TIMEOUT = 2 };
+/* se_opts.flags: real-space sum with the dense-block path. Targets are grouped in blocks of 32
+ * consecutive cell-sorted targets; a block whose targets lie in a box of side <= r_c / 2 is
+ * summed by one warp against the candidates of the whole box (staged in shared memory and
+ * shared by the 32 targets), the targets of the other blocks one warp per target as without
+ * the flag. Pays off where targets have many neighbours (clustered points, large r_c);
+ * se_autotune_timed chooses it by timing. Same sums to rounding. */
+enum { SE_FLAG_REAL_BLOCKS = 4 };
+/* se_opts.flags: FFT-friendly grid sizes. se_autotune rounds every grid extent it chooses (M_i,
+ * and M'_i of the free directions) up to the next multiple of f_M whose prime factors are
+ * 2, 3, 5 and 7 only (cuFFT's fastest radices; the D = 0 transform length 2 M' then has them
+ * too), and se_plan_create does the same for the upsampled class lengths of Sec. 4.5. The
+ * grid only gets finer (h smaller), so the tolerance rules still hold. Without the flag the
+ * sizes are the paper's multiples of f_M. */
+enum { SE_FLAG_FFT_SIZES = 8 };
 
 /* Fill *opts with the defaults above. */
 se_status se_opts_default(se_opts* opts);
@@ -218,7 +232,8 @@ typedef struct {
 se_status se_get_info(se_plan_h plan, se_info* info);
 
 /* Copy the plan's spread grid (after the last evaluation, before the FFT) to host memory:
- * component-major [C][m0][m1][m2] in the plan's precision; bytes must be >= the grid size.
+ * component-major [C][n0][n1][n2] (D = 0: [C][m0][n1][n2], the first m0 planes of the zero-
+ * padded grid) in the plan's precision; bytes must be >= the grid size.
  * Used to check the gridding step (Eq. SE-gridding-disc) in isolation. */
 se_status se_debug_grid(se_plan_h plan, void* host_dst, unsigned long long bytes);
 

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libse.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["se_core.cu", "se_free.cu", "se_spread_tc.cu", "se_host.cpp", "se_api.cpp"]
+SOURCES = ["se_core.cu", "se_real.cu", "se_grid.cu", "se_free.cu", "se_spread_tc.cu", "se_host.cpp", "se_api.cpp"]
 
 
 def _nvcc():

@@ -40,28 +40,20 @@ se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out) {
 
 // ============================================================ point binning (counting sort)
 
-// Wrap a coordinate of a periodic direction into [0, L); flag a free coordinate outside
-// [0, L) or a non-finite one.
-__device__ inline double wrap_coord(double x, double L, int periodic, int* status) {
-  if (!isfinite(x)) {
-    atomicOr(status, 1);
-    return 0.0;
-  }
-  if (periodic) {
-    double w = x - floor(x / L) * L;
-    if (w >= L) w -= L;
-    if (w < 0) w = 0;
-    return w;
-  }
-  if (x < 0.0 || x >= L) atomicOr(status, 1);
-  return fmin(fmax(x, 0.0), nextafter(L, 0.0));
-}
 
-// key of the spread tile of each point; rank within the tile by atomic counting
-__global__ void k_tile_keys(GridGeom g, const double* __restrict__ x, int n, int* __restrict__ key,
+// key of the gridding bin of each point (bins of bs^3 cells, z fastest); rank within the bin
+// by atomic counting
+struct BinGeom {
+  GridGeom g;
+  int bs;
+  int nb[3];
+};
+
+__global__ void k_tile_keys(BinGeom bg, const double* __restrict__ x, int n, int* __restrict__ key,
                             int* __restrict__ rank, int* __restrict__ count, int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  const GridGeom& g = bg.g;
   int c[3];
   for (int d = 0; d < 3; ++d) {
     double w = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
@@ -71,22 +63,14 @@ __global__ void k_tile_keys(GridGeom g, const double* __restrict__ x, int n, int
       if (cc >= g.m[d]) cc -= g.m[d];
     }
     cc = min(max(cc, 0), g.m[d] - 1);
-    c[d] = cc / TS;
+    c[d] = cc / bg.bs;
   }
-  int k = (c[0] * g.ntile[1] + c[1]) * g.ntile[2] + c[2];
+  int k = (c[0] * bg.nb[1] + c[1]) * bg.nb[2] + c[2];
   key[i] = k;
   rank[i] = atomicAdd(&count[k], 1);
 }
 
-// key of the real-space cell of each point (cells of side >= rc / S)
-struct CellGeom {
-  int nc[3];
-  int range[3];
-  int periodic[3];
-  double L[3];
-  double inv_cs[3];
-};
-
+// key of the real-space cell of each point (CellGeom); rank within the cell by atomic counting
 __global__ void k_cell_keys(CellGeom g, const double* __restrict__ x, int n, int* __restrict__ key,
                             int* __restrict__ rank, int* __restrict__ count, int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +152,7 @@ static se_status counting_sort(se_plan_t* p, cudaStream_t st, const char* tag, i
 static void tile_keyfun(se_plan_t* p, cudaStream_t st, const double* x, int n, int* key, int* rank, int* count,
                         const void* geom) {
   ++p->launches;
-  k_tile_keys<<<grid1d(n, 256), 256, 0, st>>>(*(const GridGeom*)geom, x, n, key, rank, count, p->d_status);
+  k_tile_keys<<<grid1d(n, 256), 256, 0, st>>>(*(const BinGeom*)geom, x, n, key, rank, count, p->d_status);
 }
 static void cell_keyfun(se_plan_t* p, cudaStream_t st, const double* x, int n, int* key, int* rank, int* count,
                         const void* geom) {
@@ -293,150 +277,6 @@ __global__ void k_scatter_tile(GridGeom g, WinArgs<T> w, const int* __restrict__
   perm[s] = i;
   put_weights(g, w, x, i, s, base, wts, status);
   if (f) put_spread_strengths(kernel, f, n, n_rhs, i, s, sf);
-}
-
-// ========================================================= gridding, Eq. (SE-gridding-disc)
-//
-// Output-driven: one CTA per TS^3 tile of the grid; each thread owns two grid points along
-// direction 0 and accumulates all components in registers over the points of the tiles
-// whose windows reach the tile. No atomics; each grid value is written once.
-
-// Gridding, Eq. (SE-gridding-disc). Output-driven: the CTA (tile t, slab j) owns the TS^3
-// tile t and the j-th share of the source tiles that reach it (the source tiles are dealt
-// out round-robin over nslab CTAs). Each of the 64 threads owns one (y, z) column of the
-// tile and accumulates its TS = 8 grid points along direction 0 and all components in
-// registers: per point one product of the (y, z) window values, a test, and 8 C FMAs with
-// the direction-0 window values read as vectors from shared memory. The partial tile is
-// stored (nslab = 1) or added atomically into the zeroed grid.
-template <typename T, int CMAX>
-__global__ void __launch_bounds__(64) k_spread(GridGeom g, const int* __restrict__ tile_start,
-                                               const int* __restrict__ base, const T* __restrict__ wts,
-                                               const T* __restrict__ sf, int Ctot, int c0, int C, int nslab,
-                                               T* __restrict__ grid) {
-  // components c0 .. c0 + C - 1 of the Ctot spread components
-  constexpr int CH = 64;  // points staged per chunk
-  __shared__ __align__(16) T s_w[CH][3 * TS];
-  __shared__ T s_f[CH][CMAX];
-  __shared__ int s_bin[3][SP_MAXB], s_sh[3][SP_MAXB], s_nb[3];
-  // reaching points not yet spread: (index, first tap - tile origin per direction); < CH
-  // carried over plus one candidate pass of CH
-  __shared__ int4 s_pend[2 * CH];
-  __shared__ int s_wcnt[2];
-  const int P = g.P;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int lz = tid & 7, ly = tid >> 3;
-  const int slab = blockIdx.x % nslab;
-  const int t0 = blockIdx.x / nslab, t1 = blockIdx.y, t2 = blockIdx.z;
-  const int o[3] = {t0 * TS, t1 * TS, t2 * TS};
-  T acc[TS][CMAX];
-#pragma unroll
-  for (int xx = 0; xx < TS; ++xx)
-#pragma unroll
-    for (int c = 0; c < CMAX; ++c) acc[xx][c] = T(0);
-  if (tid < 3) s_nb[tid] = tile_list(g, tid, o[tid], TS, s_bin[tid], s_sh[tid]);
-  __syncthreads();
-  const int nbx = s_nb[0], nby = s_nb[1], nbz = s_nb[2];
-  const int nbins = nbx * nby * nbz;
-  // spread the first n pending points (n <= CH); uniform
-  auto spread_pending = [&](int n) {
-    for (int idx = tid; idx < n * 3 * TS; idx += 64) {
-      const int pp = idx / (3 * TS), r = idx - pp * 3 * TS;
-      const int d = r / TS, l = r - d * TS;
-      const int4 pe = s_pend[pp];
-      const int q = l - (d == 0 ? pe.y : (d == 1 ? pe.z : pe.w));
-      s_w[pp][r] = (q >= 0 && q < P) ? wts[((size_t)pe.x * 3 + d) * P + q] : T(0);
-    }
-    for (int idx = tid; idx < n * C; idx += 64) {
-      const int pp = idx / C, c = idx - pp * C;
-      s_f[pp][c] = sf[(size_t)s_pend[pp].x * Ctot + c0 + c];
-    }
-    __syncthreads();
-    for (int pp = 0; pp < n; ++pp) {
-      const T wyz = s_w[pp][TS + ly] * s_w[pp][2 * TS + lz];
-      if (wyz != T(0)) {
-        // many components: skip the half of the x points the support misses (the same for
-        // every thread: no divergence); few components: the test costs more than it saves
-        int xh = 3;
-        if (CMAX >= 12) {
-          const int s0 = s_pend[pp].y;
-          xh = (s0 < TS / 2 ? 1 : 0) | (s0 + P > TS / 2 ? 2 : 0);
-        }
-#pragma unroll
-        for (int hf = 0; hf < 2; ++hf) {
-          if (xh & (1 << hf)) {
-            T wx[TS / 2];
-#pragma unroll
-            for (int xx = 0; xx < TS / 2; ++xx) wx[xx] = s_w[pp][hf * (TS / 2) + xx] * wyz;
-#pragma unroll
-            for (int c = 0; c < CMAX; ++c) {
-              if (c < C) {
-                const T fv = s_f[pp][c];
-#pragma unroll
-                for (int xx = 0; xx < TS / 2; ++xx) acc[hf * (TS / 2) + xx][c] += wx[xx] * fv;
-              }
-            }
-          }
-        }
-      }
-    }
-    __syncthreads();
-  };
-  // stream the source bins: keep the points whose support [base + rel, base + rel + P) meets
-  // the tile [0, TS) in all three directions (a source tile is reached only in part),
-  // collected across bins so that every staged chunk is full
-  int npend = 0;
-  for (int ib = slab; ib < nbins; ib += nslab) {
-    const int ix = ib / (nby * nbz), iy = (ib / nbz) % nby, iz = ib % nbz;
-    const int bin = (s_bin[0][ix] * g.ntile[1] + s_bin[1][iy]) * g.ntile[2] + s_bin[2][iz];
-    const int beg = tile_start[bin], end = tile_start[bin + 1];
-    const int rel0 = s_sh[0][ix] - o[0], rel1 = s_sh[1][iy] - o[1], rel2 = s_sh[2][iz] - o[2];
-    for (int p0 = beg; p0 < end; p0 += CH) {
-      const int cnt = min(CH, end - p0);
-      bool reach = false;
-      int s0 = 0, s1 = 0, s2 = 0;
-      if (tid < cnt) {
-        const int* bp = base + 3 * (size_t)(p0 + tid);
-        s0 = bp[0] + rel0;
-        s1 = bp[1] + rel1;
-        s2 = bp[2] + rel2;
-        reach = s0 < TS && s0 + P > 0 && s1 < TS && s1 + P > 0 && s2 < TS && s2 + P > 0;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, reach);
-      if (lane == 0) s_wcnt[warp] = __popc(bal);
-      __syncthreads();
-      const int w0c = s_wcnt[0], tot = w0c + s_wcnt[1];
-      if (reach) s_pend[npend + (warp ? w0c : 0) + __popc(bal & ((1u << lane) - 1u))] = make_int4(p0 + tid, s0, s1, s2);
-      npend += tot;
-      __syncthreads();
-      if (npend >= CH) {
-        spread_pending(CH);
-        npend -= CH;  // move the rest (< CH) to the front
-        int4 v = make_int4(0, 0, 0, 0);
-        if (tid < npend) v = s_pend[CH + tid];
-        __syncthreads();
-        if (tid < npend) s_pend[tid] = v;
-        __syncthreads();
-      }
-    }
-  }
-  if (npend > 0) spread_pending(npend);
-  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
-  const int y = o[1] + ly, z = o[2] + lz;
-  if (y < g.m[1] && z < g.m[2]) {
-#pragma unroll
-    for (int xx = 0; xx < TS; ++xx) {
-      const int x = o[0] + xx;
-      if (x >= g.m[0]) continue;
-      const size_t off = ((size_t)x * g.n[1] + y) * g.n[2] + z;
-#pragma unroll
-      for (int c = 0; c < CMAX; ++c) {
-        if (c < C) {
-          if (nslab == 1) grid[(c0 + c) * G + off] = acc[xx][c];
-          else atomicAdd(&grid[(c0 + c) * G + off], acc[xx][c]);
-        }
-      }
-    }
-  }
 }
 
 // ============================================== scaling step, Eq. (SE-scaling-disc), D = 3
@@ -569,7 +409,7 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
   T acc[NCMAX];
 #pragma unroll
   for (int c = 0; c < NCMAX; ++c) acc[c] = T(0);
-  const int G = g.n[0] * n12;  // grid points per component (< 2^31, checked at plan creation)
+  const int G = (int)g.cs;  // grid points per component (< 2^31, checked at plan creation)
   const T* w0 = s_w[warp];
   const T* w1 = s_w[warp] + P;
   const T* w2 = s_w[warp] + 2 * P;
@@ -629,414 +469,6 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
   }
 }
 
-// ====================================== real-space sum, Eq. (real-space-potential-Dp)
-//
-// Cell list of cells with side >= rc / S (S = range); one thread per target looping over
-// the (2S+1)^3 neighbour cells with periodic images in the periodic directions. A pair at
-// exactly zero separation is the omitted self interaction of the star sum: it contributes
-// the self term -G^F(0) . f (Eq. self-term) instead, so the star form and explicit
-// coincident targets agree.
-
-template <typename T>
-struct RealArgs {
-  CellGeom cg;
-  T xi, rc2;
-  int kernel, n_rhs, nsrc, ntgt;
-  T Lhi[3], Llo[3];                  // box lengths as hi + lo parts (image shifts)
-  int overwrite;                     // 1: u = sum, 0: u += sum
-  int maxseg, cols_per_round;        // segment-table layout (real_seg_setup)
-  const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
-  const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
-  const T* fs;                       // sorted strengths [ns][c * n_rhs]
-  const int* cstart;                 // cell starts [ncell+1]
-  const typename Vec4<T>::type* xt;  // sorted targets
-  const typename Vec4<T>::type* xtl; // low parts of the sorted targets (FP32 only)
-  const int* tperm;                  // sorted target -> original index
-  const int* tcell;                  // cell of each sorted target ([3] ints)
-  T* u;
-};
-
-// erfc(x), x >= 0, given g = exp(-x^2) (computed anyway for the Gaussian terms).
-// FP32: erfc(x) = g t R(t), t = 1 / (1 + a x), R the degree-10 polynomial of se_erfc_fit.h
-// (relative error of the fit < 1e-8; a few FP32 ulp after rounding). FP64: the library erfc.
-template <typename T>
-__device__ inline T dev_erfc_g(T x, T g);
-template <> __device__ __forceinline__ float dev_erfc_g<float>(float x, float g) {
-  const float t = __frcp_rn(fmaf(float(SE_ERFC_FIT_A), x, 1.0f));
-  float r = float(SE_ERFC_FIT_C10);
-  r = fmaf(r, t, float(SE_ERFC_FIT_C9));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C8));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C7));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C6));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C5));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C4));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C3));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C2));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C1));
-  r = fmaf(r, t, float(SE_ERFC_FIT_C0));
-  return g * (t * r);
-}
-template <> __device__ __forceinline__ double dev_erfc_g<double>(double x, double) { return erfc(x); }
-
-// One pair (target, source image): accumulate G^R(r) . f into acc, or the self term when
-// the separation is exactly zero (the omitted n = m, p = 0 term of the star sum).
-template <typename T, int KERNEL, int RMAX>
-__device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, T c2pi, const T* __restrict__ f,
-                                          int n_rhs, T* acc) {
-  if (rr2 == T(0)) {
-    if (KERNEL == SE_STOKESLET || KERNEL == SE_KERNEL_ST) {
-      const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi), Eq. (3p-stokeslet-self-term)
-      constexpr int STRIDE = KERNEL == SE_KERNEL_ST ? 9 : 3;
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r)
-        if (r < n_rhs)
-          for (int q = 0; q < 3; ++q) acc[3 * r + q] += cs * f[STRIDE * r + q];
-    }
-    return;
-  }
-  const T inv = rsqrt(rr2);
-  const T rn = rr2 * inv;
-  const T inv2 = inv * inv;
-  const T e = exp(-xi2 * rr2);
-  const T ec = dev_erfc_g(xi * rn, e) * inv;
-  if (KERNEL == SE_STOKESLET) {
-    // Eq. (stokeslet-real): (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e/sqrt pi
-    const T c1 = ec + c2pi * e;
-    const T c0 = c1 - T(2) * c2pi * e;
-    const T c1i = c1 * inv2;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r < n_rhs) {
-        const T* fr = f + 3 * r;
-        const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1i;
-        acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
-        acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
-        acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
-      }
-    }
-  } else if (KERNEL == SE_HARMONIC_FIELD) {
-    // -grad of the screened harmonic kernel erfc(xi r)/r: r_j / r^2 (erfc/r + 2 xi e/sqrt pi) q
-    // (the rotlet's radial factor, Eq. rotlet-real, with the gradient in place of the curl)
-    const T c1 = (ec + c2pi * e) * inv2;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r < n_rhs) {
-        const T cq = c1 * f[r];
-        acc[3 * r + 0] += cq * r0;
-        acc[3 * r + 1] += cq * r1;
-        acc[3 * r + 2] += cq * r2;
-      }
-    }
-  } else if (KERNEL == SE_ROTLET) {
-    // Eq. (rotlet-real): eps_jlm r_m / r^2 (erfc/r + 2 xi e/sqrt pi) f_l = (f x r)_j c
-    const T c1 = (ec + c2pi * e) * inv2;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r < n_rhs) {
-        const T* fr = f + 3 * r;
-        acc[3 * r + 0] += c1 * (fr[1] * r2 - fr[2] * r1);
-        acc[3 * r + 1] += c1 * (fr[2] * r0 - fr[0] * r2);
-        acc[3 * r + 2] += c1 * (fr[0] * r1 - fr[1] * r0);
-      }
-    }
-  } else {
-    // Eq. (stresslet-real): -2 r_j r_l r_m / r^4 (3 erfc/r + (3 + 2 xi^2 r^2) 2 xi e/sqrt pi)
-    //   + (delta_jl r_m + delta_mj r_l + delta_lm r_j) 4 xi^3 e / sqrt pi
-    // (S|T: the stokeslet term of Eq. stokeslet-real on f as above, then this on (q, nu))
-    constexpr int STRIDE = KERNEL == SE_KERNEL_ST ? 9 : 6;
-    constexpr int QOFF = KERNEL == SE_KERNEL_ST ? 3 : 0;
-    if (KERNEL == SE_KERNEL_ST) {
-      const T c1 = ec + c2pi * e;
-      const T c0 = c1 - T(2) * c2pi * e;
-      const T c1i = c1 * inv2;
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        if (r < n_rhs) {
-          const T* fr = f + STRIDE * r;
-          const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1i;
-          acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
-          acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
-          acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
-        }
-      }
-    }
-    const T A = T(3) * ec + (T(3) + T(2) * xi2 * rr2) * c2pi * e;
-    const T B = T(2) * xi2 * c2pi * e;
-    const T Ai = -T(2) * A * inv2 * inv2;
-#pragma unroll
-    for (int r = 0; r < RMAX; ++r) {
-      if (r < n_rhs) {
-        const T* q = f + STRIDE * r + QOFF;
-        const T* nu = q + 3;
-        const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
-        const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
-        const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
-        const T c3 = Ai * rq * rnu + qn * B;
-        const T bq = B * rnu, bn = B * rq;
-        acc[3 * r + 0] += c3 * r0 + bq * q[0] + bn * nu[0];
-        acc[3 * r + 1] += c3 * r1 + bq * q[1] + bn * nu[1];
-        acc[3 * r + 2] += c3 * r2 + bq * q[2] + bn * nu[2];
-      }
-    }
-  }
-}
-
-// Real-space sum: one warp per target.
-// (1) Column table: the neighbour columns of the target's cell (along direction 2, trimmed to
-//     the cells that can hold sources within rc, split at periodic images into contiguous
-//     source ranges, "segments") are set up one column per lane, all cstart loads in flight
-//     at once; a warp scan lays the segments out as one flat candidate list.
-// (2) Candidates: the warp walks the flat list U x 32 at a time (U = 2 independent loads per
-//     lane), tests them on the hi parts and compacts the ones inside rc (ballot + popc) into a
-//     per-warp ring of pairs.
-// (3) Pairs: whenever 32 are queued they are evaluated one per lane with the exact hi + lo
-//     separation. Lane partial sums are combined by shuffles.
-// More than 32 columns (or more segments than the table holds) are done in rounds.
-constexpr int RS_WARPS = 4;    // warps per CTA
-constexpr int RS_SEGCAP = 64;  // column segments per round
-constexpr int RS_RING = 256;   // pair ring entries (power of two, >= 32 (RS_U + 1))
-template <typename T>
-struct RsU {  // candidate chunks of 32 in flight per lane
-  static constexpr int value = 2;  // 4 in FP32 measured 5 % slower (registers, occupancy)
-};
-
-template <typename T>
-struct RealSmem {
-  typename Vec4<T>::type seg[RS_SEGCAP];  // image shift (x, y, z); w: first source - flat start
-  int start[RS_SEGCAP + 1];              // flat start of each segment (+ total)
-  int len[RS_SEGCAP];
-  int pk[RS_SEGCAP];                     // packed image numbers (3 x 8 bits, biased by 128)
-  int ring_j[RS_RING];
-  int ring_pk[RS_RING];
-};
-
-__device__ __forceinline__ float ipack(int v, float) { return __int_as_float(v); }
-__device__ __forceinline__ double ipack(int v, double) { return __longlong_as_double((long long)v); }
-__device__ __forceinline__ int iunpack(float v) { return __float_as_int(v); }
-__device__ __forceinline__ int iunpack(double v) { return (int)__double_as_longlong(v); }
-
-// wrap an unwrapped cell index into [0, n) and return the image number
-__device__ __forceinline__ int wrap_cell(int u, int n, int* im) {
-  int k = 0;
-  while (u < 0) { u += n; --k; }
-  while (u >= n) { u -= n; ++k; }
-  *im = k;
-  return u;
-}
-
-template <typename T, int KERNEL, int RMAX>
-__global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
-  __shared__ RealSmem<T> sm_all[RS_WARPS];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * RS_WARPS + warp;
-  if (s >= a.ntgt) return;  // warp-uniform
-  RealSmem<T>& sm = sm_all[warp];
-  typedef typename Vec4<T>::type V4;
-  const V4 xt = a.xt[s];
-  V4 xtl;
-  xtl.x = xtl.y = xtl.z = xtl.w = T(0);
-  if (sizeof(T) == 4) xtl = a.xtl[s];
-  const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
-  const int nc = kernel_comps(KERNEL);
-  const int C = nc * a.n_rhs;
-  T acc[3 * RMAX];
-#pragma unroll
-  for (int k = 0; k < 3 * RMAX; ++k) acc[k] = T(0);
-  const T xi = a.xi;
-  const T xi2 = xi * xi;
-  const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
-  const CellGeom& g = a.cg;
-  // candidate pre-test on the hi parts with a slightly larger radius; the exact test runs
-  // on the hi + lo separation when the pair is evaluated
-  const T cs0 = a.Lhi[0] / T(g.nc[0]), cs1 = a.Lhi[1] / T(g.nc[1]), cs2 = a.Lhi[2] / T(g.nc[2]);
-  const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);
-  const T tx = xt.x, ty = xt.y, tz = xt.z;
-  const T inv_cs2 = T(g.nc[2]) / a.Lhi[2];
-  unsigned head = 0, tail = 0;  // pair ring [head, tail)
-  // evaluate the pairs ring[head .. head + cnt) (cnt <= 32), one per lane
-  // evaluate the queued pairs [0, cnt) (cnt <= 32), one per lane
-  auto flush = [&](int cnt) {
-    __syncwarp();
-    if (lane < cnt) {
-      const int e = (head + lane) & (RS_RING - 1);
-      const int j = sm.ring_j[e], pk = sm.ring_pk[e];
-      const T i0 = T((pk & 255) - 128), i1 = T(((pk >> 8) & 255) - 128), i2 = T(((pk >> 16) & 255) - 128);
-      const V4 xs = a.xs[j];
-      T r0, r1, r2;
-      if (sizeof(T) == 4) {
-        // r = x_target - (x_source + p): hi + lo parts, x_source_hi + shift split exactly
-        const V4 xl = a.xsl[j];
-        const T shx = i0 * a.Lhi[0], shy = i1 * a.Lhi[1], shz = i2 * a.Lhi[2];
-        const T ax = xs.x + shx, ay = xs.y + shy, az = xs.z + shz;
-        const T ex = xs.x - (ax - shx), ey = xs.y - (ay - shy), ez = xs.z - (az - shz);
-        r0 = (xt.x - ax) + ((xtl.x - xl.x) - (i0 * a.Llo[0] + ex));
-        r1 = (xt.y - ay) + ((xtl.y - xl.y) - (i1 * a.Llo[1] + ey));
-        r2 = (xt.z - az) + ((xtl.z - xl.z) - (i2 * a.Llo[2] + ez));
-      } else {
-        r0 = xt.x - (xs.x + i0 * a.Lhi[0]);
-        r1 = xt.y - (xs.y + i1 * a.Lhi[1]);
-        r2 = xt.z - (xs.z + i2 * a.Lhi[2]);
-      }
-      const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
-      if (rr2 < a.rc2)
-        real_pair<T, KERNEL, RMAX>(r0, r1, r2, rr2, xi, xi2, c2pi, a.fs + (size_t)j * C, a.n_rhs, acc);
-    }
-    __syncwarp();
-  };
-  const unsigned FULL = 0xffffffffu;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  const int rx = g.range[0], ry = g.range[1];
-  const int ncy = 2 * ry + 1, ncol = (2 * rx + 1) * ncy;
-  const int maxseg = a.maxseg, cpr = a.cols_per_round;
-  for (int c0 = 0; c0 < ncol; c0 += cpr) {
-    // ---- (1) segments of columns c0 .. c0 + cpr - 1, column c0 + lane on this lane
-    __syncwarp();
-    const int slot0 = lane * maxseg;
-    int nseg = 0, tot = 0;
-    const int k = c0 + lane;
-    if (lane < cpr && k < ncol) {
-      const int kx = k / ncy;
-      const int dx = kx - rx, dy = k - kx * ncy - ry;
-      int imx = 0, imy = 0, ux = cx + dx, uy = cy + dy;
-      bool ok = true;
-      if (g.periodic[0]) ux = wrap_cell(ux, g.nc[0], &imx);
-      else ok = ux >= 0 && ux < g.nc[0];
-      if (g.periodic[1]) uy = wrap_cell(uy, g.nc[1], &imy);
-      else ok = ok && uy >= 0 && uy < g.nc[1];
-      if (ok) {
-        // distance from the target to this image of the column, directions 0 and 1
-        const T x0 = T(cx + dx) * cs0, x1 = x0 + cs0;
-        const T ddx = tx < x0 ? x0 - tx : (tx > x1 ? tx - x1 : T(0));
-        const T y0 = T(cy + dy) * cs1, y1 = y0 + cs1;
-        const T ddy = ty < y0 ? y0 - ty : (ty > y1 ? ty - y1 : T(0));
-        const T rem = rcp2 - ddx * ddx - ddy * ddy;
-        if (rem > T(0)) {
-          // cells along direction 2 that can hold sources within rc: |z - tz| < sqrt(rem)
-          const T zr = sqrt(rem);
-          int zlo = (int)floor((tz - zr) * inv_cs2), zend = (int)floor((tz + zr) * inv_cs2);
-          zlo = max(zlo, cz - g.range[2]);
-          zend = min(zend, cz + g.range[2]);
-          if (!g.periodic[2]) {
-            zlo = max(zlo, 0);
-            zend = min(zend, g.nc[2] - 1);
-          }
-          const T shx = T(imx) * a.Lhi[0], shy = T(imy) * a.Lhi[1];
-          const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
-          while (zlo <= zend && nseg < maxseg) {
-            int imz = 0, w0 = zlo;
-            if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
-            const int w1 = min(g.nc[2] - 1, w0 + (zend - zlo));  // up to the end of this image
-            const int beg = a.cstart[colbase + w0], end = a.cstart[colbase + w1 + 1];
-            V4 sg;
-            sg.x = shx;
-            sg.y = shy;
-            sg.z = T(imz) * a.Lhi[2];
-            sg.w = ipack(beg, T());
-            sm.seg[slot0 + nseg] = sg;
-            sm.len[slot0 + nseg] = end - beg;
-            sm.pk[slot0 + nseg] = (imx + 128) | ((imy + 128) << 8) | ((imz + 128) << 16);
-            tot += end - beg;
-            ++nseg;
-            zlo += w1 - w0 + 1;
-          }
-        }
-      }
-    }
-    if (lane < cpr)
-      for (int i = nseg; i < maxseg; ++i) sm.len[slot0 + i] = 0;
-    int inc = tot;  // inclusive warp scan of the per-column candidate counts
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-      const int v = __shfl_up_sync(FULL, inc, off);
-      if (lane >= off) inc += v;
-    }
-    const int total = __shfl_sync(FULL, inc, 31);
-    __syncwarp();
-    if (lane < cpr) {
-      int run = inc - tot;
-      for (int i = 0; i < maxseg; ++i) {
-        const int sl = slot0 + i;
-        sm.start[sl] = run;
-        if (i < nseg) sm.seg[sl].w = ipack(iunpack(sm.seg[sl].w) - run, T());
-        run += sm.len[sl];
-      }
-    }
-    if (lane == 0) sm.start[cpr * maxseg] = total;
-    __syncwarp();
-    // ---- (2) candidates of the flat list, RS_U x 32 per pass
-    int sp = 0;  // this lane's segment (monotone along the list)
-    constexpr int RS_U = RsU<T>::value;
-    for (int b0 = 0; b0 < total; b0 += 32 * RS_U) {
-      int jj[RS_U], sv[RS_U];
-      V4 xv[RS_U];
-      T sx[RS_U], sy[RS_U], sz[RS_U];
-#pragma unroll
-      for (int u = 0; u < RS_U; ++u) {
-        const int f = b0 + 32 * u + lane;
-        sv[u] = -1;
-        if (f < total) {
-          while (sm.start[sp + 1] <= f) ++sp;
-          const V4 sg = sm.seg[sp];
-          sv[u] = sp;
-          jj[u] = iunpack(sg.w) + f;
-          sx[u] = sg.x;
-          sy[u] = sg.y;
-          sz[u] = sg.z;
-          xv[u] = a.xs[jj[u]];
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < RS_U; ++u) {
-        bool in = false;
-        if (sv[u] >= 0) {
-          const T r0 = tx - (xv[u].x + sx[u]), r1 = ty - (xv[u].y + sy[u]), r2 = tz - (xv[u].z + sz[u]);
-          in = r0 * r0 + r1 * r1 + r2 * r2 < rcp2;
-        }
-        const unsigned bal = __ballot_sync(FULL, in);
-        if (in) {
-          const int e = (tail + __popc(bal & lt_mask)) & (RS_RING - 1);
-          sm.ring_j[e] = jj[u];
-          sm.ring_pk[e] = sm.pk[sv[u]];
-        }
-        tail += __popc(bal);
-      }
-      // ---- (3) pairs, 32 at a time
-      while (tail - head >= 32u) {
-        flush(32);
-        head += 32;
-      }
-    }
-  }
-  if (tail != head) flush((int)(tail - head));
-#pragma unroll
-  for (int k = 0; k < 3 * RMAX; ++k) {
-    T v = acc[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    acc[k] = v;
-  }
-  if (lane == 0) {
-    const int i = a.tperm[s];
-    for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-      for (int qq = 0; qq < 3; ++qq) {
-        T* o = a.u + ((size_t)r * a.ntgt + i) * 3 + qq;
-        *o = a.overwrite ? acc[3 * r + qq] : *o + acc[3 * r + qq];
-      }
-  }
-}
-
-// Segment-table layout of a real-space launch: segments per column (periodic direction 2
-// splits a column at each image boundary) and columns per round.
-template <typename T>
-static se_status real_seg_setup(RealArgs<T>& ra) {
-  const CellGeom& g = ra.cg;
-  int maxseg = 1;
-  if (g.periodic[2]) maxseg = (2 * g.range[2] + 1 + g.nc[2] - 1) / g.nc[2] + 1;
-  if (maxseg > RS_SEGCAP) return SE_ERR_UNSUPPORTED;
-  ra.maxseg = maxseg;
-  ra.cols_per_round = std::min(32, RS_SEGCAP / maxseg);
-  return SE_OK;
-}
 
 // cell sort, last pass: perm, the wrapped position of point i as hi (+ lo, FP32) parts, its
 // cell coordinates (when cell3 is given) and (sources) its strengths, at slot start[key] + rank
@@ -1147,6 +579,10 @@ static void free_plan(se_plan_t* p) {
     for (auto& kv : *p->inv) cufftDestroy(kv.second);
     delete p->inv;
   }
+  if (p->ffree) {
+    for (auto& kv : *p->ffree) cufftDestroy(kv.second);
+    delete p->ffree;
+  }
   if (p->pkb_coef.p) cudaFree(p->pkb_coef.p);
   for (int d = 0; d < 3; ++d) {
     if (p->gtab[d].p) cudaFree(p->gtab[d].p);
@@ -1222,6 +658,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   p->bufs = new std::map<std::string, DevBuf>();
   p->fwd = new std::map<int, cufftHandle>();
   p->inv = new std::map<int, cufftHandle>();
+  p->ffree = new std::map<long long, cufftHandle>();
   p->D = D;
   for (int d = 0; d < 3; ++d) p->L[d] = box[d];
   p->xi = xi;
@@ -1265,7 +702,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
           double theta = k == SE_ROTLET ? 0.0 : 8.0;
           v = std::max(v, md + P + (lam - 1.0) * std::max((double)P, theta));
         }
-        me = fM * (int)std::ceil(v / fM - 1e-9);
+        me = round_extent((int)std::ceil(v - 1e-9), fM, (o.flags & SE_FLAG_FFT_SIZES) != 0);
       }
       if ((me & 1) || me < (int)std::ceil(md - 1e-9) + P) {
         free_plan(p);
@@ -1278,6 +715,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
     }
     g.ntile[d] = cdiv(g.m[d], TS);
   }
+  g.cs = D == 0 ? (long long)g.m[0] * g.n[1] * g.n[2] : (long long)g.n[0] * g.n[1] * g.n[2];
   if ((double)g.n[0] * g.n[1] * g.n[2] >= 2147483647.0) {  // grid offsets are 32-bit per component
     free_plan(p);
     return SE_ERR_UNSUPPORTED;
@@ -1309,9 +747,10 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
       if (D == 2) kmax = std::min(kmax, g.m[1] / 2 - 1);
       p->kbar_star = std::max(0, std::min(ks, kmax));
     }
+    const bool smooth = (o.flags & SE_FLAG_FFT_SIZES) != 0;
     for (int d = D; d < 3; ++d) {
-      p->ncls[0][d] = fM * (int)std::ceil(p->s0 * g.m[d] / fM - 1e-9);
-      p->ncls[1][d] = fM * (int)std::ceil(std::max(1.0, p->s_star) * g.m[d] / fM - 1e-9);
+      p->ncls[0][d] = round_extent((int)std::ceil(p->s0 * g.m[d] - 1e-9), fM, smooth);
+      p->ncls[1][d] = round_extent((int)std::ceil(std::max(1.0, p->s_star) * g.m[d] - 1e-9), fM, smooth);
       p->ncls[2][d] = g.m[d];
     }
   }
@@ -1396,7 +835,7 @@ extern "C" se_status se_debug_grid(se_plan_h p, void* dst, unsigned long long by
   auto it = p->bufs->find("grid");
   if (it == p->bufs->end() || p->last_grid_comps == 0) return SE_ERR_ARG;
   size_t es = p->prec == SE_FP32 ? 4 : 8;
-  size_t need = es * (size_t)p->last_grid_comps * p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
+  size_t need = es * (size_t)p->last_grid_comps * (size_t)p->geom.cs;
   if (bytes < need) return SE_ERR_ARG;
   SE_CUDA(cudaStreamSynchronize(p->stream));
   SE_CUDA(cudaMemcpy(dst, it->second.p, need, cudaMemcpyDeviceToHost));
@@ -1454,37 +893,18 @@ se_status fft_exec<double>(cufftHandle h, bool forward, double* real, double* cp
   return SE_OK;
 }
 
-template <typename T, int CMAX>
-void spread_launch_group(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int Ctot,
-                         int c0, int C, int nslab, T* grid) {
-  const GridGeom& g = p->geom;
-  dim3 grd(g.ntile[0] * nslab, g.ntile[1], g.ntile[2]);
-  ++p->launches;
-  k_spread<T, CMAX><<<grd, 64, 0, p->stream>>>(g, tile_start, base, w, sf, Ctot, c0, C, nslab, grid);
+// the gridding on the tensor cores (opt-in, FP32, P <= 16) bins points by TS^3 cells; the
+// CUDA-core gridding (k_grid, se_grid.cu) by 4^3 cells
+bool use_tc_gridding(const se_plan_t* p) {
+  return p->prec == SE_FP32 && (p->flags & SE_FLAG_TC_GRIDDING) && p->geom.P <= 16;
 }
 
 template <typename T>
-se_status spread_launch(se_plan_t* p, const int* tile_start, const int* base, const T* w, const T* sf, int C,
+se_status spread_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C,
                         T* grid) {
-  if (sizeof(T) == 4 && (p->flags & SE_FLAG_TC_GRIDDING) && p->geom.P <= 16)
-    return spread_tc_launch(p, tile_start, base, (const float*)w, (const float*)sf, C, (float*)grid);
-  // deal the source tiles of each output tile over nslab CTAs so that the grid has enough
-  // CTAs to fill the GPU; the partial tiles are then added atomically into a zeroed grid.
-  // Components go in groups that keep the register accumulators small enough for several
-  // CTAs per SM (12 floats or 6 doubles per grid point; 24 halved the rate at 8 RHS).
-  const GridGeom& g = p->geom;
-  const long long tiles = (long long)g.ntile[0] * g.ntile[1] * g.ntile[2];
-  int nslab = (int)std::min<long long>(9, std::max<long long>(1, (16LL * 152 + tiles - 1) / tiles));
-  const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
-  if (nslab > 1) cudaMemsetAsync(grid, 0, sizeof(T) * C * G, p->stream);
-  const int CG = sizeof(T) == 4 ? 12 : 6;
-  for (int c0 = 0; c0 < C; c0 += CG) {
-    const int Cc = std::min(CG, C - c0);
-    if (Cc <= 3) spread_launch_group<T, 3>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
-    else if (Cc <= 6) spread_launch_group<T, 6>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
-    else spread_launch_group<T, 12>(p, tile_start, base, w, sf, C, c0, Cc, nslab, grid);
-  }
-  return SE_OK;
+  if (sizeof(T) == 4 && use_tc_gridding(p))
+    return spread_tc_launch(p, bin_start, base, (const float*)w, (const float*)sf, C, (float*)grid);
+  return grid_launch<T>(p, bin_start, base, w, sf, C, grid);
 }
 
 template <typename T, int NC>
@@ -1492,20 +912,6 @@ void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, c
                    T scale, T* u) {
   ++p->launches;
   k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u);
-}
-
-template <typename T, int K, int R>
-void real_launch_k(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
-  ++p->launches;
-  k_real<T, K, R><<<grid1d(a.ntgt, RS_WARPS), 32 * RS_WARPS, 0, st>>>(a);
-}
-template <typename T, int R>
-void real_launch(se_plan_t* p, cudaStream_t st, const RealArgs<T>& a) {
-  if (a.kernel == SE_STOKESLET) real_launch_k<T, SE_STOKESLET, R>(p, st, a);
-  else if (a.kernel == SE_ROTLET) real_launch_k<T, SE_ROTLET, R>(p, st, a);
-  else if (a.kernel == SE_STRESSLET) real_launch_k<T, SE_STRESSLET, R>(p, st, a);
-  else if (a.kernel == SE_HARMONIC_FIELD) real_launch_k<T, SE_HARMONIC_FIELD, R>(p, st, a);
-  else real_launch_k<T, SE_KERNEL_ST, R>(p, st, a);
 }
 
 // u += v elementwise (join of the real-space part computed on the side stream)
@@ -1548,8 +954,11 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   }
   // ---------------- real-space part
   if (parts & (SE_PART_REAL | SE_PART_CORR)) {
+    // cells of side >= rc / S: S = 2 for k_real alone; S = 4 with the dense-block path
+    // (SE_FLAG_REAL_BLOCKS), whose blocks of 32 targets then fit in one or two cells
+    const bool blocks = (p->flags & SE_FLAG_REAL_BLOCKS) != 0;
     CellGeom cg;
-    const int S = 2;
+    const int S = blocks ? 4 : 2;
     for (int d = 0; d < 3; ++d) {
       int nc = (int)std::floor(S * p->L[d] / p->rc);
       nc = std::max(1, std::min(nc, 128));
@@ -1594,7 +1003,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       tperm = tp2;
     }
     if ((parts & SE_PART_REAL) && NT > 0) {
-      RealArgs<T> ra;
+      RealArgs<T> ra{};
       ra.cg = cg;
       for (int d = 0; d < 3; ++d) {
         ra.Lhi[d] = (T)p->L[d];
@@ -1616,12 +1025,16 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       ra.tcell = (int*)tcell;
       ra.u = overlap ? ureal : u;
       ra.overwrite = overlap ? 1 : 0;
+      for (int d = 0; d < 3; ++d) ra.cs[d] = (T)(p->L[d] / cg.nc[d]);
       SE_TRY(real_seg_setup(ra));
       if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
-      if (n_rhs <= 1) real_launch<T, 1>(p, rs, ra);
-      else if (n_rhs <= 4) real_launch<T, 4>(p, rs, ra);
-      else if (n_rhs <= 8) real_launch<T, 8>(p, rs, ra);
-      else real_launch<T, 16>(p, rs, ra);
+      if (blocks) {
+        void* work;
+        SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 2), &work));
+        SE_TRY(real_launch_blocks<T>(rs, ra, (int*)work, 0.5 * p->rc, &p->launches));
+      } else {
+        p->launches += real_launch<T>(rs, ra);
+      }
       if (p->timers.on) cudaEventRecord(p->timers.ev[11], rs);
       SE_CUDA(cudaGetLastError());
     }
@@ -1630,7 +1043,11 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
 
   // ---------------- Fourier-space part (Alg. 1)
   if (parts & SE_PART_FOURIER) {
-    const int ntiles = g.ntile[0] * g.ntile[1] * g.ntile[2];
+    BinGeom bg;
+    bg.g = g;
+    bg.bs = use_tc_gridding(p) ? TS : 4;
+    for (int d = 0; d < 3; ++d) bg.nb[d] = cdiv(g.m[d], bg.bs);
+    const int ntiles = bg.nb[0] * bg.nb[1] * bg.nb[2];
     int *perm, *tstart;
     void *base, *wts, *sf;
     SE_TRY(buf(p, "base", sizeof(int) * 3 * (size_t)std::max(N, 1), &base));
@@ -1644,7 +1061,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     wa.beta = (T)p->win.beta;
     wa.inv_i0beta = (T)(1.0 / p->win.i0beta);
     wa.pkb = (const T*)p->pkb_coef.p;
-    SE_TRY(counting_sort(p, st, "tile", N, ntiles, tile_keyfun, src, &g, &perm, &tstart,
+    SE_TRY(counting_sort(p, st, "tile", N, ntiles, tile_keyfun, src, &bg, &perm, &tstart,
                          [&](const int* key, const int* rank, const int* start, int* pm) {
                            k_scatter_tile<T><<<grid1d(N, 128), 128, 0, st>>>(g, wa, key, rank, start, N, src,
                                                                             kernel, strengths, n_rhs, pm,
@@ -1652,15 +1069,21 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
                                                                             p->d_status);
                          }));
     stage.mark();  // 1: bin + weights
-    const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t G = (size_t)g.cs;
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
     void *grid, *spec = nullptr, *ugrid;
     SE_TRY(buf(p, "grid", sizeof(T) * C * G, &grid));
     // the scaling step writes NC components in place over C (the harmonic field: C < NC)
     if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * std::max(C, NC) * H, &spec));
     SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
-    if (g.n[0] != g.m[0] || g.n[1] != g.m[1] || g.n[2] != g.m[2])
-      SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));  // zero padding (D = 0)
+    if (p->D == 0 && (p->zeroed_grid != grid || p->zeroed_grid_C != C)) {
+      // D = 0: the grid [C][M'0][2M'1][2M'2] is zero beyond M' along directions 1 and 2; the
+      // gridding writes only the first M' (every point there), so the padding is set once
+      // per buffer and layout
+      SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));
+      p->zeroed_grid = grid;
+      p->zeroed_grid_C = C;
+    }
     SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid));
     SE_CUDA(cudaGetLastError());
     p->last_grid_comps = C;
@@ -1691,7 +1114,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       void *base2, *wts2;
       SE_TRY(buf(p, "tbase", sizeof(int) * 3 * (size_t)std::max(NT, 1), &base2));
       SE_TRY(buf(p, "twts", sizeof(T) * 3 * g.P * (size_t)std::max(NT, 1), &wts2));
-      SE_TRY(counting_sort(p, st, "ttile", NT, ntiles, tile_keyfun, tgt, &g, &perm2, &tstart2,
+      SE_TRY(counting_sort(p, st, "ttile", NT, ntiles, tile_keyfun, tgt, &bg, &perm2, &tstart2,
                            [&](const int* key, const int* rank, const int* start, int* pm) {
                              k_scatter_tile<T><<<grid1d(NT, 128), 128, 0, st>>>(
                                  g, wa, key, rank, start, NT, tgt, kernel, (const T*)nullptr, n_rhs, pm,
@@ -1708,7 +1131,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       if (NC <= 3) {
         gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
       } else {
-        const size_t GG = (size_t)g.n[0] * g.n[1] * g.n[2];
+        const size_t GG = (size_t)g.cs;
         for (int c0 = 0; c0 < NC; c0 += 6)
           gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), scale,
                               u + (size_t)(c0 / 3) * NT * 3);
@@ -2040,7 +1463,7 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   k_scan<<<1, 1024, 0, st>>>(count, start, ncell);
   k_scatter_cell<T><<<grid1d(N, 256), 256, 0, st>>>(cg, key, rank, start, N, src, kernel, f, 1, perm, xs, xsl,
                                                      tcell, fs, status);
-  RealArgs<T> ra;
+  RealArgs<T> ra{};
   ra.cg = cg;
   for (int d = 0; d < 3; ++d) {
     ra.Lhi[d] = (T)box[d];
@@ -2063,10 +1486,7 @@ se_status real_noalloc_impl(int D, const double* box, double xi, double rc, int 
   ra.u = u;
   ra.overwrite = 0;
   SE_TRY(real_seg_setup(ra));
-  const int grid = grid1d(N, RS_WARPS);
-  if (kernel == SE_STOKESLET) k_real<T, SE_STOKESLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
-  else if (kernel == SE_ROTLET) k_real<T, SE_ROTLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
-  else k_real<T, SE_STRESSLET, 1><<<grid, 32 * RS_WARPS, 0, st>>>(ra);
+  real_launch<T>(st, ra);
   SE_CUDA(cudaGetLastError());
   // the binning kernels flag a free-direction coordinate outside [0, L) or a non-finite one;
   // read the word back (4 bytes into a host variable, no allocation) and wait for the stream

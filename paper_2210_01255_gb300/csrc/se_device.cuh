@@ -122,4 +122,70 @@ __device__ inline int tile_list(const GridGeom& g, int d, int o, int E, int* bin
   return nb;
 }
 
+
+// ---------------------------------------------------------------- real-space cell list
+
+// Wrap a coordinate of a periodic direction into [0, L); flag a free coordinate outside
+// [0, L) or a non-finite one.
+__device__ inline double wrap_coord(double x, double L, int periodic, int* status) {
+  if (!isfinite(x)) {
+    atomicOr(status, 1);
+    return 0.0;
+  }
+  if (periodic) {
+    double w = x - floor(x / L) * L;
+    if (w >= L) w -= L;
+    if (w < 0) w = 0;
+    return w;
+  }
+  if (x < 0.0 || x >= L) atomicOr(status, 1);
+  return fmin(fmax(x, 0.0), nextafter(L, 0.0));
+}
+
+// key of the real-space cell of each point (cells of side >= rc / S)
+struct CellGeom {
+  int nc[3];
+  int range[3];
+  int periodic[3];
+  double L[3];
+  double inv_cs[3];
+};
+
+// Arguments of the real-space kernels (Eq. real-space-potential-Dp), se_real.cu.
+template <typename T>
+struct RealArgs {
+  CellGeom cg;
+  T xi, rc2;
+  int kernel, n_rhs, nsrc, ntgt;
+  T Lhi[3], Llo[3];                  // box lengths as hi + lo parts (image shifts)
+  int overwrite;                     // 1: u = sum, 0: u += sum
+  int maxseg, cols_per_round;        // segment-table layout (real_seg_setup)
+  const typename Vec4<T>::type* xs;  // sorted sources (wrapped), by cell
+  const typename Vec4<T>::type* xsl; // low parts x - (T)x of the sorted sources (FP32 only)
+  const T* fs;                       // sorted strengths [ns][c * n_rhs]
+  const int* cstart;                 // cell starts [ncell+1]
+  const typename Vec4<T>::type* xt;  // sorted targets
+  const typename Vec4<T>::type* xtl; // low parts of the sorted targets (FP32 only)
+  const int* tperm;                  // sorted target -> original index
+  const int* tcell;                  // cell of each sorted target ([3] ints)
+  T* u;
+  // dense-block path (k_real_blk) and target lists
+  T cs[3];                           // cell sides L_d / nc_d
+  const int* tlist;                  // k_real: sorted targets to evaluate (NULL: all ntgt)
+  const int* tcount;                 // k_real: number of entries of tlist (device)
+};
+
+// segment-table layout of a sparse real-space launch (se_real.cu)
+template <typename T>
+se_status real_seg_setup(RealArgs<T>& ra);
+// the sparse real-space kernel over a.ntgt targets (or the a.tlist entries, grid for at most
+// a.ntgt); returns the kernels launched
+template <typename T>
+int real_launch(cudaStream_t st, const RealArgs<T>& a);
+// the dense-block path: targets grouped in blocks of 32 consecutive (cell-sorted) targets;
+// blocks whose targets lie within a box of side <= thr go to the block kernel, the others'
+// targets to the sparse kernel. work: int scratch of >= ceil(ntgt / 32) + ntgt + 2 entries.
+template <typename T>
+se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, int* work, double thr, int* launches);
+
 }  // namespace se

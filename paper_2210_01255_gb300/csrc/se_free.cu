@@ -8,8 +8,9 @@
 //          K_* (|kbar_i| <= kbar_*, padded to n_*), K_inf (length M'2, in place).
 //   D = 1: grid [C][M0][M'1][M'2] -> 1-D R2C over 0 -> spec [C][M0/2+1][M'1][M'2]; the planes
 //          along (1,2) are transformed per class in the same way.
-//   D = 0: grid [C][2M'0][2M'1][2M'2] (points spread into the first M' of each direction)
-//          -> 3-D R2C -> scaled by the precomputed kernel -> C2R.
+//   D = 0: grid [C][M'0][2M'1][2M'2] (points spread into the first M' of each direction, the
+//          rest zero) -> 2-D R2C over (1,2) into [C][2M'0][2M'1][M'2+1] (planes >= M'0 zero)
+//          -> 1-D C2C over 0 -> scaled by the precomputed kernel -> the inverse steps.
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -618,9 +619,9 @@ namespace {
 // cached cuFFT plans for the free-direction transforms, keyed by a small integer tag
 se_status free_fft(se_plan_t* p, int tag, int batch, int rank, const int* n, int* inembed, int istride,
                    int idist, int* onembed, int ostride, int odist, cufftType type, cufftHandle* out) {
-  int key = (tag << 20) ^ batch;
-  auto it = p->fwd->find(-1 - key);
-  if (it != p->fwd->end()) {
+  const long long key = ((long long)tag << 32) | (unsigned)batch;
+  auto it = p->ffree->find(key);
+  if (it != p->ffree->end()) {
     SE_CUFFT(cufftSetStream(it->second, p->stream));  // the stream the caller issues on now
     *out = it->second;
     return SE_OK;
@@ -629,7 +630,7 @@ se_status free_fft(se_plan_t* p, int tag, int batch, int rank, const int* n, int
   int nn[3] = {n[0], rank > 1 ? n[1] : 0, rank > 2 ? n[2] : 0};
   SE_CUFFT(cufftPlanMany(&h, rank, nn, inembed, istride, idist, onembed, ostride, odist, type, batch));
   SE_CUFFT(cufftSetStream(h, p->stream));
-  (*p->fwd)[-1 - key] = h;
+  (*p->ffree)[key] = h;
   *out = h;
   return SE_OK;
 }
@@ -668,22 +669,43 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   // outputs (C < NC for the harmonic field)
   const int CS = std::max(C, NC);
   if (D == 0) {
-    // 3-D R2C on the 2M' grid, scaled by A^_{R,tr} (Sec. 3.5), C2R
+    // the 3-D R2C of the 2M' grid, scaling by A^_{R,tr} (Sec. 3.5), the C2R. The grid holds
+    // only the first M'_0 planes along direction 0 ([C][M'0][2M'1][2M'2], zero beyond M' along
+    // directions 1 and 2): the transform is done as 2-D R2C over (1, 2) of those M'_0 planes
+    // into a buffer [C][2M'0][2M'1][M'2+1] whose other planes stay zero, then 1-D C2C along
+    // direction 0 into the spectrum; the inverse runs the same steps backwards and keeps the
+    // first M'_0 planes. Same transform as the 3-D one, without its passes over zero planes.
     const int biharm = !harmonic_family(kernel);
     if (!p->atr[biharm].p) return SE_ERR_UNSUPPORTED;  // kernel not in the plan's kernel_mask
-    const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
-    const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
-    void* spec;
+    const int m0 = g.m[0], n0 = g.n[0], n1 = g.n[1], n2 = g.n[2], h2 = n2 / 2 + 1;
+    const size_t GS = (size_t)g.cs;               // real elements per grid component
+    const size_t H = (size_t)n0 * n1 * h2;        // complex elements per spectrum component
+    void *spec, *tmp;
     SE_TRY(buf(p, "spec", sizeof(T) * 2 * CS * H, &spec));
-    int n[3] = {g.n[0], g.n[1], g.n[2]};
-    cufftHandle hf, hi;
-    SE_TRY(free_fft(p, 1, C, 3, n, nullptr, 1, (int)G, nullptr, 1, (int)H, FT<T>::R2C, &hf));
-    SE_TRY(free_fft(p, 2, NC, 3, n, nullptr, 1, (int)H, nullptr, 1, (int)G, FT<T>::C2R, &hi));
-    SE_CUFFT(FT<T>::r2c(hf, grid, (T*)spec));
+    SE_TRY(buf(p, "tmp0p", sizeof(T) * 2 * C * H, &tmp));
+    if (p->zeroed_tmp != tmp || p->zeroed_tmp_C != C) {
+      SE_CUDA(cudaMemsetAsync(tmp, 0, sizeof(T) * 2 * C * H, st));
+      p->zeroed_tmp = tmp;
+      p->zeroed_tmp_C = C;
+    }
+    int nA[2] = {n1, n2};
+    int nB[1] = {n0}, eB[1] = {n0};
+    const int lines = n1 * h2;
+    cufftHandle hA, hB, hAi;
+    SE_TRY(free_fft(p, 20, m0, 2, nA, nullptr, 1, n1 * n2, nullptr, 1, lines, FT<T>::R2C, &hA));
+    SE_TRY(free_fft(p, 21, lines, 1, nB, eB, lines, 1, eB, lines, 1, FT<T>::C2C, &hB));
+    SE_TRY(free_fft(p, 22, m0, 2, nA, nullptr, 1, lines, nullptr, 1, n1 * n2, FT<T>::C2R, &hAi));
+    for (int c = 0; c < C; ++c) {
+      SE_CUFFT(FT<T>::r2c(hA, grid + c * GS, (T*)tmp + 2 * c * H));
+      SE_CUFFT(FT<T>::c2c(hB, (T*)tmp + 2 * c * H, (T*)spec + 2 * c * H, CUFFT_FORWARD));
+    }
     ScaleTables<T> tb{(const T*)p->ptab[0].p, (const T*)p->ptab[1].p, (const T*)p->ptab[2].p,
                       (const T*)p->atr[biharm].p};
     SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
-    SE_CUFFT(FT<T>::c2r(hi, (T*)spec, ugrid));
+    for (int c = 0; c < NC; ++c) {
+      SE_CUFFT(FT<T>::c2c(hB, (T*)spec + 2 * c * H, (T*)spec + 2 * c * H, CUFFT_INVERSE));
+      SE_CUFFT(FT<T>::c2r(hAi, (T*)spec + 2 * c * H, ugrid + c * GS));
+    }
     return SE_OK;
   }
   const int M0 = g.m[0];

@@ -176,6 +176,20 @@ double lambda_table(int kernel, int D) {
 
 using namespace se;
 
+namespace se {
+// the smallest multiple of fM that is >= x; with smooth, also with no prime factor above 7
+int round_extent(int x, int fM, bool smooth) {
+  int v = fM * ((std::max(x, 1) + fM - 1) / fM);
+  if (!smooth) return v;
+  for (;; v += fM) {
+    int r = v;
+    for (int q : {2, 3, 5, 7})
+      while (r % q == 0) r /= q;
+    if (r == 1) return v;
+  }
+}
+}  // namespace se
+
 extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, double Q, long long N,
                                  double tol_rel, se_opts* io, double* xi_io, double* rc_out,
                                  int M_out[3], int* P_out) {
@@ -191,6 +205,10 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
     if (rmask & k) kernels[nk++] = k;
   if (nk == 0) return SE_ERR_ARG;
   const int fM = io->f_M > 0 ? io->f_M : 4;
+  const bool smooth = (io->flags & SE_FLAG_FFT_SIZES) != 0;
+  // a grid extent >= x: the next multiple of f_M (with SE_FLAG_FFT_SIZES: whose prime factors
+  // are 2, 3, 5, 7 only)
+  auto extent = [&](double x) { return round_extent((int)std::ceil(x - 1e-9), fM, smooth); };
   // In the estimates a cube of side L is assumed; for a cuboid L^3 -> |B|, L -> |B|^(1/3).
   const double vol = box[0] * box[1] * box[2];
   const double L = std::cbrt(vol);
@@ -239,7 +257,8 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
   double P_t = Pest + (io->P_margin >= 0 ? (double)io->P_margin : (D == 0 ? 2.0 : 4.0));
   // isotropic h: the first periodic direction (or direction 0 for D = 0) fixes h
   int M[3] = {0, 0, 0};
-  M[0] = fM * (int)std::ceil(box[0] / h_t / fM);
+  // (for D = 0, M_0 only sets h; the transform extents are the M'_i below)
+  M[0] = D > 0 ? extent(box[0] / h_t) : round_extent((int)std::ceil(box[0] / h_t - 1e-9), fM, false);
   double h = box[0] / M[0];
   for (int d = 1; d < 3; ++d) {
     double md = box[d] / h;
@@ -256,7 +275,7 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
   P = std::max(2, std::min(P, MAX_P));
   // the window must fit the grid (P <= M): refine the grid where it does not
   if (M[0] < P) {
-    M[0] = fM * (int)std::ceil((double)P / fM);
+    M[0] = extent((double)P);
     h = box[0] / M[0];
     for (int d = 1; d < 3; ++d) {
       double md = box[d] / h;
@@ -281,7 +300,7 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
         double lm = lam > 0 ? lam : lambda_table(kernels[i], D);
         double theta = kernels[i] == SE_ROTLET ? 0.0 : 8.0;
         double v = box[d] / h + P + (lm - 1.0) * std::max((double)P, theta);  // Eq. (extended-grid-size)
-        Md = std::max(Md, fM * std::ceil(v / fM));
+        Md = std::max(Md, (double)extent(v));
       }
       Mext[d] = Md;
       io->Mext[d] = (int)Md;

@@ -50,6 +50,8 @@ struct GridGeom {
   double h, inv_h;
   double L[3];
   int P;
+  long long cs;     // elements per component of the spread and output grids: n0 n1 n2, or for
+                    // D = 0 m0 n1 n2 (only the first M'_0 planes along direction 0 are stored)
 };
 
 // Host-side description of the window (Sec. 3.3).
@@ -105,6 +107,8 @@ struct se_plan_t {
   // cuFFT plans keyed by batch count (forward R2C and inverse C2R)
   std::map<int, cufftHandle>* fwd = nullptr;
   std::map<int, cufftHandle>* inv = nullptr;
+  // cuFFT plans of the free-direction transforms, keyed by (tag << 32) | batch
+  std::map<long long, cufftHandle>* ffree = nullptr;
 
   // pinned host staging for se_eval_host
   void* pin = nullptr;
@@ -129,6 +133,11 @@ struct se_plan_t {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int launches = 0;  // kernels launched by the last evaluation
+  // D = 0: buffers whose zero padding is in place (pointer and component count at zeroing)
+  void* zeroed_grid = nullptr;
+  int zeroed_grid_C = 0;
+  void* zeroed_tmp = nullptr;
+  int zeroed_tmp_C = 0;
 };
 
 namespace se {
@@ -145,6 +154,9 @@ struct ScaleTables {
 };
 template <typename T>
 se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const ScaleTables<T>& t);
+// gridding on the CUDA cores (se_grid.cu): points sorted by 4^3 bins (bin_start)
+template <typename T>
+se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid);
 // FP32 gridding on the tensor cores (se_spread_tc.cu)
 se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
                            int C, float* grid);
@@ -159,6 +171,7 @@ void upsampling_rule(int D, const double* box, double h, const int* Mext, double
                      int* kbar_star);
 
 // ---- host-side helpers (se_host.cpp) ----
+int round_extent(int x, int fM, bool smooth);
 double bessel_i0(double x);
 void window_setup(WindowDesc* w, int kind, int P, double h);
 double window_hat(const WindowDesc& w, double k);

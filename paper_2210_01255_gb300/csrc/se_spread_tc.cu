@@ -408,7 +408,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
     const int m = 32 * q + lane;
     const int x = o0 + (m >> 3), y = o1 + (m & 7);
     if (x < g.m[0] && y < g.m[1]) {
-      const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+      const size_t G = (size_t)g.cs;
       const size_t row = ((size_t)x * g.n[1] + y) * g.n[2];
 #pragma unroll
       for (int i = 0; i < 24; ++i) {
@@ -448,7 +448,7 @@ se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, con
   // alone would leave SMs idle (partial tiles are then added atomically into a zeroed grid)
   const int nslab = (int)std::min<long long>(8, std::max<long long>(1, (2LL * 152 + tiles - 1) / tiles));
   if (nslab > 1) {
-    const size_t G = (size_t)g.n[0] * g.n[1] * g.n[2];
+    const size_t G = (size_t)g.cs;
     for (int c = 0; c < C; ++c) SE_CUDA(cudaMemsetAsync(grid + (size_t)(c0 + c) * G, 0, sizeof(float) * G, p->stream));
   }
   dim3 grd((unsigned)(t0 * nslab), (unsigned)t1, (unsigned)t2);
