@@ -196,8 +196,10 @@ def make_plan(cfg, item, prec, stream, flags=0):
     """A plan with the evaluation's parameters (extended grid, upsampling factors and kbar_*
     included), for its kernel only."""
     import paper_2210_01255_gb300 as se
+    import paper_2210_01255_gb300 as se_
     t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
-    o.flags = flags
+    # the gridding choice of the command line; the real-space path the selection chose
+    o.flags = flags | (t["opts"].flags & se_.FLAG_REAL_BLOCKS)
     return se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], prec, opts=o,
                    stream=stream), dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
 
@@ -463,7 +465,9 @@ def main():
         it["fdev"] = torch.tensor(it["f"], device=dev)
         it["udev"] = torch.empty((it["R"], it["N"], 3), dtype=tdt, device=dev)
         it["plan"], it["params"] = make_plan(cfg, it, prec, stream, flags)
-        it["grid_n"] = list(it["plan"].info().n)
+        info0 = it["plan"].info()
+        it["grid_n"] = list(info0.n)
+        it["grid_m"] = list(info0.m)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():
@@ -495,6 +499,7 @@ def main():
             info = it["plan"].info()       # waits for this step's stage events
             stage_ms += np.maximum(np.array(list(info.times_ms)), 0.0)
             launches += info.launches
+            it["scale_modes"] = info.scale_modes
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -550,17 +555,15 @@ def main():
     for it in items:
         N, R, P = it["N"], it["R"], it["params"]["P"]
         C = COMPS[it["kernel"]] * R
-        G = float(np.prod(it["grid_n"]))
-        H = float(it["grid_n"][0] * it["grid_n"][1] * (it["grid_n"][2] // 2 + 1))
+        G = float(np.prod(it["grid_m"]))   # grid points the gridding writes (and gathering reads)
         work["spread"] += 2.0 * N * P ** 3 * C        # one FMA per tap per component
         work["gather"] += 2.0 * N * P ** 3 * 3 * R
         # algorithmic HBM bytes: spread N (24 + 4 C) + 4 G C; gather 4 G 3R + 12 N R;
-        # k-space multiply (D = 3; for D < 3 it is timed inside the transforms) (C + 3R) x 8 B
-        # per half-spectrum mode
+        # k-space multiply (C + 3R) x 8 B per k-space mode the scaling step visits (every D:
+        # for D < 3 the modes of the three classes of the adaptive FFT)
         hbm["spread"] += N * (24 + 4 * C) + 4 * G * C
         hbm["gather"] += 4 * G * 3 * R + 12 * N * R
-        if cfg["D"] == 3:
-            hbm["scale"] = hbm.get("scale", 0.0) + (C + 3 * R) * 8 * H
+        hbm["scale"] = hbm.get("scale", 0.0) + (C + 3 * R) * 8 * float(it.get("scale_modes", 0))
         np_ = real_pairs(cfg, it, it["params"]["rc"])
         pairs += np_
         work["real"] += (PAIR_FLOPS[it["kernel"]] + PAIR_FLOPS_RHS[it["kernel"]] * (R - 1)) * np_
@@ -670,7 +673,9 @@ def main():
                                      "P_margin": P_MARGIN if P_MARGIN is not None else cfg.get("P_margin", -1),
                                      "tol_requested": cfg["tol"] / 10.0,
                                      "autotune": cfg.get("autotune", "rules"),
-                                     "timed_ms": [it["tune"].get("ms") for it in items[:4]]},
+                                     "timed_ms": [it["tune"].get("ms") for it in items[:4]],
+                                     "real_space_path": ["dense blocks" if it["tune"]["opts"].flags & se.FLAG_REAL_BLOCKS
+                                                         else "per target" for it in items[:4]]},
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "gridding": "tcgen05" if args.gridding == "tc" else "cuda cores",
                        "parallelism": "replicas" if world > 1 else "single"},

@@ -105,16 +105,18 @@ enum { SE_FLAG_TC_GRIDDING = 1 };
  * se_sync then returns SE_ERR_TIMEOUT and the evaluation's result is invalid. */
 enum { SE_FLAG_TEST_TIMEOUT = 2 };
 /* se_opts.flags: real-space sum with the dense-block path. Targets are grouped in blocks of 32
- * consecutive cell-sorted targets; a block whose targets lie in a box of side <= r_c / 2 is
+ * consecutive cell-sorted targets (cells of side >= r_c / 8); a block whose targets lie in a
+ * box of side <= r_c / 2 is
  * summed by one warp against the candidates of the whole box (staged in shared memory and
  * shared by the 32 targets), the targets of the other blocks one warp per target as without
  * the flag. Pays off where targets have many neighbours (clustered points, large r_c);
  * se_autotune_timed chooses it by timing. Same sums to rounding. */
 enum { SE_FLAG_REAL_BLOCKS = 4 };
-/* se_opts.flags: FFT-friendly grid sizes. se_autotune rounds every grid extent it chooses (M_i,
- * and M'_i of the free directions) up to the next multiple of f_M whose prime factors are
- * 2, 3, 5 and 7 only (cuFFT's fastest radices; the D = 0 transform length 2 M' then has them
- * too), and se_plan_create does the same for the upsampled class lengths of Sec. 4.5. The
+/* se_opts.flags: FFT-friendly grid sizes. se_autotune rounds every grid extent it chooses (M_i
+ * of periodic directions, and M'_i of the free directions) up to the next even number whose
+ * prime factors are 2, 3, 5 and 7 only (cuFFT's fastest radices; the D = 0 transform length
+ * 2 M' then has them too) instead of a multiple of f_M, and se_plan_create does the same for
+ * the upsampled class lengths of Sec. 4.5. The
  * grid only gets finer (h smaller), so the tolerance rules still hold. Without the flag the
  * sizes are the paper's multiples of f_M. */
 enum { SE_FLAG_FFT_SIZES = 8 };
@@ -171,7 +173,10 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * the caller's own sources and strengths (star form) once untimed and twice timed with CUDA
  * events; the walk continues in the improving direction until two candidates are more than
  * 10 % slower than the best, a candidate's grids would use more than half of the free device
- * memory, or its grid is unsupported.
+ * memory, or its grid is unsupported. The real-space path is chosen the same way: both the
+ * per-target and the dense-block path (SE_FLAG_REAL_BLOCKS) are timed at the first candidate,
+ * the faster is used along the walk, both are timed again at the chosen r_c, and the choice is
+ * returned in io_opts->flags (the other flags are kept as given).
  *   periodicity, box, kernel_mask, Q, tol_rel   as se_autotune (kernel_mask: one kernel or
  *                SE_STOKESLET|SE_STRESSLET, as for se_eval; tol_rel > 0, the absolute-tolerance
  *                mode of se_autotune is not offered here). Invalid arguments: SE_ERR_ARG.
@@ -222,12 +227,16 @@ se_status se_eval_host(se_plan_h plan, int kernel_mask, long long n_src, const d
  * direction, m[3]: spread-grid extent per direction), R (truncation radius, 0 for 3P),
  * s0, s_star, kbar_star, the number of kernels launched by the last evaluation and its
  * per-stage device times in ms (times[0..7]: bin, spread, fft, scale, ifft, gather, real,
- * corr; -1 when timing is off). Reading the times waits for the last evaluation. */
+ * corr; -1 when timing is off; for D < 3 "fft" includes the class copies of the adaptive
+ * FFT into their buffers and "ifft" the copies back), and the number of k-space modes per
+ * component that the scaling step visited (all classes). Reading the times waits for the
+ * last evaluation. */
 typedef struct {
   double h, R, s0, s_star, dL[3];
   int n[3], m[3], kbar_star, P;
   float times_ms[8];
   int launches;        /* kernels libse launched in the last evaluation (cuFFT's not counted) */
+  long long scale_modes; /* k-space modes per component that the last scaling step visited  */
 } se_info;
 se_status se_get_info(se_plan_h plan, se_info* info);
 

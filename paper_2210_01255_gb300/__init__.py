@@ -48,7 +48,7 @@ class se_info(ctypes.Structure):
     _fields_ = [("h", ctypes.c_double), ("R", ctypes.c_double), ("s0", ctypes.c_double),
                 ("s_star", ctypes.c_double), ("dL", ctypes.c_double * 3), ("n", ctypes.c_int * 3),
                 ("m", ctypes.c_int * 3), ("kbar_star", ctypes.c_int), ("P", ctypes.c_int),
-                ("times_ms", ctypes.c_float * 8), ("launches", ctypes.c_int)]
+                ("times_ms", ctypes.c_float * 8), ("launches", ctypes.c_int), ("scale_modes", ctypes.c_longlong)]
 
 
 # every symbol declared in include/se.h, with its ctypes signature

@@ -110,6 +110,39 @@ __global__ void k_scan(const int* __restrict__ count, int* __restrict__ start, i
   if (t == nt - 1) start[nk] = part[nt - 1];
 }
 
+// exclusive scan of many counts in three passes: each CTA scans 4096 counts (4 per thread)
+// and writes its total; the totals are scanned by k_scan; the CTA offsets are added.
+constexpr int SCAN_TILE = 4096;
+__global__ void k_scan_tiles(const int* __restrict__ count, int* __restrict__ start, int nk, int* __restrict__ tsum) {
+  __shared__ int part[1024];
+  const int t = threadIdx.x;
+  const size_t b = (size_t)blockIdx.x * SCAN_TILE + 4 * t;
+  int v[4], s = 0;
+  for (int k = 0; k < 4; ++k) {
+    v[k] = b + k < (size_t)nk ? count[b + k] : 0;
+    s += v[k];
+  }
+  part[t] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    const int w = t >= off ? part[t - off] : 0;
+    __syncthreads();
+    part[t] += w;
+    __syncthreads();
+  }
+  int run = t ? part[t - 1] : 0;
+  for (int k = 0; k < 4; ++k) {
+    if (b + k < (size_t)nk) start[b + k] = run;
+    run += v[k];
+  }
+  if (t == 1023) tsum[blockIdx.x] = part[1023];
+}
+__global__ void k_scan_add(int* __restrict__ start, int nk, const int* __restrict__ toff) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < (size_t)nk) start[i] += toff[i / SCAN_TILE];
+  else if (i == (size_t)nk) start[nk] = toff[(nk + SCAN_TILE - 1) / SCAN_TILE];
+}
+
 __global__ void k_scatter_perm(const int* __restrict__ key, const int* __restrict__ rank,
                                const int* __restrict__ start, int n, int* __restrict__ perm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -137,7 +170,18 @@ static se_status counting_sort(se_plan_t* p, cudaStream_t st, const char* tag, i
   SE_CUDA(cudaMemsetAsync(count, 0, sizeof(int) * (size_t)nk, st));
   if (n > 0) keyfun(p, st, x, n, (int*)key, (int*)rank, (int*)count, geom);
   ++p->launches;
-  k_scan<<<1, 1024, 0, st>>>((int*)count, (int*)start, nk);
+  if (nk <= 65536) {
+    k_scan<<<1, 1024, 0, st>>>((int*)count, (int*)start, nk);
+  } else {
+    const int nt = (nk + SCAN_TILE - 1) / SCAN_TILE;
+    void *tsum, *toff;
+    SE_TRY(buf(p, (t + ".tsum").c_str(), sizeof(int) * (size_t)nt, &tsum));
+    SE_TRY(buf(p, (t + ".toff").c_str(), sizeof(int) * (size_t)(nt + 1), &toff));
+    k_scan_tiles<<<nt, 1024, 0, st>>>((int*)count, (int*)start, nk, (int*)tsum);
+    k_scan<<<1, 1024, 0, st>>>((int*)tsum, (int*)toff, nt);
+    k_scan_add<<<grid1d((long long)nk + 1, 256), 256, 0, st>>>((int*)start, nk, (int*)toff);
+    p->launches += 2;
+  }
   if (n > 0) {
     ++p->launches;
     if (scatter) scatter((const int*)key, (const int*)rank, (const int*)start, (int*)perm);
@@ -815,6 +859,7 @@ extern "C" se_status se_get_info(se_plan_h p, se_info* info) {
   }
   for (int i = 0; i < 8; ++i) info->times_ms[i] = p->times_ms[i];
   info->launches = p->launches;
+  info->scale_modes = p->scale_modes;
   return SE_OK;
 }
 
@@ -954,14 +999,17 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   }
   // ---------------- real-space part
   if (parts & (SE_PART_REAL | SE_PART_CORR)) {
-    // cells of side >= rc / S: S = 2 for k_real alone; S = 4 with the dense-block path
-    // (SE_FLAG_REAL_BLOCKS), whose blocks of 32 targets then fit in one or two cells
+    // cells of side >= rc / S: S = 2 (at most 128 per direction) for k_real alone; S = 8 (at
+    // most 256) with the dense-block path (SE_FLAG_REAL_BLOCKS): a block of 32 targets in a
+    // dense region then lies within about one cell, and the candidate columns follow the
+    // sphere around it closely
     const bool blocks = (p->flags & SE_FLAG_REAL_BLOCKS) != 0;
     CellGeom cg;
-    const int S = blocks ? 4 : 2;
+    const int S = blocks ? 8 : 2;
+    const int ncmax = blocks ? 256 : 128;
     for (int d = 0; d < 3; ++d) {
       int nc = (int)std::floor(S * p->L[d] / p->rc);
-      nc = std::max(1, std::min(nc, 128));
+      nc = std::max(1, std::min(nc, ncmax));
       cg.nc[d] = nc;
       double cs = p->L[d] / nc;
       cg.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
@@ -1090,10 +1138,10 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     stage.mark();  // 2: spread
     if (p->D < 3) {
       // adaptive FFT (D = 2, 1) or padded FFT with the precomputed kernel (D = 0)
+      // the forward transforms (3) and the scaling (4) are marked inside fourier_free
       SE_TRY(fourier_free<T>(p, kernel, n_rhs, (T*)grid, C, (T*)ugrid, NC));
-      stage.mark();  // 3
-      stage.mark();  // 4
-      stage.mark();  // 5: fft + scale + ifft reported together under "fft"
+      stage.idx = 5;
+      stage.mark();  // 5: inverse transforms
     } else {
     cufftHandle hf, hi;
     SE_TRY(get_fft(p, true, C, &hf));
@@ -1102,6 +1150,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     stage.mark();  // 3: fft
     ScaleTables<T> tb{(const T*)p->gtab[0].p, (const T*)p->gtab[1].p, (const T*)p->gtab[2].p, nullptr};
     SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
+    p->scale_modes = (long long)H;
     stage.mark();  // 4: scale
     SE_TRY(fft_exec<T>(hi, false, (T*)ugrid, (T*)spec));
     stage.mark();  // 5: ifft
@@ -1324,12 +1373,35 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
     return timed_trial(D, box, kernel_mask, Q, n_src, src, strengths, n_rhs, tol_rel, window, *io,
                        nrc0 * f * f * f, mem_cap, u, e0, e1, c);
   };
+  // the real-space path (per-target k_real, or the dense-block path) is a choice too: both
+  // are timed at f = 1, the faster is kept for the walk over r_c and both are timed again at
+  // the chosen r_c
+  se_opts base = *io;
+  auto run_both = [&](double f, TimedCand* c) {
+    TimedCand a, b;
+    se_opts keep = *io;
+    io->flags = base.flags & ~SE_FLAG_REAL_BLOCKS;
+    se_status sa = run(f, &a);
+    io->flags = base.flags | SE_FLAG_REAL_BLOCKS;
+    se_status sb = run(f, &b);
+    *io = keep;
+    if (sa != SE_OK && sb != SE_OK) return sa;
+    if (sb != SE_OK || (sa == SE_OK && a.ms <= b.ms)) {
+      *c = a;
+      c->o.flags = base.flags & ~SE_FLAG_REAL_BLOCKS;
+    } else {
+      *c = b;
+      c->o.flags = base.flags | SE_FLAG_REAL_BLOCKS;
+    }
+    return SE_OK;
+  };
   // f = 1, then one step down; walk in the better direction while the time keeps improving
   // (two candidates more than 10 % slower than the best, a candidate that does not fit in
   // memory or an unsupported grid end the walk)
   if (st == SE_OK) {
     TimedCand c1, c2;
-    st = run(1.0, &c1);
+    st = run_both(1.0, &c1);
+    if (st == SE_OK) io->flags = c1.o.flags;
     if (st == SE_OK) {
       best = c1;
       se_status s2 = run(step, &c2);
@@ -1354,6 +1426,10 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
         }
       }
     }
+  }
+  if (st == SE_OK && best.f != 1.0) {  // both real-space paths at the chosen r_c
+    TimedCand c;
+    if (run_both(best.f, &c) == SE_OK && c.ms < best.ms) best = c;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

@@ -692,16 +692,19 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     int nB[1] = {n0}, eB[1] = {n0};
     const int lines = n1 * h2;
     cufftHandle hA, hB, hAi;
-    SE_TRY(free_fft(p, 20, m0, 2, nA, nullptr, 1, n1 * n2, nullptr, 1, lines, FT<T>::R2C, &hA));
-    SE_TRY(free_fft(p, 21, lines, 1, nB, eB, lines, 1, eB, lines, 1, FT<T>::C2C, &hB));
-    SE_TRY(free_fft(p, 22, m0, 2, nA, nullptr, 1, lines, nullptr, 1, n1 * n2, FT<T>::C2R, &hAi));
+    SE_TRY(free_fft(p, 30, m0, 2, nA, nullptr, 1, n1 * n2, nullptr, 1, lines, FT<T>::R2C, &hA));
+    SE_TRY(free_fft(p, 31, lines, 1, nB, eB, lines, 1, eB, lines, 1, FT<T>::C2C, &hB));
+    SE_TRY(free_fft(p, 32, m0, 2, nA, nullptr, 1, lines, nullptr, 1, n1 * n2, FT<T>::C2R, &hAi));
     for (int c = 0; c < C; ++c) {
       SE_CUFFT(FT<T>::r2c(hA, grid + c * GS, (T*)tmp + 2 * c * H));
       SE_CUFFT(FT<T>::c2c(hB, (T*)tmp + 2 * c * H, (T*)spec + 2 * c * H, CUFFT_FORWARD));
     }
+    stage_event(p, 3);
     ScaleTables<T> tb{(const T*)p->ptab[0].p, (const T*)p->ptab[1].p, (const T*)p->ptab[2].p,
                       (const T*)p->atr[biharm].p};
     SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
+    p->scale_modes = (long long)H;
+    stage_event(p, 4);
     for (int c = 0; c < NC; ++c) {
       SE_CUFFT(FT<T>::c2c(hB, (T*)spec + 2 * c * H, (T*)spec + 2 * c * H, CUFFT_INVERSE));
       SE_CUFFT(FT<T>::c2r(hAi, (T*)spec + 2 * c * H, ugrid + c * GS));
@@ -753,6 +756,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
       SE_CUFFT(FT<T>::c2c(hzS, (T*)bS, (T*)bS, CUFFT_FORWARD));
     }
     // (iii) scaling per class
+    stage_event(p, 3);
     FreeScale fs;
     fs.h = g.h;
     fs.kf0 = 2.0 * M_PI / g.L[0];
@@ -783,6 +787,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
       k_scale_free<T><<<grid1d((long long)ncolS * nS, 256), 256, 0, st>>>(
           fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[1][2].p, nullptr, nullptr, nullptr, (T*)bS);
     }
+    p->scale_modes = (long long)M0 * H1 * Mz + n0 + (long long)std::max(ncolS, 0) * nS;
+    stage_event(p, 4);
     // (iv) inverse per class, truncate and merge, inverse over (0, 1)
     SE_CUFFT(FT<T>::c2c(hzi, (T*)spec, (T*)spec, CUFFT_INVERSE));
     SE_CUFFT(FT<T>::c2c(hz0i, (T*)b0, (T*)b0, CUFFT_INVERSE));
@@ -838,6 +844,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     SE_TRY(free_fft(p, 27, NC * kst, 2, npS, nullptr, 1, nSy * nSz, nullptr, 1, nSy * nSz, FT<T>::C2C, &hpSi));
     SE_CUFFT(FT<T>::c2c(hpS, (T*)bS, (T*)bS, CUFFT_FORWARD));
   }
+  stage_event(p, 3);
   FreeScale fs;
   fs.h = g.h;
   fs.kf0 = 2.0 * M_PI / g.L[0];
@@ -872,6 +879,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
         fs, kernel, n_rhs, tp0, nullptr, (const T*)p->ftab[1][1].p, (const T*)p->ftab[1][2].p, nullptr, nullptr,
         (T*)bS);
   }
+  p->scale_modes = (long long)H0 * PL + (long long)n0y * n0z + (long long)kst * nSy * nSz;
+  stage_event(p, 4);
   SE_CUFFT(FT<T>::c2c(hpi, (T*)spec, (T*)spec, CUFFT_INVERSE));
   SE_CUFFT(FT<T>::c2c(hp0i, (T*)b0, (T*)b0, CUFFT_INVERSE));
   cm.mode = 0;

@@ -177,11 +177,12 @@ double lambda_table(int kernel, int D) {
 using namespace se;
 
 namespace se {
-// the smallest multiple of fM that is >= x; with smooth, also with no prime factor above 7
+// the smallest multiple of fM that is >= x; with smooth, the smallest even number >= x with no
+// prime factor above 7 (cuFFT's fastest radices)
 int round_extent(int x, int fM, bool smooth) {
   int v = fM * ((std::max(x, 1) + fM - 1) / fM);
   if (!smooth) return v;
-  for (;; v += fM) {
+  for (v = std::max(2, x + (x & 1));; v += 2) {
     int r = v;
     for (int q : {2, 3, 5, 7})
       while (r % q == 0) r /= q;

@@ -133,6 +133,7 @@ struct se_plan_t {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int launches = 0;  // kernels launched by the last evaluation
+  long long scale_modes = 0;  // k-space modes per component the last scaling step visited
   // D = 0: buffers whose zero padding is in place (pointer and component count at zeroing)
   void* zeroed_grid = nullptr;
   int zeroed_grid_C = 0;
@@ -141,6 +142,11 @@ struct se_plan_t {
 };
 
 namespace se {
+
+// record stage event i (per-stage timing, se_set_timing) on the plan's stream
+inline void stage_event(se_plan_t* p, int i) {
+  if (p->timers.on) cudaEventRecord(p->timers.ev[i], p->stream);
+}
 
 // buffer helper: returns device pointer with at least `bytes` bytes (grows, never shrinks)
 se_status buf(se_plan_t* p, const char* name, size_t bytes, void** out);
