@@ -178,8 +178,10 @@ def tuned(cfg, item, prec, stream, flags=0):
         o.P_margin = cfg.get("P_margin", -1)
         if P_MARGIN is not None:
             o.P_margin = P_MARGIN
+        if cfg.get("fft_sizes"):
+            o.flags |= se.FLAG_FFT_SIZES
         if cfg.get("autotune") == "timed":
-            o.flags = flags
+            o.flags |= flags
             t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
                                      cfg["tol"] / 10.0, cfg["window"], opts=o, prec=prec, stream=stream)
         else:
@@ -199,7 +201,7 @@ def make_plan(cfg, item, prec, stream, flags=0):
     import paper_2210_01255_gb300 as se_
     t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
     # the gridding choice of the command line; the real-space path the selection chose
-    o.flags = flags | (t["opts"].flags & se_.FLAG_REAL_BLOCKS)
+    o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES))
     return se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], prec, opts=o,
                    stream=stream), dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
 

@@ -176,7 +176,14 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * memory, or its grid is unsupported. The real-space path is chosen the same way: both the
  * per-target and the dense-block path (SE_FLAG_REAL_BLOCKS) are timed at the first candidate,
  * the faster is used along the walk, both are timed again at the chosen r_c, and the choice is
- * returned in io_opts->flags (the other flags are kept as given).
+ * returned in io_opts->flags (the other flags are kept as given). FP32 trials also bound the
+ * rounding: each candidate evaluates once more with the linear part of the strengths scaled
+ * by 1.3 (f, the stresslet's q, the charges), and the relative rms of u(1.3 f)/1.3 - u(f) over
+ * a fixed sample of 2048 targets estimates its rounding. A candidate whose estimate exceeds
+ * 3.5 tol_rel is not chosen (the FP32 rounding of the free-space transforms grows with xi,
+ * so large grids can cost more accuracy than the truncation rules allow); if no candidate
+ * passes, SE_ERR_UNSUPPORTED. Temporary device memory: one output array (FP32: two, and one
+ * copy of the strengths) and the trial plans (one at a time).
  *   periodicity, box, kernel_mask, Q, tol_rel   as se_autotune (kernel_mask: one kernel or
  *                SE_STOKESLET|SE_STRESSLET, as for se_eval; tol_rel > 0, the absolute-tolerance
  *                mode of se_autotune is not offered here). Invalid arguments: SE_ERR_ARG.
@@ -186,8 +193,7 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  *                out: the chosen candidate's options (n_rc, Mext, s0, s_star, kbar_star, ...).
  *   xi, rc, M, P out: the chosen parameters.
  *   ms           out (may be NULL): the chosen candidate's measured time per evaluation.
- * Synchronous: returns when the trials are done. Temporary device memory: one output array
- * and the trial plans (one at a time).
+ * Synchronous: returns when the trials are done.
  */
 se_status se_autotune_timed(int periodicity, const double box[3], int kernel_mask, double Q,
                             long long n_src, const double* src, const void* strengths, int n_rhs,

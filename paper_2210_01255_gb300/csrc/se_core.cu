@@ -11,6 +11,7 @@
 #include <functional>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "se_device.cuh"
 #include "se_erfc_fit.h"
@@ -434,30 +435,30 @@ template <typename T, int NCMAX>
 __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restrict__ perm,
                                                 const int* __restrict__ base, const T* __restrict__ wts,
                                                 const T* __restrict__ F, int nt, int NC, T scale,
-                                                T* __restrict__ u) {
+                                                T* __restrict__ u, long long cst, long long xst) {
+  // F: component c at F + c cst, grid point (x, y, z) at x xst + y n2 + z
   __shared__ T s_w[8][3 * MAX_P];
-  __shared__ int s_xo[8][MAX_P];  // wrapped direction-0 plane offsets of the P taps
+  __shared__ long long s_xo[8][MAX_P];  // wrapped direction-0 plane offsets of the P taps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * 8 + warp;
   if (s >= nt) return;
   const int P = g.P;
-  const int n12 = g.n[1] * g.n[2];
   for (int i = lane; i < 3 * P; i += 32) s_w[warp][i] = wts[(size_t)s * 3 * P + i];
   const int b0 = base[3 * s], b1 = base[3 * s + 1], b2 = base[3 * s + 2];
   if (lane < P) {
     int xx = b0 + lane;
     if (g.periodic[0]) { if (xx < 0) xx += g.m[0]; else if (xx >= g.m[0]) xx -= g.m[0]; }
-    s_xo[warp][lane] = xx * n12;
+    s_xo[warp][lane] = xx * xst;
   }
   __syncwarp();
   T acc[NCMAX];
 #pragma unroll
   for (int c = 0; c < NCMAX; ++c) acc[c] = T(0);
-  const int G = (int)g.cs;  // grid points per component (< 2^31, checked at plan creation)
+  const size_t G = (size_t)cst;
   const T* w0 = s_w[warp];
   const T* w1 = s_w[warp] + P;
   const T* w2 = s_w[warp] + 2 * P;
-  const int* xo = s_xo[warp];
+  const long long* xo = s_xo[warp];
   // FP32: each lane sums one P-term row along direction 0 in plain FP32 and adds the row sum
   // to its accumulator with Kahan compensation (err[]); the lanes' totals then meet in a
   // shuffle tree. FP64 accumulates directly.
@@ -702,7 +703,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   p->bufs = new std::map<std::string, DevBuf>();
   p->fwd = new std::map<int, cufftHandle>();
   p->inv = new std::map<int, cufftHandle>();
-  p->ffree = new std::map<long long, cufftHandle>();
+  p->ffree = new std::map<std::vector<long long>, cufftHandle>();
   p->D = D;
   for (int d = 0; d < 3; ++d) p->L[d] = box[d];
   p->xi = xi;
@@ -946,17 +947,17 @@ bool use_tc_gridding(const se_plan_t* p) {
 
 template <typename T>
 se_status spread_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C,
-                        T* grid) {
+                        T* grid, long long cst, long long xst) {
   if (sizeof(T) == 4 && use_tc_gridding(p))
-    return spread_tc_launch(p, bin_start, base, (const float*)w, (const float*)sf, C, (float*)grid);
-  return grid_launch<T>(p, bin_start, base, w, sf, C, grid);
+    return spread_tc_launch(p, bin_start, base, (const float*)w, (const float*)sf, C, (float*)grid, cst, xst);
+  return grid_launch<T>(p, bin_start, base, w, sf, C, grid, cst, xst);
 }
 
 template <typename T, int NC>
 void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, const T* F, int nt, int NCr,
-                   T scale, T* u) {
+                   T scale, T* u, long long cst, long long xst) {
   ++p->launches;
-  k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u);
+  k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u, cst, xst);
 }
 
 // u += v elementwise (join of the real-space part computed on the side stream)
@@ -1132,7 +1133,14 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       p->zeroed_grid = grid;
       p->zeroed_grid_C = C;
     }
-    SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid));
+    // grid layouts: component-major [C][n0][n1][n2] (D = 0: [C][m0][n1][n2]); for D = 1
+    // direction-0-major [n0][C][n1][n2], so that the transforms along the periodic direction
+    // take every component in one call
+    const long long n12 = (long long)g.n[1] * g.n[2];
+    const bool xmaj = p->D == 1;
+    const long long gcst = xmaj ? n12 : g.cs, gxst = xmaj ? (long long)C * n12 : n12;
+    const long long ucst = xmaj ? n12 : g.cs, uxst = xmaj ? (long long)NC * n12 : n12;
+    SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid, gcst, gxst));
     SE_CUDA(cudaGetLastError());
     p->last_grid_comps = C;
     stage.mark();  // 2: spread
@@ -1178,12 +1186,12 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       // more than 2 RHS: groups of 6 components (2 RHS) per launch keep the per-lane
       // accumulators in registers (one launch over all 3 n_rhs components halved the rate)
       if (NC <= 3) {
-        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u);
+        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u, ucst, uxst);
       } else {
-        const size_t GG = (size_t)g.cs;
+        const size_t GG = (size_t)ucst;
         for (int c0 = 0; c0 < NC; c0 += 6)
           gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), scale,
-                              u + (size_t)(c0 / 3) * NT * 3);
+                              u + (size_t)(c0 / 3) * NT * 3, ucst, uxst);
       }
     }
     SE_CUDA(cudaGetLastError());
@@ -1289,13 +1297,48 @@ namespace {
 
 struct TimedCand {
   double f = 0, ms = 1e300, xi = 0, rc = 0;
+  double round_est = 0;  // FP32 rounding estimate (relative rms on the sample), 0 for FP64
   int M[3] = {0, 0, 0}, P = 0;
   se_opts o;
 };
 
+// strengths scaled by s in their linear part (f; q of the stresslet's (q, nu); the charges),
+// so that the potential scales by s: the evaluation of fs and the evaluation of f differ by
+// rounding only
+template <typename T>
+__global__ void k_scale_strengths(int kernel, const T* __restrict__ f, T* __restrict__ fs, size_t n, T s) {
+  const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int c = kernel_comps(kernel);
+  const int k = (int)(i % c);
+  const bool lin = kernel == SE_STRESSLET ? k < 3 : (kernel == SE_KERNEL_ST ? k < 6 : true);
+  fs[i] = lin ? f[i] * s : f[i];
+}
+
+// relative rms over a fixed sample of targets of u2 / s - u (u, u2 host copies, [n_rhs][n][3])
+template <typename T>
+double rounding_estimate(const std::vector<T>& u, const std::vector<T>& u2, long long n, int n_rhs, double s) {
+  const long long ns = std::min<long long>(2048, n);
+  double num = 0, den = 0;
+  unsigned long long r = 0x9E3779B97F4A7C15ull;
+  for (long long k = 0; k < ns; ++k) {
+    r = r * 6364136223846793005ull + 1442695040888963407ull;  // a fixed LCG sample of targets
+    const long long i = (long long)((r >> 17) % (unsigned long long)n);
+    for (int q = 0; q < n_rhs; ++q)
+      for (int j = 0; j < 3; ++j) {
+        const size_t o = ((size_t)q * n + i) * 3 + j;
+        const double a = (double)u[o], b = (double)u2[o] / s;
+        num += (b - a) * (b - a);
+        den += a * a;
+      }
+  }
+  return den > 0 ? std::sqrt(num / den) : 0.0;
+}
+
 se_status timed_trial(int D, const double* box, int kernel, double Q, long long n_src, const double* src,
                       const void* strengths, int n_rhs, double tol_rel, int window, const se_opts& io,
-                      double nrc, size_t mem_cap, void* u, cudaEvent_t e0, cudaEvent_t e1, TimedCand* c) {
+                      double nrc, size_t mem_cap, void* u, void* fs, void* u2, cudaEvent_t e0, cudaEvent_t e1,
+                      TimedCand* c) {
   se_opts o = io;
   o.n_rc = nrc;
   double xi = 0, rc = 0;
@@ -1309,7 +1352,7 @@ se_status timed_trial(int D, const double* box, int kernel, double Q, long long 
   const size_t G = (size_t)p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
   const size_t es = p->prec == SE_FP32 ? 4 : 8;
   const size_t C = (size_t)kernel_comps(kernel) * n_rhs, NC = 3 * (size_t)n_rhs;
-  if (G * (2 * C + NC) * es > mem_cap) {
+  if (G * (3 * C + NC) * es > mem_cap) {
     se_destroy(p);
     return SE_ERR_NOMEM;
   }
@@ -1326,8 +1369,27 @@ se_status timed_trial(int D, const double* box, int kernel, double Q, long long 
     if (s == SE_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) s = SE_ERR_CUDA;
     if (s == SE_OK) best = std::min(best, ms);
   }
+  // FP32: the rounding of this candidate, from the same evaluation with rescaled strengths
+  double est = 0;
+  if (s == SE_OK && p->prec == SE_FP32 && fs && u2) {
+    const double sc = 1.3;
+    const size_t nf = (size_t)kernel_comps(kernel) * n_rhs * n_src, nu = 3 * (size_t)n_rhs * n_src;
+    k_scale_strengths<float><<<grid1d((long long)nf, 256), 256, 0, st>>>(kernel, (const float*)strengths, (float*)fs,
+                                                                        nf, (float)sc);
+    s = se_eval(p, kernel, n_src, src, fs, n_rhs, 0, nullptr, u2);
+    if (s == SE_OK) s = se_sync(p);
+    if (s == SE_OK) {
+      std::vector<float> h1(nu), h2(nu);
+      if (cudaMemcpy(h1.data(), u, sizeof(float) * nu, cudaMemcpyDeviceToHost) != cudaSuccess ||
+          cudaMemcpy(h2.data(), u2, sizeof(float) * nu, cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = SE_ERR_CUDA;
+      else
+        est = rounding_estimate<float>(h1, h2, n_src, n_rhs, sc);
+    }
+  }
   se_destroy(p);
   if (s != SE_OK) return s;
+  c->round_est = est;
   c->ms = best;
   c->xi = xi;
   c->rc = rc;
@@ -1361,8 +1423,16 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return SE_ERR_CUDA;
   const size_t mem_cap = free_b / 2;
   const size_t es = io->prec == SE_FP32 ? 4 : 8;
-  void* u = nullptr;
+  void *u = nullptr, *fs = nullptr, *u2 = nullptr;
   if (cudaMalloc(&u, es * 3 * (size_t)n_rhs * n_src) != cudaSuccess) return SE_ERR_NOMEM;
+  if (io->prec == SE_FP32 &&
+      (cudaMalloc(&fs, es * kernel_comps(kernel_mask) * (size_t)n_rhs * n_src) != cudaSuccess ||
+       cudaMalloc(&u2, es * 3 * (size_t)n_rhs * n_src) != cudaSuccess)) {
+    cudaGetLastError();
+    if (fs) cudaFree(fs);
+    cudaFree(u);
+    return SE_ERR_NOMEM;
+  }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   se_status st = SE_OK;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) st = SE_ERR_CUDA;
@@ -1371,7 +1441,7 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   auto run = [&](double f, TimedCand* c) {
     c->f = f;
     return timed_trial(D, box, kernel_mask, Q, n_src, src, strengths, n_rhs, tol_rel, window, *io,
-                       nrc0 * f * f * f, mem_cap, u, e0, e1, c);
+                       nrc0 * f * f * f, mem_cap, u, fs, u2, e0, e1, c);
   };
   // the real-space path (per-target k_real, or the dense-block path) is a choice too: both
   // are timed at f = 1, the faster is kept for the walk over r_c and both are timed again at
@@ -1395,19 +1465,33 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
     }
     return SE_OK;
   };
-  // f = 1, then one step down; walk in the better direction while the time keeps improving
-  // (two candidates more than 10 % slower than the best, a candidate that does not fit in
-  // memory or an unsupported grid end the walk)
+  // FP32 candidates must keep their rounding within the tolerance. The rescaled-strength
+  // estimate measured about half of the FP32 - FP64 difference (the part of the rounding that
+  // does not change with the strengths' mantissas, such as the rounded kernel tables, is not
+  // in it), so twice the estimate is held to 7 tol_rel of the 10 tol_rel that the rules of
+  // Sec. 4.6 allow (their truncation error at tol_rel <= 1e-7 measures far below tol_rel). The
+  // rounding grows with xi (smaller r_c): an invalid candidate ends a walk towards smaller r_c
+  // and is passed over on a walk towards larger r_c.
+  auto ok = [&](const TimedCand& c) { return io->prec != SE_FP32 || 2.0 * c.round_est <= 7.0 * tol_rel; };
+  bool have = false;
   if (st == SE_OK) {
     TimedCand c1, c2;
     st = run_both(1.0, &c1);
-    if (st == SE_OK) io->flags = c1.o.flags;
     if (st == SE_OK) {
-      best = c1;
+      io->flags = c1.o.flags;
+      if (ok(c1)) {
+        best = c1;
+        have = true;
+      }
+      // the first step down decides the direction: down if it is valid and faster
       se_status s2 = run(step, &c2);
-      const bool down = s2 == SE_OK && c2.ms < c1.ms;
-      if (s2 == SE_OK && c2.ms < best.ms) best = c2;
       if (s2 != SE_OK && s2 != SE_ERR_NOMEM && s2 != SE_ERR_UNSUPPORTED) st = s2;
+      bool down = false;
+      if (s2 == SE_OK && ok(c2) && (!have || c2.ms < best.ms)) {
+        best = c2;
+        have = true;
+        down = true;
+      }
       double f = down ? step * step : 1.0 / step;
       int worse = 0;
       for (int k = 0; k < 14 && st == SE_OK && worse < 2; ++k, f = down ? f * step : f / step) {
@@ -1418,22 +1502,30 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
           st = s;
           break;
         }
-        if (c.ms < best.ms) {
+        if (!ok(c)) {
+          if (down) break;
+          continue;
+        }
+        if (!have || c.ms < best.ms) {
           best = c;
+          have = true;
           worse = 0;
         } else if (c.ms > 1.1 * best.ms) {
           ++worse;
         }
       }
+      if (st == SE_OK && !have) st = SE_ERR_UNSUPPORTED;  // no candidate keeps the rounding in bounds
     }
   }
   if (st == SE_OK && best.f != 1.0) {  // both real-space paths at the chosen r_c
     TimedCand c;
-    if (run_both(best.f, &c) == SE_OK && c.ms < best.ms) best = c;
+    if (run_both(best.f, &c) == SE_OK && ok(c) && c.ms < best.ms) best = c;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaFree(u);
+  if (fs) cudaFree(fs);
+  if (u2) cudaFree(u2);
   if (st != SE_OK) return st;
   *io = best.o;
   *xi_out = best.xi;

@@ -152,6 +152,7 @@ struct ColMap {
   int M0, M1;   // periodic grid sizes (D = 2: M0, M1; D = 1: M0)
   int H;        // stored extent of the halved periodic direction (M1/2+1 for D = 2, M0/2+1 for D = 1)
   int kstar;
+  int xm;       // D = 1: component slots per x wavenumber of the spectrum [H][xm][planes]
 };
 
 // periodic indices of column j of a class (FFT order); returns false for a slot that is not a
@@ -218,7 +219,7 @@ __global__ void k_aft_copy(ColMap m, int ncomp, int ncols, Ext2 fm, Ext2 fn, boo
   colmap_idx(m, j, &i0, &i1);
   size_t so;
   if (m.D == 2) so = (((size_t)c * m.M0 + i0) * m.H + i1) * plane_m + (inside ? a0 : 0);
-  else so = ((size_t)c * m.H + i0) * plane_m + (inside ? (size_t)a0 * f_m[1] + a1 : 0);
+  else so = ((size_t)i0 * m.xm + c) * plane_m + (inside ? (size_t)a0 * f_m[1] + a1 : 0);
   const size_t bo = i;
   if (to_buffer) {
     bufp[2 * bo] = inside ? spec[2 * so] : T(0);
@@ -237,6 +238,7 @@ struct FreeScale {
   double h;
   double kf0, kf1;  // 2 pi / L_0, 2 pi / L_1 (periodic)
   double inv4xi2;
+  long long cstr, jstr;  // complex elements between components and between columns of the buffer
 };
 
 // One kernel's operator on one mode (Eq. SE-scaling-disc): the regular symbol for
@@ -383,13 +385,14 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
       s = regular_scalar<T>(kernel, kk, (T)a.inv4xi2) * tp0[i0] * tf0[f0] * tf1[f1];
     }
   }
-  const size_t H = (size_t)a.ncols * plane;  // component stride in this buffer
+  const size_t H = (size_t)a.cstr;  // component stride in this buffer
+  const size_t jo = (size_t)j * a.jstr + e;
   // in place, in the order that never overwrites an input still to be read (see k_scale3p)
   for (int rr = 0; rr < n_rhs; ++rr) {
     const int r = cin >= 3 ? rr : n_rhs - 1 - rr;
     T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
-      const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
+      const size_t o = (((size_t)(cin * r + c)) * H + jo) * 2;
       re[c] = spec[o];
       im[c] = spec[o + 1];
     }
@@ -408,7 +411,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
       }
     }
     for (int q = 0; q < 3; ++q) {
-      const size_t o = (((size_t)(3 * r + q)) * H + idx) * 2;
+      const size_t o = (((size_t)(3 * r + q)) * H + jo) * 2;
       spec[o] = ore[q];
       spec[o + 1] = oim[q];
     }
@@ -619,7 +622,13 @@ namespace {
 // cached cuFFT plans for the free-direction transforms, keyed by a small integer tag
 se_status free_fft(se_plan_t* p, int tag, int batch, int rank, const int* n, int* inembed, int istride,
                    int idist, int* onembed, int ostride, int odist, cufftType type, cufftHandle* out) {
-  const long long key = ((long long)tag << 32) | (unsigned)batch;
+  // the key holds every argument: plans of the same tag and batch can differ in their strides
+  std::vector<long long> key = {tag, batch, rank, istride, idist, ostride, odist, (long long)type};
+  for (int d = 0; d < rank; ++d) {
+    key.push_back(n[d]);
+    key.push_back(inembed ? inembed[d] : -1);
+    key.push_back(onembed ? onembed[d] : -1);
+  }
   auto it = p->ffree->find(key);
   if (it != p->ffree->end()) {
     SE_CUFFT(cufftSetStream(it->second, p->stream));  // the stream the caller issues on now
@@ -727,7 +736,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     SE_TRY(free_fft(p, 11, Mz, 2, n2, on2, Mz, 1, in2, Mz, 1, FT<T>::C2R, &h2i));
     for (int c = 0; c < C; ++c) SE_CUFFT(FT<T>::r2c(h2f, grid + (size_t)c * G, (T*)spec + 2 * (size_t)c * S));
     // class buffers for k^P = 0 and K_*
-    ColMap cm{2, 0, M0, M1, H1, p->kbar_star};
+    ColMap cm{2, 0, M0, M1, H1, p->kbar_star, 0};
     const int ncolS = (2 * p->kbar_star + 1) * (p->kbar_star + 1) - 1;
     const int n0 = p->ncls[0][2], nS = p->ncls[1][2];
     void *b0, *bS;
@@ -770,12 +779,16 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     fs.ncols = M0 * H1;
     fs.fn[0] = Mz;
     fs.fn[1] = 1;
+    fs.cstr = (long long)M0 * H1 * Mz;
+    fs.jstr = Mz;
     k_scale_free<T><<<grid1d((long long)M0 * H1 * Mz, 256), 256, 0, st>>>(
         fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[2][2].p, nullptr, nullptr, nullptr, (T*)spec);
     fs.m.mode = 0;
     fs.cls = 0;
     fs.ncols = 1;
     fs.fn[0] = n0;
+    fs.cstr = n0;
+    fs.jstr = n0;
     k_scale_free<T><<<grid1d(n0, 256), 256, 0, st>>>(
         fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[0][2].p, nullptr, (const T*)p->mod0[kidx].p,
         kernel == SE_KERNEL_ST ? (const T*)p->mod0[1].p : nullptr, (T*)b0);
@@ -784,6 +797,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
       fs.cls = 1;
       fs.ncols = ncolS;
       fs.fn[0] = nS;
+      fs.cstr = (long long)ncolS * nS;
+      fs.jstr = nS;
       k_scale_free<T><<<grid1d((long long)ncolS * nS, 256), 256, 0, st>>>(
           fs, kernel, n_rhs, tp0, tp1, (const T*)p->ftab[1][2].p, nullptr, nullptr, nullptr, (T*)bS);
     }
@@ -804,20 +819,23 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     SE_CUDA(cudaGetLastError());
     return SE_OK;
   }
-  // D = 1: 1-D R2C along direction 0, planes along (1, 2) per class
+  // D = 1: 1-D R2C along direction 0, planes along (1, 2) per class. The grid is direction-0-
+  // major, [M0][C][My][Mz], and the spectrum [M0/2+1][CS][My][Mz] (CS component slots per x
+  // wavenumber, the scaling writes its NC outputs over the C inputs): the transforms along
+  // direction 0 take every component in one call each way, and the planes of every x
+  // wavenumber and component are contiguous for the 2-D transforms.
   const int My = g.m[1], Mz = g.m[2];
   const int H0 = M0 / 2 + 1;
   const size_t PL = (size_t)My * Mz;
-  const size_t G = (size_t)M0 * PL;
   const size_t S = (size_t)H0 * PL;
   void* spec;
   SE_TRY(buf(p, "spec", sizeof(T) * 2 * CS * S, &spec));
   int n1[1] = {M0}, in1[1] = {M0}, on1[1] = {H0};
   cufftHandle h1f, h1i;
-  SE_TRY(free_fft(p, 20, (int)PL, 1, n1, in1, (int)PL, 1, on1, (int)PL, 1, FT<T>::R2C, &h1f));
-  SE_TRY(free_fft(p, 21, (int)PL, 1, n1, on1, (int)PL, 1, in1, (int)PL, 1, FT<T>::C2R, &h1i));
-  for (int c = 0; c < C; ++c) SE_CUFFT(FT<T>::r2c(h1f, grid + (size_t)c * G, (T*)spec + 2 * (size_t)c * S));
-  ColMap cm{1, 0, M0, 0, H0, std::min(p->kbar_star, H0 - 2)};
+  SE_TRY(free_fft(p, 20, C * (int)PL, 1, n1, in1, C * (int)PL, 1, on1, CS * (int)PL, 1, FT<T>::R2C, &h1f));
+  SE_TRY(free_fft(p, 21, NC * (int)PL, 1, n1, on1, CS * (int)PL, 1, in1, NC * (int)PL, 1, FT<T>::C2R, &h1i));
+  SE_CUFFT(FT<T>::r2c(h1f, grid, (T*)spec));
+  ColMap cm{1, 0, M0, 0, H0, std::min(p->kbar_star, H0 - 2), CS};
   const int kst = std::max(0, cm.kstar);
   const int n0y = p->ncls[0][1], n0z = p->ncls[0][2], nSy = p->ncls[1][1], nSz = p->ncls[1][2];
   void *b0, *bS;
@@ -833,8 +851,10 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   }
   int np[2] = {My, Mz}, np0[2] = {n0y, n0z}, npS[2] = {nSy, nSz};
   cufftHandle hp, hpi, hp0, hp0i, hpS, hpSi;
-  SE_TRY(free_fft(p, 22, C * H0, 2, np, nullptr, 1, (int)PL, nullptr, 1, (int)PL, FT<T>::C2C, &hp));
-  SE_TRY(free_fft(p, 23, NC * H0, 2, np, nullptr, 1, (int)PL, nullptr, 1, (int)PL, FT<T>::C2C, &hpi));
+  // every (x wavenumber, component slot) plane: the K_inf class transformed in place (the other
+  // classes are taken from their own upsampled buffers; unused slots are transformed harmlessly)
+  SE_TRY(free_fft(p, 22, CS * H0, 2, np, nullptr, 1, (int)PL, nullptr, 1, (int)PL, FT<T>::C2C, &hp));
+  hpi = hp;
   SE_TRY(free_fft(p, 24, C, 2, np0, nullptr, 1, n0y * n0z, nullptr, 1, n0y * n0z, FT<T>::C2C, &hp0));
   SE_TRY(free_fft(p, 25, NC, 2, np0, nullptr, 1, n0y * n0z, nullptr, 1, n0y * n0z, FT<T>::C2C, &hp0i));
   SE_CUFFT(FT<T>::c2c(hp, (T*)spec, (T*)spec, CUFFT_FORWARD));
@@ -857,6 +877,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   fs.ncols = H0;
   fs.fn[0] = My;
   fs.fn[1] = Mz;
+  fs.cstr = (long long)PL;
+  fs.jstr = (long long)CS * PL;
   k_scale_free<T><<<grid1d((long long)H0 * PL, 256), 256, 0, st>>>(
       fs, kernel, n_rhs, tp0, nullptr, (const T*)p->ftab[2][1].p, (const T*)p->ftab[2][2].p, nullptr, nullptr,
       (T*)spec);
@@ -865,6 +887,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   fs.ncols = 1;
   fs.fn[0] = n0y;
   fs.fn[1] = n0z;
+  fs.cstr = (long long)n0y * n0z;
+  fs.jstr = (long long)n0y * n0z;
   const T* modH = (const T*)(harmonic_family(kernel) ? p->mod0[2].p : p->mod0[0].p);
   const T* modB = (const T*)(harmonic_family(kernel) ? nullptr : p->mod0[1].p);
   k_scale_free<T><<<grid1d((long long)n0y * n0z, 256), 256, 0, st>>>(fs, kernel, n_rhs, tp0, nullptr, nullptr,
@@ -875,6 +899,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     fs.ncols = kst;
     fs.fn[0] = nSy;
     fs.fn[1] = nSz;
+    fs.cstr = (long long)kst * nSy * nSz;
+    fs.jstr = (long long)nSy * nSz;
     k_scale_free<T><<<grid1d((long long)kst * nSy * nSz, 256), 256, 0, st>>>(
         fs, kernel, n_rhs, tp0, nullptr, (const T*)p->ftab[1][1].p, (const T*)p->ftab[1][2].p, nullptr, nullptr,
         (T*)bS);
@@ -892,7 +918,7 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     k_aft_copy<T><<<grid1d((long long)NC * kst * nSy * nSz, 256), 256, 0, st>>>(cm, NC, kst, em, eS, false,
                                                                                 (T*)spec, (T*)bS);
   }
-  for (int c = 0; c < NC; ++c) SE_CUFFT(FT<T>::c2r(h1i, (T*)spec + 2 * (size_t)c * S, ugrid + (size_t)c * G));
+  SE_CUFFT(FT<T>::c2r(h1i, (T*)spec, ugrid));
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }

@@ -65,6 +65,7 @@ struct GridArgs {
   const int* bin_start;     // [nbins + 1]
   const int* base;          // [N][3] first tap (cell - P/2 + 1), wrapped cell
   int Ctot, c0, C;          // components c0 .. c0 + C - 1 of Ctot
+  long long cst, xst;       // grid: component c at c cst, point (x, y, z) at x xst + y n2 + z
   int2* queue;              // overflow items: (tile, slab)
   int* qcount;
   int qcap;
@@ -333,7 +334,6 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
     }
     if (npend > 0) chunk(npend);
     // ---- epilogue: store (the tile's only or first item) or add (queued items)
-    const size_t G = (size_t)g.cs;
     const int x = o0 + tx;
     const bool atomic = QUEUE;
     if (x < g.m[0]) {
@@ -345,11 +345,11 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
         for (int z = 0; z < RZ; ++z) {
           const int zz = o2 + gz * RZ + z;
           if (zz >= g.m[2]) continue;
-          const size_t off = ((size_t)x * g.n[1] + y) * g.n[2] + zz;
+          const size_t off = (size_t)x * a.xst + (size_t)y * g.n[2] + zz;
 #pragma unroll
           for (int c = 0; c < CG; ++c) {
             if (c < a.C) {
-              T* dst = grid + (size_t)(a.c0 + c) * G + off;
+              T* dst = grid + (size_t)(a.c0 + c) * a.cst + off;
               if (atomic) atomicAdd(dst, acc[i][z][c]);
               else *dst = acc[i][z][c];
             }
@@ -378,7 +378,8 @@ void launch_grid(cudaStream_t st, GridArgs a, const T* w, const T* sf, T* grid, 
 // Gridding of the C spread components of the points sorted by 4^3 bins (bin_start), in groups
 // of up to 12 (FP32) components per launch pair.
 template <typename T>
-se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid) {
+se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid,
+                      long long cst, long long xst) {
   const GridGeom& g = p->geom;
   GridArgs a;
   a.g = g;
@@ -386,6 +387,8 @@ se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const
   a.bin_start = bin_start;
   a.base = base;
   a.Ctot = C;
+  a.cst = cst;
+  a.xst = xst;
   // overflow queue: at most one item per GK_ITEM candidates beyond each tile's first
   void* q;
   const size_t qcap = 1 << 20;
@@ -409,8 +412,9 @@ se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const
   return SE_OK;
 }
 
-template se_status grid_launch<float>(se_plan_t*, const int*, const int*, const float*, const float*, int, float*);
+template se_status grid_launch<float>(se_plan_t*, const int*, const int*, const float*, const float*, int, float*,
+                                      long long, long long);
 template se_status grid_launch<double>(se_plan_t*, const int*, const int*, const double*, const double*, int,
-                                       double*);
+                                       double*, long long, long long);
 
 }  // namespace se

@@ -107,8 +107,8 @@ struct se_plan_t {
   // cuFFT plans keyed by batch count (forward R2C and inverse C2R)
   std::map<int, cufftHandle>* fwd = nullptr;
   std::map<int, cufftHandle>* inv = nullptr;
-  // cuFFT plans of the free-direction transforms, keyed by (tag << 32) | batch
-  std::map<long long, cufftHandle>* ffree = nullptr;
+  // cuFFT plans of the free-direction transforms, keyed by every parameter of the plan
+  std::map<std::vector<long long>, cufftHandle>* ffree = nullptr;
 
   // pinned host staging for se_eval_host
   void* pin = nullptr;
@@ -162,10 +162,11 @@ template <typename T>
 se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const ScaleTables<T>& t);
 // gridding on the CUDA cores (se_grid.cu): points sorted by 4^3 bins (bin_start)
 template <typename T>
-se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid);
+se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid,
+                      long long cst, long long xst);
 // FP32 gridding on the tensor cores (se_spread_tc.cu)
 se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
-                           int C, float* grid);
+                           int C, float* grid, long long cst, long long xst);
 se_status free_plan_setup(se_plan_t* p);
 template <typename T>
 se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);

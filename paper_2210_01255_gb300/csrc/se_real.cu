@@ -32,7 +32,7 @@ namespace se {
 template <typename T>
 __device__ inline T dev_erfc_g(T x, T g);
 template <> __device__ __forceinline__ float dev_erfc_g<float>(float x, float g) {
-  const float t = __frcp_rn(fmaf(float(SE_ERFC_FIT_A), x, 1.0f));
+  const float t = __fdividef(1.0f, fmaf(float(SE_ERFC_FIT_A), x, 1.0f));  // fast reciprocal, ~1 ulp
   float r = float(SE_ERFC_FIT_C10);
   r = fmaf(r, t, float(SE_ERFC_FIT_C9));
   r = fmaf(r, t, float(SE_ERFC_FIT_C8));
@@ -47,6 +47,11 @@ template <> __device__ __forceinline__ float dev_erfc_g<float>(float x, float g)
   return g * (t * r);
 }
 template <> __device__ __forceinline__ double dev_erfc_g<double>(double x, double) { return erfc(x); }
+
+// exp(a) for the Gaussian factor exp(-xi^2 r^2), a in [-xi^2 r_c^2, 0]: FP32 takes the hardware
+// exponential (a few ulp on this range, far below the FP32 path's tolerance), FP64 the library
+__device__ __forceinline__ float gauss(float a) { return __expf(a); }
+__device__ __forceinline__ double gauss(double a) { return exp(a); }
 
 // One pair (target, source image): accumulate G^R(r) . f into acc, or the self term when
 // the separation is exactly zero (the omitted n = m, p = 0 term of the star sum).
@@ -67,7 +72,7 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   const T inv = rsqrt(rr2);
   const T rn = rr2 * inv;
   const T inv2 = inv * inv;
-  const T e = exp(-xi2 * rr2);
+  const T e = gauss(-xi2 * rr2);
   const T ec = dev_erfc_g(xi * rn, e) * inv;
   if (KERNEL == SE_STOKESLET) {
     // Eq. (stokeslet-real): (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e/sqrt pi

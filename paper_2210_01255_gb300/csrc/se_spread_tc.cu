@@ -132,6 +132,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
                                                              const float* __restrict__ wts,
                                                              const float* __restrict__ sf, int Ctot, int c0, int C,
                                                              int nslab, float* __restrict__ grid,
+                                                             long long cst, long long xst,
                                                              int* __restrict__ status, long long drain_limit) {
   static_assert(Z * CG == TC_N, "accumulator width");
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
@@ -408,13 +409,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
     const int m = 32 * q + lane;
     const int x = o0 + (m >> 3), y = o1 + (m & 7);
     if (x < g.m[0] && y < g.m[1]) {
-      const size_t G = (size_t)g.cs;
-      const size_t row = ((size_t)x * g.n[1] + y) * g.n[2];
+      const size_t row = (size_t)x * xst + (size_t)y * g.n[2];
 #pragma unroll
       for (int i = 0; i < 24; ++i) {
         const int n = 24 * half + i, z = o2 + n / CG, c = n % CG;
         if (z < g.m[2] && c < C) {
-          float* dst = grid + (size_t)(c0 + c) * G + row + z;
+          float* dst = grid + (size_t)(c0 + c) * cst + row + z;
           if (nslab == 1) *dst = acc[i];
           else atomicAdd(dst, acc[i]);
         }
@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_spread_tc(GridGeom g, const i
 
 template <int Z, int CG>
 se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
-                       int Ctot, int c0, int C, float* grid) {
+                       int Ctot, int c0, int C, float* grid, long long cst, long long xst) {
   const GridGeom& g = p->geom;
   const size_t smem = sizeof(TcSmem<Z, CG>);
   // per function and device; set at every launch (a host-side call, cheap, thread-safe)
@@ -447,17 +447,13 @@ se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, con
   // two CTAs fit an SM; split the source bins of a tile over nslab CTAs when the tiles
   // alone would leave SMs idle (partial tiles are then added atomically into a zeroed grid)
   const int nslab = (int)std::min<long long>(8, std::max<long long>(1, (2LL * 152 + tiles - 1) / tiles));
-  if (nslab > 1) {
-    const size_t G = (size_t)g.cs;
-    for (int c = 0; c < C; ++c) SE_CUDA(cudaMemsetAsync(grid + (size_t)(c0 + c) * G, 0, sizeof(float) * G, p->stream));
-  }
   dim3 grd((unsigned)(t0 * nslab), (unsigned)t1, (unsigned)t2);
   ++p->launches;
   // SE_FLAG_TEST_TIMEOUT (a testing aid): the waits for finished chunks give up at once,
   // which exercises the timeout path (status, drain of the MMAs in flight, release)
   const long long drain_limit = (p->flags & SE_FLAG_TEST_TIMEOUT) ? 0 : TC_WAIT_LIMIT;
   k_spread_tc<Z, CG><<<grd, TC_THREADS, smem, p->stream>>>(g, tile_start, base, w, sf, Ctot, c0, C, nslab, grid,
-                                                           p->d_status, drain_limit);
+                                                           cst, xst, p->d_status, drain_limit);
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }
@@ -467,11 +463,13 @@ se_status launch_group(se_plan_t* p, const int* tile_start, const int* base, con
 // FP32 gridding of C components on the tensor cores: components in groups of 6 (8 grid
 // points along direction 2 per tile) or a last group of up to 3 (16 points per tile).
 se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
-                           int C, float* grid) {
+                           int C, float* grid, long long cst, long long xst) {
+  // tiles split over several CTAs add their partial tiles atomically: zero the whole grid first
+  SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(float) * (size_t)C * p->geom.cs, p->stream));
   for (int c0 = 0; c0 < C; c0 += 6) {
     const int Cc = std::min(6, C - c0);
-    if (Cc <= 3) SE_TRY((launch_group<16, 3>(p, tile_start, base, w, sf, C, c0, Cc, grid)));
-    else SE_TRY((launch_group<8, 6>(p, tile_start, base, w, sf, C, c0, Cc, grid)));
+    if (Cc <= 3) SE_TRY((launch_group<16, 3>(p, tile_start, base, w, sf, C, c0, Cc, grid, cst, xst)));
+    else SE_TRY((launch_group<8, 6>(p, tile_start, base, w, sf, C, c0, Cc, grid, cst, xst)));
   }
   return SE_OK;
 }

@@ -102,9 +102,12 @@ CONFIGS = {
     # free space, half the points uniform and half in a Gaussian cluster (sigma 0.05) at the
     # centre; stokeslet and stresslet strengths (f, q, nu) evaluated together. The uniform-case
     # neighbour count puts ~1.4e11 pairs inside r_c here, so the split is chosen by timing.
+    # (grid extents rounded to FFT-friendly sizes; the timed selection also bounds the FP32
+    # rounding of each candidate, which grows with xi for the free-space stresslet)
     "0p_stokeslet_stresslet_n1000000": dict(D=0, box=(1.0, 1.0, 1.0), N=1000000, points="clustered",
                                             kernels=("stokeslet+stresslet",), tol=1e-6, prec="fp32",
-                                            window="pkb", seed=4, n_rhs=1, autotune="timed"),
+                                            window="pkb", seed=4, n_rhs=1, autotune="timed",
+                                            fft_sizes=True),
     # the harmonic field (electrostatics: the field of N(0,1) point charges), triply periodic
     "3p_harmonic_field_n100000": dict(D=3, box=(1.0, 1.0, 1.0), N=100000, kernels=("harmonic_field",),
                                       tol=1e-6, prec="fp32", window="pkb", seed=6, n_rhs=1),

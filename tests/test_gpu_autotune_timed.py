@@ -34,19 +34,24 @@ def timed_plan(D, box, kernel, x, f, tol, prec):
 
 def test_clustered_free_space_fused():
     """0P stokeslet + stresslet, N = 2e5 (half in a Gaussian cluster of width 0.05), FP32 at
-    1e-6: the timed choice has a smaller r_c than the uniform-case rule and meets the
-    tolerance at 64 sampled targets."""
+    1e-6 (1e-7 requested): the timed choice meets the tolerance at 256 sampled targets, and its
+    FP32 rounding alone (against FP64 with the same parameters, on the same targets) stays
+    within that tolerance too (the selection's rounding check aims at 7e-7)."""
     box = (1.0, 1.0, 1.0)
     N = 200000
     x = W.clustered_points(N, seed=21)
     f = W.strengths(ST, N, seed=22)
     t, u = timed_plan(0, box, ST, x, f, 1e-7, "fp32")
-    rule = se.se_autotune(0, box, se.KERNELS[ST], W.source_quantity(ST, f), N, 1e-7)
-    assert t["rc"] < rule["rc"] and t["ms"] > 0
-    idx = np.random.default_rng(23).choice(N, 64, replace=False)
+    assert t["ms"] > 0
+    idx = np.random.default_rng(23).choice(N, 256, replace=False)
     ref = (E.potential(0, box, "stokeslet", x, f[:, :3], targets=x[idx])
            + E.potential(0, box, "stresslet", x, f[:, 3:], targets=x[idx]))
-    assert E.rms_rel(u[idx], ref) < 1e-5
+    assert E.rms_rel(u[idx], ref) < 1e-6
+    o = t["opts"]
+    p64 = se.Plan(0, box, t["xi"], t["rc"], t["M"], t["P"], "pkb", "fp64", opts=o)
+    u64 = p64.evaluate(ST, torch.tensor(x, device="cuda"), torch.tensor(f, device="cuda"))
+    p64.sync()
+    assert E.rms_rel(u[idx], u64.cpu().numpy()[idx]) < 1e-6
 
 
 @pytest.mark.parametrize("prec,tol,bar", [("fp32", 1e-7, 1e-5), ("fp64", 1e-11, 1e-10)])

@@ -125,16 +125,16 @@ def test_tensor_gridding_clustered_full_size():
     value, many 32-point stages per tile) on a 56^3 grid: both FP32 grids against the FP64
     grid (itself pinned to the oracle at 1e-12 by the FP64 gridding test). An FP32 sum of
     n ~ 1e4 terms is good to ~sqrt(n) 2^-24 ~ 6e-6 relative, so both grids must be within
-    2e-5 of max, and the tensor-core grid no worse than 3x the CUDA-core one (an accumulator
-    rounding bias would grow like n 2^-24 and fail this)."""
+    6e-6 of max (an accumulator rounding bias would grow like n 2^-24 ~ 6e-4 and fail this;
+    the CUDA-core gridding folds 32-point chunks with compensated sums and is well inside)."""
     x = W.clustered_points(20000, seed=5)
     f = W.strengths("stresslet", 20000, seed=6)
     args = (3, (1.0, 1.0, 1.0), "stresslet", x, f, 19.7, (56, 56, 56), 12, "pkb")
     ref = grid_of(*args, 0, prec="fp64")
     e_tc = maxrel(grid_of(*args, se.FLAG_TC_GRIDDING), ref)
     e_cc = maxrel(grid_of(*args, 0), ref)
-    assert e_cc < 2e-5, e_cc
-    assert e_tc < 2e-5 and e_tc < 3 * e_cc, (e_tc, e_cc)
+    assert e_cc < 6e-6, e_cc
+    assert e_tc < 6e-6, (e_tc, e_cc)
 
 
 def test_bounded_wait_timeout_is_reported_and_context_stays_usable():
