@@ -39,6 +39,8 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = "0p_stokeslet_stresslet_n1000000"   # default (--workload selects another configuration)
 P_MARGIN = None   # --p-margin: overrides the workload's window margin of the selection
+NRC_SCALE = None  # --nrc-scale: the tolerance rules at r_c scaled from the uniform-case rule (no timing)
+REAL_PATH = "auto"  # --real-path: the real-space path (auto: the selection's choice)
 METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
 METRIC = METRIC_FMT % "0P stokeslet+stresslet, N=1e6 clustered"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
@@ -133,6 +135,11 @@ def replica_value(targets_per_step, world, steps, ms_max):
     return targets_per_step * world * steps / (ms_max / 1e3)
 
 
+def W_CONFIGS():
+    from paper_2210_01255_gb300 import workloads as W
+    return W.CONFIGS
+
+
 def make_items(cfg):
     """The evaluations of one step: name, kernel, positions (N, 3) and strengths (n_rhs, N, c)
     in the workload's precision."""
@@ -180,7 +187,16 @@ def tuned(cfg, item, prec, stream, flags=0):
             o.P_margin = P_MARGIN
         if cfg.get("fft_sizes"):
             o.flags |= se.FLAG_FFT_SIZES
-        if cfg.get("autotune") == "timed":
+        if NRC_SCALE is not None:
+            # fixed selection: the uniform-case rule's neighbour count scaled by NRC_SCALE^3
+            # (r_c by NRC_SCALE), everything else from the tolerance rules
+            o0 = se.se_opts()
+            ctypes.memmove(ctypes.byref(o0), ctypes.byref(o), ctypes.sizeof(o))
+            o0.n_rc = 0.0
+            t0 = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o0)
+            o.n_rc = 4.0 / 3.0 * math.pi * t0["rc"] ** 3 * item["N"] / float(np.prod(cfg["box"])) * NRC_SCALE ** 3
+            t = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
+        elif cfg.get("autotune") == "timed":
             o.flags |= flags
             t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
                                      cfg["tol"] / 10.0, cfg["window"], opts=o, prec=prec, stream=stream)
@@ -202,6 +218,10 @@ def make_plan(cfg, item, prec, stream, flags=0):
     t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
     # the gridding choice of the command line; the real-space path the selection chose
     o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES))
+    if REAL_PATH == "blocks":
+        o.flags |= se_.FLAG_REAL_BLOCKS
+    elif REAL_PATH == "target":
+        o.flags &= ~se_.FLAG_REAL_BLOCKS
     return se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], prec, opts=o,
                    stream=stream), dict(xi=t["xi"], rc=t["rc"], M=t["M"], P=t["P"])
 
@@ -219,7 +239,7 @@ def real_pairs(cfg, item, rc):
     return N * float(np.mean(cnt - 1))
 
 
-KERNEL_SOURCES = {"real": "se_core.cu", "spread": "se_core.cu", "gather": "se_core.cu"}
+KERNEL_SOURCES = {"real": "se_real.cu", "spread": "se_grid.cu", "gather": "se_core.cu"}
 
 
 def param_key(p):
@@ -242,7 +262,10 @@ def kernel_traffic(workload, stage, params, gridding="cuda"):
     if stage == "spread" and gridding == "tc":
         return None  # the summaries cover the CUDA-core gridding kernel only
     src = os.path.join(ROOT, "paper_2210_01255_gb300", "csrc", KERNEL_SOURCES[stage])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
     vals = []
     for name, p in params.items():
         for f in lines:
@@ -412,7 +435,7 @@ def run_experiment(args):
 
 
 def main():
-    global WORKLOAD, METRIC, P_MARGIN
+    global WORKLOAD, METRIC, P_MARGIN, NRC_SCALE, REAL_PATH
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -426,6 +449,13 @@ def main():
                     help="FP32 gridding on the CUDA cores (default) or the tensor cores (tcgen05)")
     ap.add_argument("--p-margin", type=int, default=None,
                     help="window points added by the error-pollution rule (default: the workload's)")
+    ap.add_argument("--nrc-scale", type=float, default=None,
+                    help="fixed selection instead of the workload's: the tolerance rules with r_c scaled "
+                         "by this factor from the uniform-case rule (for profiling a given choice)")
+    ap.add_argument("--real-path", choices=["auto", "blocks", "target"], default="auto",
+                    help="real-space path: the selection's choice, the dense-block path or per target")
+    ap.add_argument("--n-points", type=int, default=None,
+                    help="override N of a single-system workload (a smaller case of the same kind)")
     ap.add_argument("--experiment", choices=["complexity", "time_vs_error"], default=None,
                     help="the timing experiments of Sec. 5.2 instead of the benchmark line")
     ap.add_argument("--exp-d", default="3,2,1,0")
@@ -439,6 +469,10 @@ def main():
     WORKLOAD = args.workload
     METRIC = METRIC_FMT % METRIC_NAMES[WORKLOAD]
     P_MARGIN = args.p_margin
+    NRC_SCALE = args.nrc_scale
+    REAL_PATH = args.real_path
+    if args.n_points is not None and "N" in W_CONFIGS()[WORKLOAD]:
+        W_CONFIGS()[WORKLOAD]["N"] = args.n_points
     if args.impl == "reference":
         return run_reference(args)
 
@@ -498,14 +532,31 @@ def main():
         step()
         ev[s][1].record(stream)
         for it in items:
-            info = it["plan"].info()       # waits for this step's stage events
-            stage_ms += np.maximum(np.array(list(info.times_ms)), 0.0)
+            info = it["plan"].info()       # waits for this step's events
             launches += info.launches
             it["scale_modes"] = info.scale_modes
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     targets_per_step = sum(it["N"] * it["R"] for it in items)  # (target, RHS) evaluations per step
+    # per-stage times without overlap: in the eager and batched forms the real-space sum runs on
+    # a side stream, concurrently with (and slowing) the Fourier-space kernels; here each
+    # evaluation runs as its real-space part, then its Fourier-space part and corrections
+    n_stage = max(2, min(args.steps, 5))
+    for it in items:
+        it["uparts"] = torch.empty_like(it["udev"])
+    for s_ in range(n_stage):
+        for it in items:
+            flush.zero_()
+            it["plan"].evaluate(it["kernel"], it["xdev"], it["fdev"], out=it["uparts"], parts=se.PART_REAL)
+            stage_ms[6] += max(it["plan"].info().times_ms[6], 0.0)
+            flush.zero_()
+            it["plan"].evaluate(it["kernel"], it["xdev"], it["fdev"], out=it["uparts"],
+                                parts=se.PART_FOURIER | se.PART_CORR)
+            t_ = np.maximum(np.array(list(it["plan"].info().times_ms)), 0.0)
+            t_[6] = 0.0
+            stage_ms += t_
+    stage_ms /= n_stage / args.steps      # per_stage below divides by args.steps
     # FP32 batched: all evaluations of a step captured into one CUDA graph (se_batch_*) on a
     # stream of their own and replayed; L2 flushed between replays, timed with events
     gstream = torch.cuda.Stream(device=dev)

@@ -198,21 +198,23 @@ __global__ void k_aft_copy(ColMap m, int ncomp, int ncols, Ext2 fm, Ext2 fn, boo
   const int* f_m = fm.v;
   const int* f_n = fn.v;
   const int nf = m.D == 2 ? 1 : 2;
-  const size_t plane_n = nf == 1 ? (size_t)f_n[0] : (size_t)f_n[0] * f_n[1];
+  // 32-bit index arithmetic (the launcher checks ncomp ncols plane_n < 2^31)
+  const unsigned plane_n = nf == 1 ? (unsigned)f_n[0] : (unsigned)f_n[0] * f_n[1];
   const size_t plane_m = nf == 1 ? (size_t)f_m[0] : (size_t)f_m[0] * f_m[1];
-  const size_t N = (size_t)ncomp * ncols * plane_n;
-  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned N = (unsigned)ncomp * ncols * plane_n;
+  const unsigned i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  const size_t e = i % plane_n;
-  const int j = (int)((i / plane_n) % ncols);
-  const int c = (int)(i / (plane_n * ncols));
+  const unsigned q = i / plane_n;
+  const unsigned e = i - q * plane_n;
+  const int j = (int)(q % (unsigned)ncols);
+  const int c = (int)(q / (unsigned)ncols);
   int a0, a1;
   if (nf == 1) {
     a0 = (int)e;
     a1 = 0;
   } else {
-    a0 = (int)(e / f_n[1]);
-    a1 = (int)(e % f_n[1]);
+    a0 = (int)(e / (unsigned)f_n[1]);
+    a1 = (int)(e - (unsigned)a0 * f_n[1]);
   }
   const bool inside = nf == 1 ? a0 < f_m[0] : (a0 < f_m[0] && a1 < f_m[1]);
   int i0, i1;
@@ -220,7 +222,7 @@ __global__ void k_aft_copy(ColMap m, int ncomp, int ncols, Ext2 fm, Ext2 fn, boo
   size_t so;
   if (m.D == 2) so = (((size_t)c * m.M0 + i0) * m.H + i1) * plane_m + (inside ? a0 : 0);
   else so = ((size_t)i0 * m.xm + c) * plane_m + (inside ? (size_t)a0 * f_m[1] + a1 : 0);
-  const size_t bo = i;
+  const size_t bo = (size_t)i;
   if (to_buffer) {
     bufp[2 * bo] = inside ? spec[2 * so] : T(0);
     bufp[2 * bo + 1] = inside ? spec[2 * so + 1] : T(0);
@@ -739,6 +741,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
     ColMap cm{2, 0, M0, M1, H1, p->kbar_star, 0};
     const int ncolS = (2 * p->kbar_star + 1) * (p->kbar_star + 1) - 1;
     const int n0 = p->ncls[0][2], nS = p->ncls[1][2];
+    if ((double)CS * std::max(ncolS, 1) * nS >= 2147483647.0 || (double)CS * n0 >= 2147483647.0)
+      return SE_ERR_UNSUPPORTED;  // class buffers are indexed with 32-bit offsets
     void *b0, *bS;
     SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * CS * (size_t)n0, &b0));
     SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * CS * (size_t)std::max(ncolS, 1) * nS, &bS));
@@ -838,6 +842,8 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   ColMap cm{1, 0, M0, 0, H0, std::min(p->kbar_star, H0 - 2), CS};
   const int kst = std::max(0, cm.kstar);
   const int n0y = p->ncls[0][1], n0z = p->ncls[0][2], nSy = p->ncls[1][1], nSz = p->ncls[1][2];
+  if ((double)CS * std::max(kst, 1) * nSy * nSz >= 2147483647.0 || (double)CS * n0y * n0z >= 2147483647.0)
+    return SE_ERR_UNSUPPORTED;  // class buffers are indexed with 32-bit offsets
   void *b0, *bS;
   SE_TRY(buf(p, "aft.b0", sizeof(T) * 2 * CS * (size_t)n0y * n0z, &b0));
   SE_TRY(buf(p, "aft.bS", sizeof(T) * 2 * CS * (size_t)std::max(kst, 1) * nSy * nSz, &bS));

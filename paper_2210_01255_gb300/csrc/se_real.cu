@@ -156,6 +156,82 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   }
 }
 
+// The pair terms of real_pair without branches, for a pair that may or may not count: the
+// radial coefficients are formed from a safe r^2 and then kept (a pair inside r_c at r > 0),
+// replaced by the self term (r = 0, the omitted star-sum term: the stokeslet's -4 xi/sqrt(pi)
+// f, nothing for the other kernels) or zeroed (outside r_c). Same arithmetic as real_pair for
+// a pair that counts; with no branch, the terms of two candidates interleave (k_real_blk).
+template <typename T, int KERNEL, int RMAX>
+__device__ __forceinline__ void real_pair_m(T r0, T r1, T r2, T rr2, bool inside, T xi, T xi2, T c2pi,
+                                            const T* __restrict__ f, int n_rhs, T* acc) {
+  const bool reg = inside && rr2 > T(0);
+  const bool self = inside && rr2 == T(0);
+  const T q2 = reg ? rr2 : T(1);
+  const T inv = rsqrt(q2);
+  const T rn = q2 * inv;
+  const T inv2 = inv * inv;
+  const T e = gauss(-xi2 * q2);
+  const T ec = dev_erfc_g(xi * rn, e) * inv;
+  if (KERNEL == SE_STOKESLET || KERNEL == (SE_STOKESLET | SE_STRESSLET)) {
+    constexpr int STRIDE = KERNEL == SE_STOKESLET ? 3 : 9;
+    const T c1 = ec + c2pi * e;
+    T c0 = c1 - T(2) * c2pi * e;
+    c0 = reg ? c0 : (self ? -T(2) * c2pi : T(0));
+    const T c1i = reg ? c1 * inv2 : T(0);
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T* fr = f + STRIDE * r;
+        const T rf = (r0 * fr[0] + r1 * fr[1] + r2 * fr[2]) * c1i;
+        acc[3 * r + 0] += c0 * fr[0] + r0 * rf;
+        acc[3 * r + 1] += c0 * fr[1] + r1 * rf;
+        acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
+      }
+    }
+  }
+  if (KERNEL == SE_HARMONIC_FIELD || KERNEL == SE_ROTLET) {
+    const T c1 = reg ? (ec + c2pi * e) * inv2 : T(0);
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        if (KERNEL == SE_HARMONIC_FIELD) {
+          const T cq = c1 * f[r];
+          acc[3 * r + 0] += cq * r0;
+          acc[3 * r + 1] += cq * r1;
+          acc[3 * r + 2] += cq * r2;
+        } else {
+          const T* fr = f + 3 * r;
+          acc[3 * r + 0] += c1 * (fr[1] * r2 - fr[2] * r1);
+          acc[3 * r + 1] += c1 * (fr[2] * r0 - fr[0] * r2);
+          acc[3 * r + 2] += c1 * (fr[0] * r1 - fr[1] * r0);
+        }
+      }
+    }
+  }
+  if (KERNEL == SE_STRESSLET || KERNEL == (SE_STOKESLET | SE_STRESSLET)) {
+    constexpr int STRIDE = KERNEL == SE_STRESSLET ? 6 : 9;
+    constexpr int QOFF = KERNEL == SE_STRESSLET ? 0 : 3;
+    const T A = T(3) * ec + (T(3) + T(2) * xi2 * q2) * c2pi * e;
+    const T B = reg ? T(2) * xi2 * c2pi * e : T(0);
+    const T Ai = reg ? -T(2) * A * inv2 * inv2 : T(0);
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r) {
+      if (r < n_rhs) {
+        const T* q = f + STRIDE * r + QOFF;
+        const T* nu = q + 3;
+        const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
+        const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
+        const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
+        const T c3 = Ai * rq * rnu + qn * B;
+        const T bq = B * rnu, bn = B * rq;
+        acc[3 * r + 0] += c3 * r0 + bq * q[0] + bn * nu[0];
+        acc[3 * r + 1] += c3 * r1 + bq * q[1] + bn * nu[1];
+        acc[3 * r + 2] += c3 * r2 + bq * q[2] + bn * nu[2];
+      }
+    }
+  }
+}
+
 // Real-space sum: one warp per target.
 // (1) Column table: the neighbour columns of the target's cell (along direction 2, trimmed to
 //     the cells that can hold sources within rc, split at periodic images into contiguous
@@ -612,17 +688,28 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
       T part[3 * RMAX];
 #pragma unroll
       for (int q = 0; q < 3 * RMAX; ++q) part[q] = T(0);
-      for (int jj = 0; jj < cnt; ++jj) {
-        const V4 sv = sm.pos[jj];
-        T r0 = th.x - sv.x, r1 = th.y - sv.y, r2 = th.z - sv.z;
-        if (tv && r0 * r0 + r1 * r1 + r2 * r2 < rcp2) {
-          const V4 sl = sm.low[jj];
-          r0 += tl.x - sl.x;
-          r1 += tl.y - sl.y;
-          r2 += tl.z - sl.z;
-          const T rr2 = r0 * r0 + r1 * r1 + r2 * r2;
-          if (rr2 < a.rc2) real_pair<T, KERNEL, RMAX>(r0, r1, r2, rr2, xi, xi2, c2pi, sm.str[jj], a.n_rhs, part);
-        }
+      // two staged candidates at a time, their pair terms without branches (real_pair_m)
+      // so that the two evaluations interleave; a pair of candidates that no lane needs is
+      // skipped (warp-uniform). Unused staging slots hold a far position (never inside).
+      for (int jj = 0; jj < cnt; jj += 2) {
+        const V4 sa = sm.pos[jj], sb = sm.pos[jj + 1];
+        const V4 la = sm.low[jj], lb = sm.low[jj + 1];
+        T a0 = th.x - sa.x, a1 = th.y - sa.y, a2 = th.z - sa.z;
+        T b0 = th.x - sb.x, b1 = th.y - sb.y, b2 = th.z - sb.z;
+        bool ina = tv && a0 * a0 + a1 * a1 + a2 * a2 < rcp2;
+        bool inb = tv && jj + 1 < cnt && b0 * b0 + b1 * b1 + b2 * b2 < rcp2;
+        if (!__any_sync(FULL, ina || inb)) continue;
+        a0 += tl.x - la.x;
+        a1 += tl.y - la.y;
+        a2 += tl.z - la.z;
+        b0 += tl.x - lb.x;
+        b1 += tl.y - lb.y;
+        b2 += tl.z - lb.z;
+        const T ra = a0 * a0 + a1 * a1 + a2 * a2, rb = b0 * b0 + b1 * b1 + b2 * b2;
+        ina = ina && ra < a.rc2;
+        inb = inb && rb < a.rc2;
+        real_pair_m<T, KERNEL, RMAX>(a0, a1, a2, ra, ina, xi, xi2, c2pi, sm.str[jj], a.n_rhs, part);
+        real_pair_m<T, KERNEL, RMAX>(b0, b1, b2, rb, inb, xi, xi2, c2pi, sm.str[jj + 1], a.n_rhs, part);
       }
       // fold the chunk into the sums (compensated in FP32)
 #pragma unroll

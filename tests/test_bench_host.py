@@ -108,7 +108,7 @@ def test_traffic_rows_need_matching_parameters_and_sources(tmp_path, monkeypatch
     (tmp_path / "profiles").mkdir()
     csrc = tmp_path / "paper_2210_01255_gb300" / "csrc"
     csrc.mkdir(parents=True)
-    (csrc / "se_core.cu").write_text("// kernel source\n")
+    (csrc / "se_real.cu").write_text("// kernel source\n")
     sha = hashlib.sha256(b"// kernel source\n").hexdigest()[:16]
     p = {"M": [100, 100, 100], "P": 8, "rc": 0.05}
     (tmp_path / "profiles" / "traffic_w.txt").write_text(
@@ -117,7 +117,7 @@ def test_traffic_rows_need_matching_parameters_and_sources(tmp_path, monkeypatch
     assert bench.kernel_traffic("w", "real", {"st": dict(p, P=10)}) is None
     assert bench.kernel_traffic("w", "spread", {"st": p}) is None
     assert bench.kernel_traffic("other", "real", {"st": p}) is None
-    (csrc / "se_core.cu").write_text("// changed\n")
+    (csrc / "se_real.cu").write_text("// changed\n")
     assert bench.kernel_traffic("w", "real", {"st": p}) is None
 
 
