@@ -52,6 +52,14 @@ def lib():
                               ctypes.c_double, dp, dp]
         L.orc_Q1p0.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         L.orc_GF.argtypes = [ctypes.c_int, ctypes.c_double, dp, dp, dp]
+        L.orc_h_real.argtypes = [ctypes.c_int, dp, ctypes.c_double, ctypes.c_double, ctypes.c_long,
+                                 dp, dp, ctypes.c_long, dp, dp]
+        for name in ("orc_h_fourier3p", "orc_h_fourier2p", "orc_h_fourier1p"):
+            getattr(L, name).argtypes = [dp, ctypes.c_double, ctypes.c_double, ctypes.c_long, dp, dp,
+                                         ctypes.c_long, dp, dp]
+        L.orc_h_k0_3p.argtypes = [dp, ctypes.c_double, ctypes.c_long, dp, ctypes.c_long, dp]
+        L.orc_h_direct0p.argtypes = [ctypes.c_long, dp, dp, ctypes.c_long, dp, dp]
+        L.orc_h_self.argtypes = [ctypes.c_double, ctypes.c_long, dp, dp, ctypes.c_long, dp, dp]
         _lib = L
     return _lib
 
@@ -128,7 +136,10 @@ def parts(D, L, kernel, x, f, targets=None, xi=None, rc=None, kmax=None):
 
 
 def potential(D, L, kernel, x, f, targets=None, xi=None):
-    """The D-periodic potential u^{DP} (star form when targets is None), FP64, (Nt,3)."""
+    """The D-periodic potential u^{DP} (star form when targets is None), FP64, (Nt,3); the
+    harmonic potential ("harmonic", 16) as (Nt,1)."""
+    if kernel in ("harmonic", 16):
+        return harmonic(D, L, x, f, targets, xi)[:, None]
     if kernel in ("harmonic_field", 8):
         return harmonic_field(D, L, x, f, targets, xi)
     p = parts(D, L, kernel, x, f, targets, xi)
@@ -155,6 +166,58 @@ def harmonic_field(D, L, x, q, targets=None, xi=None):
             out = np.zeros_like(u)
         out[:, comp] = u[:, row]
     return out
+
+
+def harmonic_parts(D, L, x, q, targets=None, xi=None, rc=None, kmax=None):
+    """Parts {real, fourier, k0, self} (each (Nt,)) of the Ewald sum of the harmonic
+    potential phi(x) = sum q / |x - y| (charges q, (N,) or (N,1)); for D = 0 only 'direct'.
+    Zero-mode conventions as in ewald_oracle.h: 3P zero mean over the cell, 2P the k^P = 0
+    kernel -2 pi |r_3| (App. A), 1P the k_1 = 0 kernel -2 log(rho) (App. B, l_H = 1)."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    assert q.shape[0] == x.shape[0]
+    t = None if targets is None else np.ascontiguousarray(targets, dtype=np.float64).reshape(-1, 3)
+    N = x.shape[0]
+    nt = N if t is None else t.shape[0]
+    tp = None if t is None else _p(t)
+    lb = lib()
+    out = {}
+    if D == 0:
+        u = np.zeros(nt)
+        assert lb.orc_h_direct0p(N, _p(x), _p(q), nt, tp, _p(u)) == 0
+        out["direct"] = u
+        return out
+    if xi is None:
+        xi = default_xi(D, L)
+    if rc is None:
+        rc = 7.0 / xi
+    if kmax is None:
+        kmax = 13.6 * xi
+    ur = np.zeros(nt)
+    assert lb.orc_h_real(D, _p(L), xi, rc, N, _p(x), _p(q), nt, tp, _p(ur)) == 0
+    out["real"] = ur
+    uf = np.zeros(nt)
+    fn = {3: lb.orc_h_fourier3p, 2: lb.orc_h_fourier2p, 1: lb.orc_h_fourier1p}[D]
+    assert fn(_p(L), xi, kmax, N, _p(x), _p(q), nt, tp, _p(uf)) == 0
+    out["fourier"] = uf
+    uk = np.zeros(nt)
+    if D == 3:
+        assert lb.orc_h_k0_3p(_p(L), xi, N, _p(q), nt, _p(uk)) == 0
+    out["k0"] = uk
+    us = np.zeros(nt)
+    assert lb.orc_h_self(xi, N, _p(x), _p(q), nt, tp, _p(us)) == 0
+    out["self"] = us
+    out["xi"] = xi
+    return out
+
+
+def harmonic(D, L, x, q, targets=None, xi=None):
+    """The D-periodic harmonic potential phi (star form when targets is None), FP64, (Nt,)."""
+    p = harmonic_parts(D, L, x, q, targets, xi)
+    if D == 0:
+        return p["direct"]
+    return p["real"] + p["fourier"] + p["k0"] + p["self"]
 
 
 def Knu(nu, a, b):

@@ -785,3 +785,203 @@ int orc_self(double xi, int kernel, long N, const double* x, const double* f, lo
         for (int j = 0; j < 3; ++j) u[m * 3 + j] += c * f[n * 3 + j];
   return 0;
 }
+
+/* ------------------------------------------ harmonic (Laplace) potential, phi = sum q / r
+ *
+ * The scalar potential of the harmonic kernel H(r) = 1/|r| (Sec. 2.1) with one strength q
+ * per source; one output per target, u[m]. Ewald split with the Ewald screening function
+ * (Eq. ewald-screening): real-space kernel erfc(xi r) / r, Fourier-space kernel
+ * 4 pi / k^2 exp(-k^2 / 4 xi^2). Zero-mode conventions:
+ *   3P: the potential has zero mean over the cell (the k = 0 term of the full kernel is
+ *       left out); the Ewald form then carries the constant -pi Q / (xi^2 V), Q = sum q,
+ *       which is minus the k -> 0 limit of the real-space kernel's transform over V.
+ *   2P: the k^P = 0 mode uses the App. A result for the harmonic, whose kernel in the free
+ *       direction is -2 pi |r_3| (no constant).
+ *   1P: the k_1 = 0 mode uses the App. B result with gauge l_H = 1, i.e. the kernel
+ *       -2 log(rho) in the free plane.
+ *   0P: the plain free-space sum. */
+
+int orc_h_real(int D, const double L[3], double xi, double rc, long N, const double* x,
+               const double* q, long Nt, const double* t, double* u) {
+  if (D < 0 || D > 3 || !(xi > 0) || !(rc > 0) || N < 0) return -1;
+  if (t == NULL) { t = x; Nt = N; }
+  int pmax[3] = {0, 0, 0};
+  for (int d = 0; d < D; ++d) pmax[d] = (int)floor(rc / L[d]) + 1;
+#pragma omp parallel for schedule(dynamic, 4)
+  for (long m = 0; m < Nt; ++m) {
+    double acc = 0;
+    for (long n = 0; n < N; ++n)
+      for (int p0 = -pmax[0]; p0 <= pmax[0]; ++p0)
+        for (int p1 = -pmax[1]; p1 <= pmax[1]; ++p1)
+          for (int p2 = -pmax[2]; p2 <= pmax[2]; ++p2) {
+            double r0 = t[m * 3 + 0] - x[n * 3 + 0] + p0 * L[0];
+            double r1 = t[m * 3 + 1] - x[n * 3 + 1] + p1 * L[1];
+            double r2 = t[m * 3 + 2] - x[n * 3 + 2] + p2 * L[2];
+            double rr = r0 * r0 + r1 * r1 + r2 * r2;
+            if (rr == 0.0 || rr >= rc * rc) continue;
+            double r = sqrt(rr);
+            acc += q[n] * erfc(xi * r) / r;
+          }
+    u[m] += acc;
+  }
+  return 0;
+}
+
+/* 3P, k != 0, |k| <= kmax: (1/V) sum_k 4 pi / k^2 exp(-k^2/4xi^2) sum_n q_n e^{i k.(x - x_n)} */
+int orc_h_fourier3p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u) {
+  if (!(xi > 0) || !(kmax > 0)) return -1;
+  if (t == NULL) { t = x; Nt = N; }
+  int K[3];
+  for (int d = 0; d < 3; ++d) K[d] = (int)floor(kmax * L[d] / (2.0 * M_PI));
+  long nmax = (long)(2 * K[0] + 1) * (2 * K[1] + 1) * (2 * K[2] + 1);
+  double* kv = (double*)malloc(sizeof(double) * 4 * nmax);
+  long nk = 0;
+  for (int a = -K[0]; a <= K[0]; ++a)
+    for (int b = -K[1]; b <= K[1]; ++b)
+      for (int c = -K[2]; c <= K[2]; ++c) {
+        if (a == 0 && b == 0 && c == 0) continue;
+        double k0 = 2.0 * M_PI * a / L[0], k1 = 2.0 * M_PI * b / L[1], k2 = 2.0 * M_PI * c / L[2];
+        double kk = k0 * k0 + k1 * k1 + k2 * k2;
+        if (kk > kmax * kmax) continue;
+        kv[nk * 4 + 0] = k0;
+        kv[nk * 4 + 1] = k1;
+        kv[nk * 4 + 2] = k2;
+        kv[nk * 4 + 3] = 4.0 * M_PI / kk * exp(-kk / (4.0 * xi * xi));
+        ++nk;
+      }
+  double complex* S = (double complex*)malloc(sizeof(double complex) * (nk > 0 ? nk : 1));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long k = 0; k < nk; ++k) {
+    double complex acc = 0;
+    for (long n = 0; n < N; ++n)
+      acc += q[n] * cexp(-I * (kv[k * 4] * x[n * 3] + kv[k * 4 + 1] * x[n * 3 + 1] + kv[k * 4 + 2] * x[n * 3 + 2]));
+    S[k] = acc;
+  }
+  const double vol = L[0] * L[1] * L[2];
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long m = 0; m < Nt; ++m) {
+    double acc = 0;
+    for (long k = 0; k < nk; ++k)
+      acc += kv[k * 4 + 3] *
+             creal(S[k] * cexp(I * (kv[k * 4] * t[m * 3] + kv[k * 4 + 1] * t[m * 3 + 1] + kv[k * 4 + 2] * t[m * 3 + 2])));
+    u[m] += acc / vol;
+  }
+  free(kv);
+  free(S);
+  return 0;
+}
+
+/* 3P zero-mean constant -pi Q / (xi^2 V), added to every target. */
+int orc_h_k0_3p(const double L[3], double xi, long N, const double* q, long Nt, double* u) {
+  double Q = 0;
+  for (long n = 0; n < N; ++n) Q += q[n];
+  const double c = -M_PI * Q / (xi * xi * L[0] * L[1] * L[2]);
+  for (long m = 0; m < Nt; ++m) u[m] += c;
+  return 0;
+}
+
+/* 2P: (1/A) [ sum_{k^P != 0} Q^{H,2P}(k1,k2,r3) e^{i(k1 r1 + k2 r2)} + Q^{H,2P,(0)}(r3) ]
+ * per source, with Q^{H,2P} = (pi / alpha) beta^+ (Eq. 2p-QH-integral, auxiliary variables
+ * Eq. 2p-aux) and Q^{H,2P,(0)} = -2 pi (r3 erf(xi r3) + exp(-xi^2 r3^2) / (sqrt(pi) xi))
+ * (App. A, zero mode of the harmonic). */
+int orc_h_fourier2p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u) {
+  if (!(xi > 0) || !(kmax > 0)) return -1;
+  if (t == NULL) { t = x; Nt = N; }
+  int K1 = (int)floor(kmax * L[0] / (2.0 * M_PI));
+  int K2 = (int)floor(kmax * L[1] / (2.0 * M_PI));
+  const double area = L[0] * L[1];
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long m = 0; m < Nt; ++m) {
+    double acc = 0;
+    for (long n = 0; n < N; ++n) {
+      double r1 = t[m * 3 + 0] - x[n * 3 + 0];
+      double r2 = t[m * 3 + 1] - x[n * 3 + 1];
+      double r3 = t[m * 3 + 2] - x[n * 3 + 2];
+      double s = 0;
+      for (int a = -K1; a <= K1; ++a)
+        for (int b = -K2; b <= K2; ++b) {
+          if (a == 0 && b == 0) continue;
+          double k1 = 2.0 * M_PI * a / L[0], k2 = 2.0 * M_PI * b / L[1];
+          double al2 = k1 * k1 + k2 * k2;
+          if (al2 > kmax * kmax) continue;
+          double al = sqrt(al2);
+          double bp = theta(+1.0, al, xi, r3) + theta(-1.0, al, xi, r3);
+          s += M_PI / al * bp * cos(k1 * r1 + k2 * r2);
+        }
+      s += -2.0 * M_PI * (r3 * erf(xi * r3) + exp(-xi * xi * r3 * r3) / (SQRTPI * xi));
+      acc += q[n] * s;
+    }
+    u[m] += acc / area;
+  }
+  return 0;
+}
+
+/* 1P: (1/L1) [ sum_{k1 != 0} K_0(U,V) e^{i k1 r1} + Q^{H,1P,(0)}(r2,r3) ] per source, with
+ * Q^{H,1P} = K_0(U,V) (Eq. 1p-QH-integral, U, V of Eq. 1p-aux, K_nu of Eq. Knu-def) and
+ * Q^{H,1P,(0)} = -log(rho^2) - E_1(xi^2 rho^2) (App. B, zero mode of the harmonic, l_H = 1),
+ * whose limit at rho = 0 is EULER_GAMMA + log(xi^2). */
+int orc_h_fourier1p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u) {
+  if (!(xi > 0) || !(kmax > 0)) return -1;
+  if (t == NULL) { t = x; Nt = N; }
+  if (!gl_ready) gl_init();
+  int K1 = (int)floor(kmax * L[0] / (2.0 * M_PI));
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long m = 0; m < Nt; ++m) {
+    double acc = 0;
+    for (long n = 0; n < N; ++n) {
+      double r1 = t[m * 3 + 0] - x[n * 3 + 0];
+      double r2 = t[m * 3 + 1] - x[n * 3 + 1];
+      double r3 = t[m * 3 + 2] - x[n * 3 + 2];
+      double rho2 = r2 * r2 + r3 * r3;
+      double V = xi * xi * rho2;
+      double s = 0;
+      for (int a = 1; a <= K1; ++a) {
+        double k1 = 2.0 * M_PI * a / L[0];
+        double Kn[4];
+        knu_all(k1 * k1 / (4.0 * xi * xi), V, Kn);
+        s += 2.0 * Kn[1] * cos(k1 * r1);     /* the +k1 and -k1 terms */
+      }
+      s += rho2 > 0 ? -log(rho2) - orc_En(1, V) : EULER_GAMMA + log(xi * xi);
+      acc += q[n] * s;
+    }
+    u[m] += acc / L[0];
+  }
+  return 0;
+}
+
+/* Free space: sum_n q_n / |t_m - x_n|, pairs at zero separation skipped. */
+int orc_h_direct0p(long N, const double* x, const double* q, long Nt, const double* t, double* u) {
+  if (t == NULL) { t = x; Nt = N; }
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long m = 0; m < Nt; ++m) {
+    double acc = 0;
+    for (long n = 0; n < N; ++n) {
+      double r0 = t[m * 3] - x[n * 3], r1 = t[m * 3 + 1] - x[n * 3 + 1], r2 = t[m * 3 + 2] - x[n * 3 + 2];
+      double rr = r0 * r0 + r1 * r1 + r2 * r2;
+      if (rr == 0.0) continue;
+      acc += q[n] / sqrt(rr);
+    }
+    u[m] += acc;
+  }
+  return 0;
+}
+
+/* Self term of the harmonic: -(2 xi / sqrt(pi)) q (the r -> 0 limit of the Fourier-space
+ * kernel erf(xi r) / r, removed for the omitted self pair); for every target coinciding
+ * exactly with a source (every target in the star form). */
+int orc_h_self(double xi, long N, const double* x, const double* q, long Nt, const double* t,
+               double* u) {
+  const double c = -2.0 * xi / SQRTPI;
+  if (t == NULL) {
+    for (long m = 0; m < N; ++m) u[m] += c * q[m];
+    return 0;
+  }
+  for (long m = 0; m < Nt; ++m)
+    for (long n = 0; n < N; ++n)
+      if (t[m * 3] == x[n * 3] && t[m * 3 + 1] == x[n * 3 + 1] && t[m * 3 + 2] == x[n * 3 + 2])
+        u[m] += c * q[n];
+  return 0;
+}

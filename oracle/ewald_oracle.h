@@ -83,6 +83,24 @@ int orc_Q1p0(int kernel, double xi, double r2, double r3, double* re);
  * nonzero k, exposed for the tests (same output layout as above). */
 int orc_GF(int kernel, double xi, const double* k, double* re, double* im);
 
+/* Harmonic (Laplace) potential phi(x) = sum_n q_n / |x - x_n| (kernel H = 1/r, Sec. 2.1):
+ * one strength q[n] per source, one output u[m] per target (added into). Ewald split with
+ * the Ewald screening function; zero-mode conventions: 3P zero mean over the cell
+ * (orc_h_k0_3p adds the constant that this needs), 2P the k^P = 0 kernel -2 pi |r_3|
+ * (App. A), 1P the k_1 = 0 kernel -2 log(rho) (App. B, gauge l_H = 1), 0P direct sum. */
+int orc_h_real(int D, const double L[3], double xi, double rc, long N, const double* x,
+               const double* q, long Nt, const double* t, double* u);
+int orc_h_fourier3p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u);
+int orc_h_k0_3p(const double L[3], double xi, long N, const double* q, long Nt, double* u);
+int orc_h_fourier2p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u);
+int orc_h_fourier1p(const double L[3], double xi, double kmax, long N, const double* x,
+                    const double* q, long Nt, const double* t, double* u);
+int orc_h_direct0p(long N, const double* x, const double* q, long Nt, const double* t, double* u);
+int orc_h_self(double xi, long N, const double* x, const double* q, long Nt, const double* t,
+               double* u);
+
 #ifdef __cplusplus
 }
 #endif

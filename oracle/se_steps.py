@@ -31,11 +31,18 @@ import math
 import numpy as np
 import scipy.special as sp
 
-STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD = 1, 2, 4, 8
-_NAMES = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET, "harmonic_field": HARMONIC_FIELD}
+STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD, HARMONIC = 1, 2, 4, 8, 16
+_NAMES = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET, "harmonic_field": HARMONIC_FIELD,
+          "harmonic": HARMONIC}
 # the harmonic field E = -grad H q (H = 1/r) is a first derivative of H like the rotlet
-# (Omega_jl = -eps_jlm d_m H): Ewald screening and the harmonic modified kernels
-_HARMONIC = (ROTLET, HARMONIC_FIELD)
+# (Omega_jl = -eps_jlm d_m H), the harmonic potential H q itself: Ewald screening and the
+# harmonic modified kernels for all three
+_HARMONIC = (ROTLET, HARMONIC_FIELD, HARMONIC)
+
+
+def n_out(kernel):
+    """Output components per target: 1 for the harmonic potential, 3 otherwise."""
+    return 1 if kernel_id(kernel) == HARMONIC else 3
 
 
 def kernel_id(kernel):
@@ -115,9 +122,12 @@ def taps(u, P):
 
 def _Khat(kernel, k):
     """Operator symbols K^(k) of Eqs. (diffop-rel-fourier-1..3), shape (..., 3, 3[, 3]);
-    the harmonic field's gradient -i k, shape (..., 3, 1)."""
+    the harmonic field's gradient -i k, shape (..., 3, 1); the identity for the harmonic
+    potential, shape (..., 1, 1)."""
     d = np.eye(3)
     k2 = np.sum(k * k, axis=-1)
+    if kernel == HARMONIC:
+        return np.ones(k.shape[:-1] + (1, 1), dtype=complex)
     if kernel == HARMONIC_FIELD:
         return (-1j * k)[..., :, None]
     if kernel == STOKESLET:
@@ -180,7 +190,7 @@ def gathering_3p(t, Ft, L, M, win):
     """Step (v), Eq. (SE-gathering-disc)."""
     h = win.h
     P = win.P
-    u = np.zeros((t.shape[0], 3))
+    u = np.zeros((t.shape[0], Ft.shape[0]))
     for m in range(t.shape[0]):
         idx, wts = [], []
         for d in range(3):
@@ -189,7 +199,7 @@ def gathering_3p(t, Ft, L, M, win):
             idx.append(np.mod(j, M[d]))
         w3 = wts[0][:, None, None] * wts[1][None, :, None] * wts[2][None, None, :]
         ix = np.ix_(idx[0], idx[1], idx[2])
-        for c in range(3):
+        for c in range(Ft.shape[0]):
             u[m, c] = h ** 3 * np.sum(Ft[c][ix] * w3)
     return u
 
@@ -244,12 +254,23 @@ def fourier_part_3p(kernel, x, f, L, M, xi, window, P, targets=None, return_step
 
 
 def self_term(kernel, xi, f):
-    """Eq. (self-term): -4 xi / sqrt(pi) f for the stokeslet, 0 otherwise."""
+    """Eq. (self-term): -4 xi / sqrt(pi) f for the stokeslet, 0 for the rotlet, stresslet
+    and harmonic field; -2 xi / sqrt(pi) q for the harmonic potential (the r -> 0 limit of
+    its Fourier-space kernel erf(xi r) / r)."""
     kernel = kernel_id(kernel)
     f = np.asarray(f, dtype=float)
     if kernel == STOKESLET:
         return -4 * xi / math.sqrt(math.pi) * f
+    if kernel == HARMONIC:
+        return -2 * xi / math.sqrt(math.pi) * f.reshape(-1, 1)
     return np.zeros((f.shape[0], 3))
+
+
+def k0_harmonic_3p(L, xi, q):
+    """The constant -pi Q / (xi^2 V) (Q = sum q) that makes the 3P harmonic potential of
+    real + Fourier (k != 0) + self parts the zero-mean one: minus the k -> 0 limit of the
+    real-space kernel's transform, pi / xi^2, over the cell volume."""
+    return -math.pi * float(np.sum(q)) / (xi * xi * float(np.prod(np.asarray(L, dtype=float))))
 
 
 def k0_stresslet_3p(L, x, f, targets=None):
@@ -413,7 +434,7 @@ def gridding(fg, x, comps, win):
 def gathering(fg, t, Ft, win):
     """Step (v) on the (extended) grid."""
     h, P = win.h, win.P
-    u = np.zeros((t.shape[0], 3))
+    u = np.zeros((t.shape[0], Ft.shape[0]))
     for m in range(t.shape[0]):
         idx, wts = [], []
         for d in range(3):
@@ -423,7 +444,7 @@ def gathering(fg, t, Ft, win):
             idx.append(np.mod(j, fg.m[d]) if d < fg.D else j)
         w3 = wts[0][:, None, None] * wts[1][None, :, None] * wts[2][None, None, :]
         ix = np.ix_(idx[0], idx[1], idx[2])
-        for c in range(3):
+        for c in range(Ft.shape[0]):
             u[m, c] = h ** 3 * np.sum(Ft[c][ix] * w3)
     return u
 
@@ -462,6 +483,9 @@ def modified_2p_column(kernel, kap, xi, R):
         D = np.array([[0, 1.0, 0], [-1.0, 0, 0], [0, 0, 0]])
         s = hat_Z2p(kap, R) * _screen(kernel, k2, xi)
         return s[:, None, None] * D
+    if kernel == HARMONIC:
+        # the truncated harmonic kernel itself (its free-direction kernel is -2 pi |r_3|)
+        return (hat_H2p(kap, R) * _screen(kernel, k2, xi))[:, None, None] * np.ones((1, 1))
     if kernel == HARMONIC_FIELD:
         # only the direction-3 derivative survives at k^P = 0: the rotlet's scalar (the same
         # derivative of the modified harmonic kernel) on (0, 0, q)
@@ -519,7 +543,8 @@ def scaling_aft(D, kernel, grid, fg, xi, win, s0, s_star, kbar_star, fM):
     per = tuple(range(1, D + 1))                  # periodic axes of the [C, x, y, z] array
     free = tuple(range(D + 1, 4))
     Fp = np.fft.fftn(grid, axes=per)              # FFT in the periodic directions
-    out = np.zeros((max(Fp.shape[0], 3),) + Fp.shape[1:], dtype=complex)  # 3 outputs
+    no = n_out(kernel)
+    out = np.zeros((max(Fp.shape[0], no),) + Fp.shape[1:], dtype=complex)  # no outputs
     kbs = [np.fft.fftfreq(M[d]) * M[d] for d in range(D)]
     for idx in np.ndindex(*[M[d] for d in range(D)]):
         kb = [kbs[d][idx[d]] for d in range(D)]
@@ -563,8 +588,8 @@ def scaling_aft(D, kernel, grid, fg, xi, win, s0, s_star, kbar_star, fM):
             G = G * keep.reshape(keep.shape + (1,) * (G.ndim - 2))
         Phit = _apply(kernel, G, Fk)
         back = np.fft.ifftn(Phit, axes=tuple(range(1, 1 + 3 - D)))
-        out[(slice(None, 3),) + idx] = back[(slice(None),) + tuple(slice(0, M[d]) for d in range(D, 3))]
-    Ft = np.fft.ifftn(out[:3], axes=per)
+        out[(slice(None, no),) + idx] = back[(slice(None),) + tuple(slice(0, M[d]) for d in range(D, 3))]
+    Ft = np.fft.ifftn(out[:no], axes=per)
     assert np.abs(Ft.imag).max() <= 1e-9 * max(np.abs(Ft.real).max(), 1e-300)
     return Ft.real
 
@@ -642,6 +667,10 @@ def fourier_part(D, kernel, x, f, L, h, P, xi, window, Mext=(0, 0, 0), s0=None, 
     else:
         Ft = scaling_aft(D, kernel, grid, fg, xi, win, s0, s_star, kbar_star, fM)
     u = gathering(fg, t, Ft, win)
+    if kernel == HARMONIC and D == 1:
+        # the k_1 = 0 class used -2 log(rho / R) (l_H = R, Eq. optimal-1p-harmonic); the output
+        # convention is l_H = 1: subtract 2 log(R) / L_1 sum q
+        u = u - 2.0 * math.log(fg.R) / L[0] * float(np.sum(f))
     if kernel == STOKESLET:
         fs = np.asarray(f, dtype=float).sum(axis=0)
         if D == 0:     # subtract 4 b_B sum f with b_B = -1/(2R)

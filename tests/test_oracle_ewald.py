@@ -297,3 +297,127 @@ def test_harmonic_field_periodic_is_xi_independent(D):
     a = E.harmonic_field(D, [1, 1, 1], x, q, xi=4.0)
     b = E.harmonic_field(D, [1, 1, 1], x, q, xi=7.0)
     assert np.abs(a - b).max() < 1e-11 * np.abs(a).max()
+
+
+# ------------------------------------------------ harmonic potential phi = sum q / r (scalar)
+
+def _madelung():
+    vals = {}
+    path = __file__.rsplit("/", 1)[0] + "/golden/madelung.txt"
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, value = line.split()[:2]
+        vals[name] = float(value)
+    return vals
+
+
+def _evjen_2d(n):
+    """Checkerboard Madelung constant by Evjen's method: the square of side 2n around the
+    ion, edge charges halved and corner charges quartered (so each shell is neutral)."""
+    i = np.arange(-n, n + 1)
+    I, J = np.meshgrid(i, i, indexing="ij")
+    w = np.where(np.abs(I) == n, 0.5, 1.0) * np.where(np.abs(J) == n, 0.5, 1.0)
+    r = np.hypot(I, J)
+    r[n, n] = 1.0
+    s = w * (-1.0) ** (I + J) / r
+    s[n, n] = 0.0
+    return -s.sum()
+
+
+def test_harmonic_madelung_constants():
+    """Ionic crystals of alternating unit charges: the 3P rock salt (cube of side 1, d = 1/2),
+    the 2P checkerboard (d = 1/2, the free direction at any height) and the 1P alternating
+    chain (d = 1/2); the potential at each ion is -+M / d, for two values of xi."""
+    M = _madelung()
+    # the 2-D constant also by brute force (Evjen sums, Richardson over n with error ~ n^-3)
+    a, b = _evjen_2d(200), _evjen_2d(400)
+    assert abs((8 * b - a) / 7 - M["square_checkerboard_2d"]) < 1e-10
+    g = np.array([(i, j, k) for i in range(2) for j in range(2) for k in range(2)], dtype=float)
+    x3 = 0.5 * g
+    q3 = np.where(g.sum(axis=1) % 2 == 0, 1.0, -1.0)
+    x2 = np.array([[0, 0, 0.3], [0.5, 0, 0.3], [0, 0.5, 0.3], [0.5, 0.5, 0.3]])
+    q2 = np.array([1.0, -1.0, -1.0, 1.0])
+    x1 = np.array([[0.0, 0.4, 0.6], [0.5, 0.4, 0.6]])
+    q1 = np.array([1.0, -1.0])
+    for D, x, q, name in ((3, x3, q3, "rock_salt_3d"), (2, x2, q2, "square_checkerboard_2d"),
+                          (1, x1, q1, "alternating_chain_1d")):
+        for s in (1.0, 1.8):
+            phi = E.harmonic(D, [1.0, 1.0, 1.0], x, q, xi=s * E.default_xi(D, [1.0, 1.0, 1.0]))
+            assert np.abs(phi * 0.5 + q * M[name]).max() < 1e-12, (D, s)
+
+
+@pytest.mark.parametrize("D,L", [(3, (1.0, 1.2, 0.8)), (2, (1.0, 1.3, 1.0)), (1, (1.2, 1.0, 1.0))])
+def test_harmonic_xi_independence_non_neutral(D, L):
+    """A charged (non-neutral) system: the total is independent of xi, including the 3P
+    zero-mean constant; star form and explicit targets (some on sources)."""
+    rng = np.random.default_rng(11 + D)
+    x = rng.random((14, 3)) * L
+    q = rng.standard_normal(14) + 0.4
+    t = np.vstack([rng.random((5, 3)) * L, x[:2]])
+    xi0 = E.default_xi(D, L)
+    for tg in (None, t):
+        a = E.harmonic(D, L, x, q, targets=tg, xi=xi0)
+        b = E.harmonic(D, L, x, q, targets=tg, xi=1.7 * xi0)
+        assert np.abs(a - b).max() < 1e-12 * np.abs(a).max()
+    # explicit targets on the sources give the star values
+    star = E.harmonic(D, L, x, q, xi=xi0)
+    assert np.abs(E.harmonic(D, L, x, q, targets=x[:2], xi=xi0) - star[:2]).max() < 1e-12 * np.abs(star).max()
+
+
+@pytest.mark.parametrize("D", [3, 2, 1, 0])
+def test_harmonic_gradient_is_the_field(D):
+    """-grad phi (5-point central differences, h = 1e-3) equals the harmonic field of the
+    same charges, which the oracle computes independently from the rotlet tensors."""
+    rng = np.random.default_rng(20 + D)
+    L = [1.0, 1.0, 1.0]
+    x = rng.random((15, 3))
+    q = rng.standard_normal(15)
+    t = rng.random((4, 3))
+    h = 1e-3
+    g = np.zeros((4, 3))
+    for j in range(3):
+        e = np.zeros(3)
+        e[j] = h
+        f = [E.harmonic(D, L, x, q, targets=t + s * e) for s in (2, 1, -1, -2)]
+        g[:, j] = -(-f[0] + 8 * f[1] - 8 * f[2] + f[3]) / (12 * h)
+    F = E.harmonic_field(D, L, x, q, targets=t)
+    assert np.abs(g - F).max() < 1e-7 * np.abs(F).max()
+
+
+def test_harmonic_gauges_far_field():
+    """The k^P = 0 conventions seen from far away, where every k^P != 0 mode has decayed:
+    2P tends to -(2 pi / A) sum q |z - z_n| and 1P to -(2 / L_1) sum q log(rho_n) (l_H = 1)."""
+    rng = np.random.default_rng(30)
+    L = [1.0, 1.0, 1.0]
+    x = rng.random((10, 3))
+    q = rng.standard_normal(10)
+    t = np.array([[0.3, 0.7, 7.0], [0.1, 0.2, -6.0]])
+    ff = np.array([-2 * np.pi * (q * np.abs(p[2] - x[:, 2])).sum() for p in t])
+    assert np.abs(E.harmonic(2, L, x, q, targets=t) - ff).max() < 1e-12 * np.abs(ff).max()
+    t = np.array([[0.3, 7.0, 0.5], [0.1, -3.0, 6.0]])
+    ff = np.array([-2 * (q * np.log(np.hypot(p[1] - x[:, 1], p[2] - x[:, 2]))).sum() for p in t])
+    assert np.abs(E.harmonic(1, L, x, q, targets=t) - ff).max() < 1e-12 * np.abs(ff).max()
+
+
+def test_harmonic_3p_zero_mean():
+    """The 3P potential of a charged system has zero mean over the cell: the midpoint rule on
+    32^3 targets (error from the 1/r singularities ~ h^2) against the constant -pi Q/(xi^2 V)
+    that the convention adds (0.27 here)."""
+    rng = np.random.default_rng(5)
+    x = rng.random((6, 3))
+    q = rng.standard_normal(6) + 0.5
+    n = 32
+    g = (np.arange(n) + 0.5) / n
+    t = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    phi = E.harmonic(3, [1.0, 1.0, 1.0], x, q, targets=t, xi=3.5)
+    assert abs(phi.mean()) < 0.01 * np.pi * abs(q.sum()) / 3.5 ** 2
+
+
+def test_harmonic_direct_0p_by_hand():
+    """Two charges at distance 2 and a target between them."""
+    x = np.array([[0.0, 0.0, 0.0], [2.0, 0.0, 0.0]])
+    q = np.array([3.0, -1.0])
+    phi = E.harmonic(0, [1.0, 1.0, 1.0], x, q, targets=np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 0.0]]))
+    assert np.allclose(phi, [3.0 - 1.0, -0.5], rtol=0, atol=1e-15)
+    assert np.allclose(E.harmonic(0, [1.0, 1.0, 1.0], x, q), [-0.5, 1.5], rtol=0, atol=1e-15)

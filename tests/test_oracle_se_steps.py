@@ -186,3 +186,49 @@ def test_alg1_harmonic_field_free_directions(D):
                        kbar_star=6)
     tot = u + _field_real(D, L, xi, x, q)
     assert E.rms_rel(tot, E.harmonic_field(D, L, x, q)) < 1e-9
+
+
+# ------------------------------------------------------------ harmonic potential (scalar)
+
+def _potential_real(D, L, xi, x, q):
+    ur = np.zeros(x.shape[0])
+    E.lib().orc_h_real(D, E._p(np.asarray(L, dtype=float)), xi, 7.0 / xi, x.shape[0],
+                       E._p(np.ascontiguousarray(x)), E._p(np.ascontiguousarray(q)), x.shape[0], None, E._p(ur))
+    return ur
+
+
+def test_alg1_harmonic_potential_3p():
+    """A charged system: Alg. 1 + real space + self term + the zero-mean constant."""
+    rng = np.random.default_rng(51)
+    N = 40
+    x = rng.random((N, 3))
+    q = rng.standard_normal(N) + 0.3
+    xi = 8.0
+    u = S.fourier_part_3p("harmonic", x, q[:, None], [1, 1, 1], (48, 48, 48), xi, "pkb", 16)[:, 0]
+    tot = u + _potential_real(3, [1, 1, 1], xi, x, q) + S.self_term("harmonic", xi, q)[:, 0] \
+        + S.k0_harmonic_3p([1, 1, 1], xi, q)
+    ref = E.harmonic(3, [1, 1, 1], x, q)
+    assert np.sqrt(np.mean((tot - ref) ** 2) / np.mean(ref ** 2)) < 1e-11
+
+
+@pytest.mark.parametrize("D", [2, 1, 0])
+def test_alg1_harmonic_potential_free_directions(D):
+    """D = 2, 1: the truncated harmonic kernels on the k^P = 0 class with the adaptive FFT (and
+    the 1P gauge change from l_H = R to 1); D = 0: the precomputed truncated harmonic kernel;
+    a charged system against the exact sums."""
+    rng = np.random.default_rng(60 + D)
+    L = np.array([1.0, 1.0, 1.0])
+    N = 24
+    x = rng.random((N, 3))
+    q = rng.standard_normal(N) + 0.3
+    xi, M, P = 6.0, 40, 16
+    lam = 2.4 if D > 0 else 1.5
+    me = 4 * math.ceil((M + P + (lam - 1) * P) / 4)
+    Mext = [0, 0, 0]
+    for d in range(D, 3):
+        Mext[d] = me
+    u = S.fourier_part(D, "harmonic", x, q[:, None], L, 1.0 / M, P, xi, "pkb", Mext=Mext, s_star=3.0,
+                       kbar_star=6)[:, 0]
+    tot = u + _potential_real(D, L, xi, x, q) + S.self_term("harmonic", xi, q)[:, 0]
+    ref = E.harmonic(D, L, x, q)
+    assert np.sqrt(np.mean((tot - ref) ** 2) / np.mean(ref ** 2)) < 1e-9
