@@ -9,7 +9,8 @@ points (se_autotune_timed), each candidate's parameters from the tolerance rules
 Sec. 4.6. --workload selects another configuration of paper_2210_01255_gb300.workloads.CONFIGS:
 the 3P stresslet + rotlet of 20,000 points, the 2P stokeslet with 8 RHS, 64 independent 1P
 stokeslet systems with 16 RHS each, or the 3P harmonic field of 1e5 charges. --experiment runs the
-timing experiments of Sec. 5.2 instead (one JSON line per data point).
+timing experiments of Sec. 5.2 or the window comparison of Sec. 5.3 instead (one JSON line per
+data point).
 
 A workload is a list of evaluations (kernel, points, strengths, plan); one step runs all of
 them (real-space sum, Fourier-space part of Alg. 1, corrections). value = (target, RHS)
@@ -20,7 +21,7 @@ and one kernel per evaluation, same parameters) and the end-to-end form through 
 buffers are reported beside it.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--workload W]
-       python bench.py --experiment complexity|time_vs_error [--exp-d 3,0] [--exp-jmax 5]
+       python bench.py --experiment complexity|time_vs_error|window [--exp-d 3,0] [--exp-jmax 5]
 Under torchrun (N > 1) every rank runs the same workload on its own GPU (replicas, weak
 scaling, no collective in the data path); value = all ranks' targets / the slowest rank's time.
 """
@@ -410,6 +411,8 @@ def run_experiment(args):
                         del plan, xd, fd
                         torch.cuda.empty_cache()
         return 0
+    if args.experiment == "window":
+        return run_window_experiment(args, stream)
     N = 100000
     x = W.uniform_points(N, (1, 1, 1), seed=300)
     xd = torch.tensor(x, device="cuda")
@@ -429,6 +432,75 @@ def run_experiment(args):
                 print(json.dumps({"experiment": "time_vs_error", "D": D, "kernel": k, "N": N, "xi": t["xi"],
                                   "tol_abs": 10.0 ** -p, "rc": t["rc"], "M": t["M"], "P": t["P"], "ms": ms,
                                   "rms_rel_err": err}), flush=True)
+                del plan
+                torch.cuda.empty_cache()
+    return 0
+
+
+# Window comparison of Sec. 5.3: xi of the uniform system at N = 1e5, D = 3 (the table of
+# Sec. 5.2) and the grid of the comparison's figure, per kernel
+WINDOW_EXP = {"stokeslet": (43.0296, 196), "stresslet": (39.4021, 192), "rotlet": (45.4936, 208)}
+
+
+def run_window_experiment(args, stream):
+    """PKB against the truncated Gaussian (Sec. 5.3): N = 1e5 uniform points, Q = 1, L = 1,
+    D = 3, FP64, xi and M fixed per kernel; P = 2, 4, ..., 14 (PKB) and 2, 4, ..., 24 (TG; the
+    plans take even P only). Per data point: gridding + gathering time (the two stages' CUDA
+    events, median over --exp-reps evaluations) against the relative rms error of the
+    Fourier-space part, the reference being the same method with the PKB window at P = 20;
+    each point averages --exp-configs point sets."""
+    import torch
+    import paper_2210_01255_gb300 as se
+    from paper_2210_01255_gb300 import workloads as W
+    N = 100000
+    kernels = [k for k in args.exp_kernels.split(",") if k in WINDOW_EXP]
+    sets = []
+    for c in range(args.exp_configs):
+        x = W.uniform_points(N, (1, 1, 1), seed=400 + c)
+        sets.append((torch.tensor(x, device="cuda"), c))
+
+    def plan_for(kernel, P, window):
+        xi, M = WINDOW_EXP[kernel]
+        o = se.se_opts_default()
+        o.kernel_mask = se.KERNELS[kernel]
+        return se.Plan(3, (1.0, 1.0, 1.0), xi, 0.1, (M, M, M), P, window, "fp64", opts=o, stream=stream)
+
+    def fourier(plan, kernel, xd, fd, reps):
+        u = plan.evaluate(kernel, xd, fd, parts=se.PART_FOURIER)
+        plan.sync()
+        se.se_set_timing(plan.handle, True)
+        ts = []
+        for _ in range(reps):
+            u = plan.evaluate(kernel, xd, fd, parts=se.PART_FOURIER)
+            t_ = plan.info().times_ms
+            ts.append((t_[1] + t_[5], sum(max(v, 0.0) for v in t_)))
+        se.se_set_timing(plan.handle, False)
+        plan.sync()
+        ts = np.array(ts)
+        return float(np.median(ts[:, 0])), float(np.median(ts[:, 1])), u.cpu().numpy()
+
+    for k in kernels:
+        fs = [torch.tensor(unit_q_strengths(k, N, seed=500 + c), device="cuda") for _, c in sets]
+        ref_plan = plan_for(k, 20, "pkb")
+        refs = [fourier(ref_plan, k, xd, fd, 1)[2] for (xd, _), fd in zip(sets, fs)]
+        del ref_plan
+        for window, Ps in (("pkb", range(2, 15, 2)), ("gaussian", range(2, 25, 2))):
+            for P in Ps:
+                plan = plan_for(k, P, window)
+                gg, four, err = [], [], []
+                for (xd, _), fd, ref in zip(sets, fs, refs):
+                    a, b, u = fourier(plan, k, xd, fd, args.exp_reps)
+                    gg.append(a)
+                    four.append(b)
+                    err.append(float(np.sqrt(((u - ref) ** 2).sum() / (ref ** 2).sum())))
+                xi, M = WINDOW_EXP[k]
+                print(json.dumps({"experiment": "window", "D": 3, "kernel": k, "N": N, "xi": xi, "M": M,
+                                  "window": "pkb" if window == "pkb" else "tg", "P": P,
+                                  "grid_gather_ms": float(np.mean(gg)), "fourier_ms": float(np.mean(four)),
+                                  "fourier_rms_rel_err": float(np.mean(err)),
+                                  "fourier_rms": float(np.mean([np.sqrt((r ** 2).sum(axis=-1).mean())
+                                                                for r in refs])),
+                                  "configs": len(sets)}), flush=True)
                 del plan
                 torch.cuda.empty_cache()
     return 0
@@ -456,13 +528,15 @@ def main():
                     help="real-space path: the selection's choice, the dense-block path or per target")
     ap.add_argument("--n-points", type=int, default=None,
                     help="override N of a single-system workload (a smaller case of the same kind)")
-    ap.add_argument("--experiment", choices=["complexity", "time_vs_error"], default=None,
-                    help="the timing experiments of Sec. 5.2 instead of the benchmark line")
+    ap.add_argument("--experiment", choices=["complexity", "time_vs_error", "window"], default=None,
+                    help="the timing experiments of Sec. 5.2 and the window comparison of Sec. 5.3 "
+                         "instead of the benchmark line")
     ap.add_argument("--exp-d", default="3,2,1,0")
-    ap.add_argument("--exp-kernels", default="stokeslet,stresslet")
+    ap.add_argument("--exp-kernels", default="stokeslet,stresslet,rotlet")
     ap.add_argument("--exp-systems", default="uniform,clustered")
     ap.add_argument("--exp-jmax", type=int, default=6)
     ap.add_argument("--exp-reps", type=int, default=3, help="timed evaluations per data point (median)")
+    ap.add_argument("--exp-configs", type=int, default=3, help="point sets averaged per window data point")
     args = ap.parse_args()
     if args.experiment:
         return run_experiment(args)
