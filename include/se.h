@@ -29,6 +29,17 @@
  *                          (both are first derivatives of H: the rotlet is the curl, this the
  *                          gradient), with the same zero-mode convention (3P k = 0 term dropped,
  *                          i.e. tin-foil boundary conditions) and no self or gauge term.
+ *       harmonic potential: strengths [n_rhs][N][1] = q; u = sum q / |x - y| (H = 1/r, Sec.
+ *                          2.1: the electrostatic potential of point charges), ONE output
+ *                          per target: u is [n_rhs][N_t][1]. Ewald screening and the
+ *                          harmonic modified kernels (Eqs. optimal-1p-harmonic,
+ *                          vico-harmonic-0p, and the 2P one of Sec. 3.1); the parameter
+ *                          rules are the rotlet's (Sec. 4). Self term -2 xi/sqrt(pi) q.
+ *                          Zero-mode conventions: 3P zero mean over the cell (for a charged
+ *                          system the constant -pi Q / (xi^2 V), Q = sum q, is added); 2P the
+ *                          k^P = 0 kernel -2 pi |r_3| of App. A (no constant); 1P the k_1 = 0
+ *                          kernel -2 log(rho) of App. B, gauge l_H = 1 (the method's l_H = R
+ *                          result is shifted by -2 log(R) Q / L_1); 0P the plain sum.
  *   - targets == NULL selects the star form (targets = sources, the self interaction
  *     omitted, Eq. periodic-potential-star). With explicit targets, a target that
  *     coincides exactly with a source is treated the same way for that source.
@@ -65,7 +76,7 @@ typedef enum {
   SE_ERR_CAPACITY = -8     /* the request exceeds a fixed capacity (see se_real_noalloc)    */
 } se_status;
 
-enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4, SE_HARMONIC_FIELD = 8 };
+enum { SE_STOKESLET = 1, SE_ROTLET = 2, SE_STRESSLET = 4, SE_HARMONIC_FIELD = 8, SE_HARMONIC = 16 };
 enum { SE_WIN_GAUSSIAN = 0, SE_WIN_KB = 1, SE_WIN_PKB = 2 };
 enum { SE_FP64 = 0, SE_FP32 = 1 };
 /* parts of the decomposition returned by se_eval_parts (bit mask) */
@@ -202,15 +213,16 @@ se_status se_autotune_timed(int periodicity, const double box[3], int kernel_mas
 
 /*
  * Evaluate the potential (Eqs. Dp-ewald-decomp / Dp-ewald-decomp-self).
- *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET, SE_STOKESLET|SE_STRESSLET or
- *                SE_HARMONIC_FIELD.
+ *   kernel_mask  SE_STOKESLET, SE_ROTLET, SE_STRESSLET, SE_STOKESLET|SE_STRESSLET,
+ *                SE_HARMONIC_FIELD or SE_HARMONIC.
  *   n_src, src   device double [n_src][3].
  *   strengths    device [n_rhs][n_src][c], c = 3 (S, Omega), 6 (T), 9 (S|T) or 1 (harmonic
- *                field); float in an
- *                SE_FP32 plan, double in an SE_FP64 plan.
+ *                field, harmonic potential); float in an SE_FP32 plan, double in an SE_FP64
+ *                plan.
  *   n_rhs        number of right-hand sides (strength vectors at the same points), >= 1.
  *   n_tgt, tgt   device double [n_tgt][3], or tgt = NULL for the star form (n_tgt ignored).
- *   u            device [n_rhs][N_t][3] of the plan's precision, overwritten.
+ *   u            device [n_rhs][N_t][3] (SE_HARMONIC: [n_rhs][N_t][1]) of the plan's
+ *                precision, overwritten.
  * Asynchronous on the plan's stream.
  */
 se_status se_eval(se_plan_h plan, int kernel_mask, long long n_src, const double* src,

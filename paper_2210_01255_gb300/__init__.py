@@ -12,7 +12,7 @@ import os
 
 from . import build as _build
 
-STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD = 1, 2, 4, 8
+STOKESLET, ROTLET, STRESSLET, HARMONIC_FIELD, HARMONIC = 1, 2, 4, 8, 16
 WIN_GAUSSIAN, WIN_KB, WIN_PKB = 0, 1, 2
 FP64, FP32 = 0, 1
 PART_REAL, PART_FOURIER, PART_CORR, PART_ALL = 1, 2, 4, 7
@@ -21,7 +21,13 @@ FLAG_TEST_TIMEOUT = 2  # se_opts.flags, testing aid: the tensor-core gridding's 
 FLAG_REAL_BLOCKS = 4  # se_opts.flags: real-space sum with the dense-block path (k_real_blk)
 FLAG_FFT_SIZES = 8  # se_opts.flags: grid extents rounded up to FFT-friendly (7-smooth) multiples of f_M
 KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
-           "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD}
+           "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD,
+           "harmonic": HARMONIC}
+
+
+def out_comps(kernel):
+    """Output components per target and RHS: 1 for the harmonic potential, 3 otherwise."""
+    return 1 if KERNELS.get(kernel, kernel) == HARMONIC else 3
 WINDOWS = {"gaussian": WIN_GAUSSIAN, "kb": WIN_KB, "pkb": WIN_PKB}
 
 SE_OK = 0
@@ -302,7 +308,7 @@ class Plan:
         n_rhs = f3.shape[0]
         nt = x.shape[0] if targets is None else targets.shape[0]
         if out is None:
-            out = torch.empty((n_rhs, nt, 3), dtype=self.dtype, device=x.device)
+            out = torch.empty((n_rhs, nt, out_comps(k)), dtype=self.dtype, device=x.device)
         se_eval_parts(self.handle, k, parts, x.contiguous(), f3.contiguous(), n_rhs,
                       None if targets is None else targets.contiguous(), out)
         return out[0] if single else out

@@ -370,12 +370,12 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
       s = regular_scalar<T>(kernel, kk, a.inv4xi2) * g;
     }
   }
-  const int cin = kernel_comps(kernel);
-  // in place: the 3 outputs of RHS r go to components 3r..3r+2, its inputs are cin r ..;
-  // with cin >= 3 ascending r never overwrites an input still to be read, with cin = 1
-  // descending r does (the buffer holds max(cin, 3) n_rhs components)
+  const int cin = kernel_comps(kernel), no = out_comps(kernel);
+  // in place: the no outputs of RHS r go to components no r .. no r + no - 1, its inputs are
+  // cin r ..; with cin >= no ascending r never overwrites an input still to be read, with
+  // cin < no descending r does (the buffer holds max(cin, no) n_rhs components)
   for (int rr = 0; rr < n_rhs; ++rr) {
-    const int r = cin >= 3 ? rr : n_rhs - 1 - rr;
+    const int r = cin >= no ? rr : n_rhs - 1 - rr;
     T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + idx) * 2;
@@ -395,8 +395,8 @@ __global__ void k_scale3p(ScaleArgs<T> a, int kernel, int n_rhs, T* __restrict__
     } else {
       apply_regular<T>(kernel, s, k0, k1, k2, re, im, ore, oim);
     }
-    for (int j = 0; j < 3; ++j) {
-      const size_t o = (((size_t)(3 * r + j)) * H + idx) * 2;
+    for (int j = 0; j < no; ++j) {
+      const size_t o = (((size_t)(no * r + j)) * H + idx) * 2;
       spec[o] = ore[j];
       spec[o + 1] = oim[j];
     }
@@ -434,7 +434,7 @@ template se_status launch_scale3p<double>(se_plan_t*, int, int, double*, const S
 template <typename T, int NCMAX>
 __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restrict__ perm,
                                                 const int* __restrict__ base, const T* __restrict__ wts,
-                                                const T* __restrict__ F, int nt, int NC, T scale,
+                                                const T* __restrict__ F, int nt, int NC, int no, T scale,
                                                 T* __restrict__ u, long long cst, long long xst) {
   // F: component c at F + c cst, grid point (x, y, z) at x xst + y n2 + z
   __shared__ T s_w[8][3 * MAX_P];
@@ -510,7 +510,7 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
     const int i = perm ? perm[s] : s;
 #pragma unroll
     for (int k = 0; k < NCMAX; ++k)
-      if (k < NC) u[((size_t)(k / 3) * nt + i) * 3 + k % 3] = scale * acc[k];
+      if (k < NC) u[((size_t)(k / no) * nt + i) * no + k % no] = scale * acc[k];
   }
 }
 
@@ -955,9 +955,10 @@ se_status spread_launch(se_plan_t* p, const int* bin_start, const int* base, con
 
 template <typename T, int NC>
 void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, const T* F, int nt, int NCr,
-                   T scale, T* u, long long cst, long long xst) {
+                   int no, T scale, T* u, long long cst, long long xst) {
   ++p->launches;
-  k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, scale, u, cst, xst);
+  k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, no, scale, u, cst,
+                                                        xst);
 }
 
 // u += v elementwise (join of the real-space part computed on the side stream)
@@ -975,7 +976,8 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   const int NT = star ? N : (int)n_tgt;
   const int cin = kernel_comps(kernel);
   const int C = cin * n_rhs;    // spread components
-  const int NC = 3 * n_rhs;     // output components
+  const int NO = out_comps(kernel);
+  const int NC = NO * n_rhs;    // output components
   if (C > MAX_COMP || n_rhs > 16) return SE_ERR_UNSUPPORTED;
   const GridGeom& g = p->geom;
   cudaStream_t st = p->stream;
@@ -1185,13 +1187,15 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
     if (NT > 0) {
       // more than 2 RHS: groups of 6 components (2 RHS) per launch keep the per-lane
       // accumulators in registers (one launch over all 3 n_rhs components halved the rate)
+      // (outputs of one RHS are contiguous per target: a group of 6 components starts at
+      // u + c0 NT whether a RHS has 3 outputs or 1)
       if (NC <= 3) {
-        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, scale, u, ucst, uxst);
+        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, NO, scale, u, ucst, uxst);
       } else {
         const size_t GG = (size_t)ucst;
         for (int c0 = 0; c0 < NC; c0 += 6)
-          gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), scale,
-                              u + (size_t)(c0 / 3) * NT * 3, ucst, uxst);
+          gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), NO,
+                              scale, u + (size_t)c0 * NT, ucst, uxst);
       }
     }
     SE_CUDA(cudaGetLastError());
@@ -1225,6 +1229,8 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   }
   if ((parts & SE_PART_CORR) && (kernel & SE_STOKESLET))
     SE_TRY(gauge_correction<T>(p, strengths, cin, N, n_rhs, NT, u));
+  if ((parts & SE_PART_CORR) && kernel == SE_HARMONIC)
+    SE_TRY(harmonic_constant<T>(p, strengths, N, n_rhs, NT, u));
   stage.mark();  // 8: corrections
   p->timed_pending = p->timers.on;
   p->real_timed = p->timers.on && (parts & SE_PART_REAL) && NT > 0;
@@ -1240,7 +1246,7 @@ extern "C" se_status se_eval_parts(se_plan_h p, int kernel, int parts, long long
   if (n_src < 0 || n_src > 0x7fffffffLL || n_rhs < 1) return SE_ERR_ARG;
   if (tgt && (n_tgt < 0 || n_tgt > 0x7fffffffLL)) return SE_ERR_ARG;
   if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET && kernel != SE_KERNEL_ST &&
-      kernel != SE_HARMONIC_FIELD)
+      kernel != SE_HARMONIC_FIELD && kernel != SE_HARMONIC)
     return SE_ERR_ARG;
   if (parts <= 0 || parts > SE_PART_ALL) return SE_ERR_ARG;
   if (cudaSetDevice(p->device) != cudaSuccess) return SE_ERR_CUDA;
@@ -1267,7 +1273,7 @@ extern "C" se_status se_eval_host(se_plan_h p, int kernel, long long n_src, cons
   const size_t bx = sizeof(double) * 3 * (size_t)n_src;
   const size_t bf = es * cin * (size_t)n_rhs * n_src;
   const size_t bt = star ? 0 : sizeof(double) * 3 * (size_t)NT;
-  const size_t bu = es * 3 * (size_t)n_rhs * NT;
+  const size_t bu = es * out_comps(kernel) * (size_t)n_rhs * NT;
   void *dx, *df, *dt = nullptr, *du;
   SE_TRY(buf(p, "host.x", bx, &dx));
   SE_TRY(buf(p, "host.f", bf, &df));
@@ -1315,9 +1321,10 @@ __global__ void k_scale_strengths(int kernel, const T* __restrict__ f, T* __rest
   fs[i] = lin ? f[i] * s : f[i];
 }
 
-// relative rms over a fixed sample of targets of u2 / s - u (u, u2 host copies, [n_rhs][n][3])
+// relative rms over a fixed sample of targets of u2 / s - u (u, u2 host copies, [n_rhs][n][no])
 template <typename T>
-double rounding_estimate(const std::vector<T>& u, const std::vector<T>& u2, long long n, int n_rhs, double s) {
+double rounding_estimate(const std::vector<T>& u, const std::vector<T>& u2, long long n, int n_rhs, int no,
+                         double s) {
   const long long ns = std::min<long long>(2048, n);
   double num = 0, den = 0;
   unsigned long long r = 0x9E3779B97F4A7C15ull;
@@ -1325,8 +1332,8 @@ double rounding_estimate(const std::vector<T>& u, const std::vector<T>& u2, long
     r = r * 6364136223846793005ull + 1442695040888963407ull;  // a fixed LCG sample of targets
     const long long i = (long long)((r >> 17) % (unsigned long long)n);
     for (int q = 0; q < n_rhs; ++q)
-      for (int j = 0; j < 3; ++j) {
-        const size_t o = ((size_t)q * n + i) * 3 + j;
+      for (int j = 0; j < no; ++j) {
+        const size_t o = ((size_t)q * n + i) * no + j;
         const double a = (double)u[o], b = (double)u2[o] / s;
         num += (b - a) * (b - a);
         den += a * a;
@@ -1351,7 +1358,7 @@ se_status timed_trial(int D, const double* box, int kernel, double Q, long long 
   // device memory of the Fourier part: spread grid, spectrum and output grid
   const size_t G = (size_t)p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
   const size_t es = p->prec == SE_FP32 ? 4 : 8;
-  const size_t C = (size_t)kernel_comps(kernel) * n_rhs, NC = 3 * (size_t)n_rhs;
+  const size_t C = (size_t)kernel_comps(kernel) * n_rhs, NC = (size_t)out_comps(kernel) * n_rhs;
   if (G * (3 * C + NC) * es > mem_cap) {
     se_destroy(p);
     return SE_ERR_NOMEM;
@@ -1373,7 +1380,8 @@ se_status timed_trial(int D, const double* box, int kernel, double Q, long long 
   double est = 0;
   if (s == SE_OK && p->prec == SE_FP32 && fs && u2) {
     const double sc = 1.3;
-    const size_t nf = (size_t)kernel_comps(kernel) * n_rhs * n_src, nu = 3 * (size_t)n_rhs * n_src;
+    const size_t nf = (size_t)kernel_comps(kernel) * n_rhs * n_src;
+    const size_t nu = (size_t)out_comps(kernel) * n_rhs * n_src;
     k_scale_strengths<float><<<grid1d((long long)nf, 256), 256, 0, st>>>(kernel, (const float*)strengths, (float*)fs,
                                                                         nf, (float)sc);
     s = se_eval(p, kernel, n_src, src, fs, n_rhs, 0, nullptr, u2);
@@ -1384,7 +1392,7 @@ se_status timed_trial(int D, const double* box, int kernel, double Q, long long 
           cudaMemcpy(h2.data(), u2, sizeof(float) * nu, cudaMemcpyDeviceToHost) != cudaSuccess)
         s = SE_ERR_CUDA;
       else
-        est = rounding_estimate<float>(h1, h2, n_src, n_rhs, sc);
+        est = rounding_estimate<float>(h1, h2, n_src, n_rhs, out_comps(kernel), sc);
     }
   }
   se_destroy(p);
@@ -1408,7 +1416,7 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   if (!box || !io || !xi_out || !rc_out || !M_out || !P_out || !src || !strengths) return SE_ERR_ARG;
   if (n_src < 1 || n_src > 0x7fffffffLL || n_rhs < 1 || !(tol_rel > 0)) return SE_ERR_ARG;
   if (kernel_mask != SE_STOKESLET && kernel_mask != SE_ROTLET && kernel_mask != SE_STRESSLET &&
-      kernel_mask != SE_KERNEL_ST && kernel_mask != SE_HARMONIC_FIELD)
+      kernel_mask != SE_KERNEL_ST && kernel_mask != SE_HARMONIC_FIELD && kernel_mask != SE_HARMONIC)
     return SE_ERR_ARG;
   // the reference point: the caller's n_rc, or the uniform-case rule's, recovered from its r_c
   double nrc0 = io->n_rc;

@@ -22,14 +22,18 @@ inline int grid1d(long long n, int block) {
 }
 
 // Apply the operator symbol K^(k) of Eqs. (diffop-rel-fourier-1..3) times the real scalar s
-// to the transformed components F (re, im), writing the 3 output components (ore, oim).
+// to the transformed components F (re, im), writing the 3 output components (ore, oim); the
+// harmonic potential's symbol is 1 (one component in, one out).
 // Stresslet components are the symmetric ones in the order 11,22,33,12,13,23.
 template <typename T>
 __device__ __forceinline__ void apply_regular(int kernel, T s, T k0, T k1, T k2, const T* re, const T* im,
                                               T* ore, T* oim) {
   const T kk = k0 * k0 + k1 * k1 + k2 * k2;
   const T kv[3] = {k0, k1, k2};
-  if (kernel == SE_STOKESLET) {
+  if (kernel == SE_HARMONIC) {
+    ore[0] = s * re[0];
+    oim[0] = s * im[0];
+  } else if (kernel == SE_STOKESLET) {
     // (-delta k^2 + k k) F
     const T kfr = k0 * re[0] + k1 * re[1] + k2 * re[2];
     const T kfi = k0 * im[0] + k1 * im[1] + k2 * im[2];
@@ -73,7 +77,7 @@ __device__ __forceinline__ void apply_regular(int kernel, T s, T k0, T k1, T k2,
 }
 
 // Scalar of the regular (unmodified) kernel without the separable factors:
-// H^ = 4 pi / k^2 (rotlet and harmonic field, Ewald screening) or
+// H^ = 4 pi / k^2 (rotlet, harmonic field and potential, Ewald screening) or
 // B^ (1 + k^2/4xi^2) = -8 pi/k^4 (1 + k^2/4xi^2)
 // (stokeslet, stresslet, Hasimoto screening); the exp(-k^2/4xi^2) and 1/w^2 factors are
 // separable and come from the per-direction tables.

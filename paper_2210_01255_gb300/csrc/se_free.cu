@@ -245,7 +245,8 @@ struct FreeScale {
 
 // One kernel's operator on one mode (Eq. SE-scaling-disc): the regular symbol for
 // k^P != 0 (scalar s), the modified kernels of Eqs. (mod-*-2p) / (mod-*-1p) for the k^P = 0
-// class (scalars mr + i mi, and tb = B^ for D = 1). Writes the 3 output components.
+// class (scalars mr + i mi, and tb = B^ for D = 1). Writes the 3 output components (1 for
+// the harmonic potential).
 template <typename T>
 __device__ __forceinline__ void free_mode(const FreeScale& a, int kernel, T s, T k0, T k1, T k2, T mr, T mi, T tb,
                                           const T* re, const T* im, T* ore, T* oim) {
@@ -256,7 +257,12 @@ __device__ __forceinline__ void free_mode(const FreeScale& a, int kernel, T s, T
     // column has only the direction-2 derivative: the rotlet's scalar (the same derivative of
     // the modified harmonic kernel) times (0, 0, q)
     T vr[3], vi[3];
-    if (kernel == SE_HARMONIC_FIELD) {
+    if (kernel == SE_HARMONIC) {
+      // the truncated harmonic kernel itself (its table holds H^_R^{2P} gamma^)
+      vr[0] = re[0]; vi[0] = im[0];
+      vr[1] = 0; vi[1] = 0;
+      vr[2] = 0; vi[2] = 0;
+    } else if (kernel == SE_HARMONIC_FIELD) {
       vr[0] = 0; vi[0] = 0;
       vr[1] = 0; vi[1] = 0;
       vr[2] = re[0]; vi[2] = im[0];
@@ -342,7 +348,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
   if (a.cls == 2 && !in_class(a.m, i0, i1, 2)) return;
   int f0 = nf == 1 ? (int)e : (int)(e / a.fn[1]);
   int f1 = nf == 1 ? 0 : (int)(e % a.fn[1]);
-  const int cin = kernel_comps(kernel);
+  const int cin = kernel_comps(kernel), no = out_comps(kernel);
   // wavenumbers
   bool zero = false;
   T k0, k1, k2;
@@ -391,7 +397,7 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
   const size_t jo = (size_t)j * a.jstr + e;
   // in place, in the order that never overwrites an input still to be read (see k_scale3p)
   for (int rr = 0; rr < n_rhs; ++rr) {
-    const int r = cin >= 3 ? rr : n_rhs - 1 - rr;
+    const int r = cin >= no ? rr : n_rhs - 1 - rr;
     T re[9], im[9];
     for (int c = 0; c < cin; ++c) {
       const size_t o = (((size_t)(cin * r + c)) * H + jo) * 2;
@@ -412,22 +418,23 @@ __global__ void k_scale_free(FreeScale a, int kernel, int n_rhs, const T* __rest
         free_mode<T>(a, kernel, s, k0, k1, k2, mr, mi, tb, re, im, ore, oim);
       }
     }
-    for (int q = 0; q < 3; ++q) {
-      const size_t o = (((size_t)(3 * r + q)) * H + jo) * 2;
+    for (int q = 0; q < no; ++q) {
+      const size_t o = (((size_t)(no * r + q)) * H + jo) * 2;
       spec[o] = ore[q];
       spec[o + 1] = oim[q];
     }
   }
 }
 
-// gauge constants: u[r][i][j] += c_j sum_n f[r][n][j] (f the first 3 of stride components)
+// gauge constants: u[r][i][j] += c_j sum_n f[r][n][j] (f the first nc <= 3 of stride
+// components, u with nc components per target)
 template <typename T>
-__global__ void k_fsum(const T* f, int stride, int n, int n_rhs, double* sums) {
+__global__ void k_fsum(const T* f, int stride, int nc, int n, int n_rhs, double* sums) {
   __shared__ double red[3][256];
   for (int r = 0; r < n_rhs; ++r) {
     double a[3] = {0, 0, 0};
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-      for (int j = 0; j < 3; ++j) a[j] += (double)f[((size_t)r * n + i) * stride + j];
+      for (int j = 0; j < nc; ++j) a[j] += (double)f[((size_t)r * n + i) * stride + j];
     for (int j = 0; j < 3; ++j) red[j][threadIdx.x] = a[j];
     __syncthreads();
     for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -442,12 +449,12 @@ __global__ void k_fsum(const T* f, int stride, int n, int n_rhs, double* sums) {
 }
 
 template <typename T>
-__global__ void k_add_const(int nt, int n_rhs, const double* sums, double c0, double c1, double c2, T* u) {
+__global__ void k_add_const(int nt, int n_rhs, int nc, const double* sums, double c0, double c1, double c2, T* u) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nt) return;
   const double c[3] = {c0, c1, c2};
   for (int r = 0; r < n_rhs; ++r)
-    for (int j = 0; j < 3; ++j) u[((size_t)r * nt + i) * 3 + j] += (T)(c[j] * sums[r * 3 + j]);
+    for (int j = 0; j < nc; ++j) u[((size_t)r * nt + i) * nc + j] += (T)(c[j] * sums[r * 3 + j]);
 }
 
 // ----------------------------------------------------------------------- host side
@@ -565,17 +572,18 @@ se_status free_plan_setup(se_plan_t* p) {
     // k^P = 0 column: modified scalar times gamma^ / w^2 and the normalisation, complex
     const int n0 = p->ncls[0][2];
     const double w00 = window_hat(p->win, 0.0);
-    for (int kind = 0; kind < 3; ++kind) {  // 0: stokeslet, 1: stresslet, 2: rotlet
+    // 0: stokeslet, 1: stresslet, 2: rotlet and harmonic field, 3: harmonic potential
+    for (int kind = 0; kind < 4; ++kind) {
       std::vector<double> t(2 * n0);
       for (int i = 0; i < n0; ++i) {
         int kb = i < n0 / 2 ? i : i - n0;
         double kap = 2.0 * M_PI * kb / (n0 * h);
         double wh = window_hat(p->win, kap);
         double e = std::exp(-kap * kap / (4.0 * p->xi * p->xi));
-        double scr = kind == 2 ? e : e * (1.0 + kap * kap / (4.0 * p->xi * p->xi));
+        double scr = kind >= 2 ? e : e * (1.0 + kap * kap / (4.0 * p->xi * p->xi));
         double norm = scr / (w00 * w00 * w00 * w00 * wh * wh) / ((double)g.m[0] * g.m[1] * n0);
         if (i == n0 / 2) norm = 0;
-        if (kind == 0) {
+        if (kind == 0 || kind == 3) {
           t[2 * i] = hat_H2p(kap, p->R) * norm;
           t[2 * i + 1] = 0;
         } else {
@@ -674,8 +682,9 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   const GridGeom& g = p->geom;
   cudaStream_t st = p->stream;
   const int D = p->D;
-  // k^P = 0 tables of D = 2 per kernel: 0 stokeslet, 1 stresslet, 2 rotlet (S|T: 0 and 1)
-  const int kidx = (kernel & SE_STOKESLET) ? 0 : (kernel == SE_STRESSLET ? 1 : 2);
+  // k^P = 0 tables of D = 2 per kernel: 0 stokeslet, 1 stresslet, 2 rotlet and harmonic
+  // field, 3 harmonic potential (S|T: 0 and 1)
+  const int kidx = kernel == SE_HARMONIC ? 3 : ((kernel & SE_STOKESLET) ? 0 : (kernel == SE_STRESSLET ? 1 : 2));
   // spectrum and class buffers hold the C inputs and, after the in-place scaling, the NC
   // outputs (C < NC for the harmonic field)
   const int CS = std::max(C, NC);
@@ -939,7 +948,7 @@ se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rh
   SE_TRY(buf(p, "gauge.sums", sizeof(double) * 3 * n_rhs, &sums));
   SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 3 * n_rhs, p->stream));
   ++p->launches;
-  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(f, stride, n, n_rhs, (double*)sums);
+  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(f, stride, 3, n, n_rhs, (double*)sums);
   double c[3];
   if (p->D == 0) {
     c[0] = c[1] = c[2] = 2.0 / p->R;
@@ -949,7 +958,27 @@ se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rh
     c[1] = c[2] = -(2.0 * lr + 1.0) / p->L[0];
   }
   ++p->launches;
-  k_add_const<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(nt, n_rhs, (double*)sums, c[0], c[1], c[2], u);
+  k_add_const<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(nt, n_rhs, 3, (double*)sums, c[0], c[1], c[2], u);
+  SE_CUDA(cudaGetLastError());
+  return SE_OK;
+}
+
+// Constants of the harmonic potential: 3P adds -pi Q / (xi^2 V) (the zero-mean potential: the
+// real-space kernel erfc(xi r)/r carries pi / xi^2 of k = 0 content per charge); 1P subtracts
+// 2 log(R) Q / L_0 (the k_1 = 0 class used -2 log(rho / R), the reported gauge is l_H = 1);
+// Q = sum q per right-hand side. 2P and 0P need none.
+template <typename T>
+se_status harmonic_constant(se_plan_t* p, const T* q, int n, int n_rhs, int nt, T* u) {
+  if (!((p->D == 3 || p->D == 1) && n > 0 && nt > 0)) return SE_OK;
+  void* sums;
+  SE_TRY(buf(p, "gauge.sums", sizeof(double) * 3 * n_rhs, &sums));
+  SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 3 * n_rhs, p->stream));
+  ++p->launches;
+  k_fsum<T><<<std::min(grid1d(n, 256), 152), 256, 0, p->stream>>>(q, 1, 1, n, n_rhs, (double*)sums);
+  const double c = p->D == 3 ? -M_PI / (p->xi * p->xi * p->L[0] * p->L[1] * p->L[2])
+                             : -2.0 * std::log(p->R) / p->L[0];
+  ++p->launches;
+  k_add_const<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(nt, n_rhs, 1, (double*)sums, c, 0.0, 0.0, u);
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }
@@ -958,5 +987,7 @@ template se_status fourier_free<float>(se_plan_t*, int, int, float*, int, float*
 template se_status fourier_free<double>(se_plan_t*, int, int, double*, int, double*, int);
 template se_status gauge_correction<float>(se_plan_t*, const float*, int, int, int, int, float*);
 template se_status gauge_correction<double>(se_plan_t*, const double*, int, int, int, int, double*);
+template se_status harmonic_constant<float>(se_plan_t*, const float*, int, int, int, float*);
+template se_status harmonic_constant<double>(se_plan_t*, const double*, int, int, int, double*);
 
 }  // namespace se

@@ -198,7 +198,7 @@ extern "C" se_status se_autotune(int D, const double box[3], int kernel_mask, do
   for (int i = 0; i < 3; ++i)
     if (!(box[i] > 0) || !std::isfinite(box[i])) return SE_ERR_ARG;
   if (!(Q > 0)) return SE_ERR_ARG;
-  if (kernel_mask & ~15) return SE_ERR_ARG;
+  if (kernel_mask & ~31) return SE_ERR_ARG;
   // the harmonic field takes the rotlet's rules (both are first derivatives of H)
   const int rmask = rule_mask(kernel_mask);
   int kernels[3], nk = 0;

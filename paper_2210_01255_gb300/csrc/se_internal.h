@@ -26,18 +26,23 @@ constexpr int SE_KERNEL_ST = SE_STOKESLET | SE_STRESSLET;
 // strength components per point and right-hand side, which is also the number of spread
 // components: f (3); (q, nu) (6, spread as the 6 symmetric q nu^T entries); (f, q, nu) (9)
 __host__ __device__ inline int kernel_comps(int kernel) {
-  return kernel == SE_STRESSLET ? 6 : (kernel == SE_KERNEL_ST ? 9 : (kernel == SE_HARMONIC_FIELD ? 1 : 3));
+  return kernel == SE_STRESSLET ? 6
+         : (kernel == SE_KERNEL_ST ? 9 : ((kernel == SE_HARMONIC_FIELD || kernel == SE_HARMONIC) ? 1 : 3));
 }
 
-// the harmonic field is a first derivative of the harmonic kernel like the rotlet: it takes
-// the rotlet's parameter rules (Sec. 4), screening (Ewald) and modified-kernel tables
+// output components per target and right-hand side: the harmonic potential is a scalar
+__host__ __device__ inline int out_comps(int kernel) { return kernel == SE_HARMONIC ? 1 : 3; }
+
+// the harmonic field (a first derivative of the harmonic kernel like the rotlet) and the
+// harmonic potential take the rotlet's parameter rules (Sec. 4), the Ewald screening and the
+// harmonic modified-kernel tables
 __host__ __device__ inline bool harmonic_family(int kernel) {
-  return kernel == SE_ROTLET || kernel == SE_HARMONIC_FIELD;
+  return kernel == SE_ROTLET || kernel == SE_HARMONIC_FIELD || kernel == SE_HARMONIC;
 }
 
-// a kernel mask with the harmonic field's rules entered as the rotlet's
+// a kernel mask with the harmonic field's and potential's rules entered as the rotlet's
 __host__ __device__ inline int rule_mask(int mask) {
-  return (mask & 7) | ((mask & SE_HARMONIC_FIELD) ? SE_ROTLET : 0);
+  return (mask & 7) | ((mask & (SE_HARMONIC_FIELD | SE_HARMONIC)) ? SE_ROTLET : 0);
 }
 
 // Geometry of the grid that gridding writes and gathering reads (Sec. 3.2).
@@ -121,7 +126,7 @@ struct se_plan_t {
   int ncls[3][3] = {};     // [class][direction] transform lengths in the free directions
   se::DevBuf ptab[3];      // periodic-direction factors exp(-k^2/4xi^2) / w^2 / n
   se::DevBuf ftab[3][3];   // [class][direction] free-direction factors
-  se::DevBuf mod0[3];      // k^P = 0 modified-kernel tables
+  se::DevBuf mod0[4];      // k^P = 0 modified-kernel tables
   se::DevBuf atr[2];       // D = 0 precomputed kernels: 0 harmonic, 1 biharmonic
 
   se::Timers timers;
@@ -172,6 +177,8 @@ template <typename T>
 se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);
 template <typename T>
 se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rhs, int nt, T* u);
+template <typename T>
+se_status harmonic_constant(se_plan_t* p, const T* q, int n, int n_rhs, int nt, T* u);
 double pot_mag(int kernel, double L, double Q, double xi);
 double lambda_table(int kernel, int D);
 void upsampling_rule(int D, const double* box, double h, const int* Mext, double lg, double* s_star,

@@ -59,6 +59,11 @@ template <typename T, int KERNEL, int RMAX>
 __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, T c2pi, const T* __restrict__ f,
                                           int n_rhs, T* acc) {
   if (rr2 == T(0)) {
+    if (KERNEL == SE_HARMONIC) {
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r)
+        if (r < n_rhs) acc[r] -= c2pi * f[r];  // -2 xi / sqrt(pi) q
+    }
     if (KERNEL == SE_STOKESLET || KERNEL == SE_KERNEL_ST) {
       const T cs = -T(2) * c2pi;  // -4 xi / sqrt(pi), Eq. (3p-stokeslet-self-term)
       constexpr int STRIDE = KERNEL == SE_KERNEL_ST ? 9 : 3;
@@ -74,7 +79,12 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
   const T inv2 = inv * inv;
   const T e = gauss(-xi2 * rr2);
   const T ec = dev_erfc_g(xi * rn, e) * inv;
-  if (KERNEL == SE_STOKESLET) {
+  if (KERNEL == SE_HARMONIC) {
+    // the Ewald-screened harmonic kernel erfc(xi r) / r times q (one output per RHS)
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+      if (r < n_rhs) acc[r] += ec * f[r];
+  } else if (KERNEL == SE_STOKESLET) {
     // Eq. (stokeslet-real): (delta + r r / r^2)(erfc/r + 2 xi e/sqrt pi) - delta 4 xi e/sqrt pi
     const T c1 = ec + c2pi * e;
     const T c0 = c1 - T(2) * c2pi * e;
@@ -159,7 +169,8 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
 // The pair terms of real_pair without branches, for a pair that may or may not count: the
 // radial coefficients are formed from a safe r^2 and then kept (a pair inside r_c at r > 0),
 // replaced by the self term (r = 0, the omitted star-sum term: the stokeslet's -4 xi/sqrt(pi)
-// f, nothing for the other kernels) or zeroed (outside r_c). Same arithmetic as real_pair for
+// f, the harmonic potential's -2 xi/sqrt(pi) q, nothing for the other kernels) or zeroed
+// (outside r_c). Same arithmetic as real_pair for
 // a pair that counts; with no branch, the terms of two candidates interleave (k_real_blk).
 template <typename T, int KERNEL, int RMAX>
 __device__ __forceinline__ void real_pair_m(T r0, T r1, T r2, T rr2, bool inside, T xi, T xi2, T c2pi,
@@ -188,6 +199,12 @@ __device__ __forceinline__ void real_pair_m(T r0, T r1, T r2, T rr2, bool inside
         acc[3 * r + 2] += c0 * fr[2] + r2 * rf;
       }
     }
+  }
+  if (KERNEL == SE_HARMONIC) {
+    const T c0 = reg ? ec : (self ? -c2pi : T(0));
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+      if (r < n_rhs) acc[r] += c0 * f[r];
   }
   if (KERNEL == SE_HARMONIC_FIELD || KERNEL == SE_ROTLET) {
     const T c1 = reg ? (ec + c2pi * e) * inv2 : T(0);
@@ -275,8 +292,15 @@ __device__ __forceinline__ int wrap_cell(int u, int n, int* im) {
   return u;
 }
 
+// outputs per target and RHS (the harmonic potential is a scalar)
+template <int KERNEL>
+struct RsOut {
+  static constexpr int value = KERNEL == SE_HARMONIC ? 1 : 3;
+};
+
 template <typename T, int KERNEL, int RMAX>
 __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
+  constexpr int NO = RsOut<KERNEL>::value;
   __shared__ RealSmem<T> sm_all[RS_WARPS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int s = blockIdx.x * RS_WARPS + warp;
@@ -295,9 +319,9 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
   const int nc = kernel_comps(KERNEL);
   const int C = nc * a.n_rhs;
-  T acc[3 * RMAX];
+  T acc[NO * RMAX];
 #pragma unroll
-  for (int k = 0; k < 3 * RMAX; ++k) acc[k] = T(0);
+  for (int k = 0; k < NO * RMAX; ++k) acc[k] = T(0);
   const T xi = a.xi;
   const T xi2 = xi * xi;
   const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
@@ -465,7 +489,7 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   }
   if (tail != head) flush((int)(tail - head));
 #pragma unroll
-  for (int k = 0; k < 3 * RMAX; ++k) {
+  for (int k = 0; k < NO * RMAX; ++k) {
     T v = acc[k];
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
@@ -474,9 +498,9 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   if (lane == 0) {
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-      for (int qq = 0; qq < 3; ++qq) {
-        T* o = a.u + ((size_t)r * a.ntgt + i) * 3 + qq;
-        *o = a.overwrite ? acc[3 * r + qq] : *o + acc[3 * r + qq];
+      for (int qq = 0; qq < NO; ++qq) {
+        T* o = a.u + ((size_t)r * a.ntgt + i) * NO + qq;
+        *o = a.overwrite ? acc[NO * r + qq] : *o + acc[NO * r + qq];
       }
   }
 }
@@ -529,7 +553,7 @@ struct BlkSmem {
 template <int KERNEL, int RMAX>
 struct BlkComps {
   static constexpr int c = KERNEL == SE_STRESSLET ? 6 : (KERNEL == (SE_STOKESLET | SE_STRESSLET) ? 9
-                           : (KERNEL == SE_HARMONIC_FIELD ? 1 : 3));
+                           : ((KERNEL == SE_HARMONIC_FIELD || KERNEL == SE_HARMONIC) ? 1 : 3));
   static constexpr int cp = (c * RMAX + 3) & ~3;
 };
 
@@ -537,6 +561,7 @@ template <typename T, int KERNEL, int RMAX>
 __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const int* __restrict__ blist,
                                                             const int* __restrict__ bcount) {
   constexpr int CP = BlkComps<KERNEL, RMAX>::cp;
+  constexpr int NO = RsOut<KERNEL>::value;
   __shared__ __align__(16) BlkSmem<T, CP> sm_all[RB_WARPS];
   typedef typename Vec4<T>::type V4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -580,9 +605,9 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
   const int ncx = uhi[0] - ulo[0] + 1, ncy = uhi[1] - ulo[1] + 1;
   const int ncol = max(0, ncx) * max(0, ncy);
   const int maxseg = a.maxseg, cpr = a.cols_per_round;
-  T acc[3 * RMAX], cmp[3 * RMAX];
+  T acc[NO * RMAX], cmp[NO * RMAX];
 #pragma unroll
-  for (int k = 0; k < 3 * RMAX; ++k) acc[k] = cmp[k] = T(0);
+  for (int k = 0; k < NO * RMAX; ++k) acc[k] = cmp[k] = T(0);
   const T xi = a.xi, xi2 = xi * xi;
   const T c2pi = T(2.0 / 1.7724538509055160273) * xi;  // 2 xi / sqrt(pi)
   for (int c0 = 0; c0 < ncol; c0 += cpr) {
@@ -685,9 +710,9 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
       __syncwarp();
       if (b0 + 32 < total) fetch(b0 + 32);  // in flight while this chunk is evaluated
       const int cnt = min(32, total - b0);
-      T part[3 * RMAX];
+      T part[NO * RMAX];
 #pragma unroll
-      for (int q = 0; q < 3 * RMAX; ++q) part[q] = T(0);
+      for (int q = 0; q < NO * RMAX; ++q) part[q] = T(0);
       // two staged candidates at a time, their pair terms without branches (real_pair_m)
       // so that the two evaluations interleave; a pair of candidates that no lane needs is
       // skipped (warp-uniform). Unused staging slots hold a far position (never inside).
@@ -713,7 +738,7 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
       }
       // fold the chunk into the sums (compensated in FP32)
 #pragma unroll
-      for (int q = 0; q < 3 * RMAX; ++q) {
+      for (int q = 0; q < NO * RMAX; ++q) {
         if (sizeof(T) == 4) {
           const T y = part[q] - cmp[q];
           const T t = acc[q] + y;
@@ -728,9 +753,9 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
   if (tv) {
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
-      for (int q = 0; q < 3; ++q) {
-        T* o = a.u + ((size_t)r * a.ntgt + i) * 3 + q;
-        *o = a.overwrite ? acc[3 * r + q] : *o + acc[3 * r + q];
+      for (int q = 0; q < NO; ++q) {
+        T* o = a.u + ((size_t)r * a.ntgt + i) * NO + q;
+        *o = a.overwrite ? acc[NO * r + q] : *o + acc[NO * r + q];
       }
   }
 }
@@ -783,6 +808,7 @@ static void launch_sparse(cudaStream_t st, const RealArgs<T>& a) {
   else if (a.kernel == SE_ROTLET) launch_sparse_k<T, SE_ROTLET, R>(st, a);
   else if (a.kernel == SE_STRESSLET) launch_sparse_k<T, SE_STRESSLET, R>(st, a);
   else if (a.kernel == SE_HARMONIC_FIELD) launch_sparse_k<T, SE_HARMONIC_FIELD, R>(st, a);
+  else if (a.kernel == SE_HARMONIC) launch_sparse_k<T, SE_HARMONIC, R>(st, a);
   else launch_sparse_k<T, SE_STOKESLET | SE_STRESSLET, R>(st, a);
 }
 
@@ -805,6 +831,7 @@ static void launch_blk(cudaStream_t st, const RealArgs<T>& a, const int* blist, 
   else if (a.kernel == SE_ROTLET) launch_blk_k<T, SE_ROTLET, R>(st, a, blist, bcount, nblk);
   else if (a.kernel == SE_STRESSLET) launch_blk_k<T, SE_STRESSLET, R>(st, a, blist, bcount, nblk);
   else if (a.kernel == SE_HARMONIC_FIELD) launch_blk_k<T, SE_HARMONIC_FIELD, R>(st, a, blist, bcount, nblk);
+  else if (a.kernel == SE_HARMONIC) launch_blk_k<T, SE_HARMONIC, R>(st, a, blist, bcount, nblk);
   else launch_blk_k<T, SE_STOKESLET | SE_STRESSLET, R>(st, a, blist, bcount, nblk);
 }
 

@@ -41,7 +41,7 @@ def two_cube_points(n, seed):
 def strengths(kernel, n, seed, n_rhs=None):
     """Stokeslet / rotlet: f ~ N(0,1)^3. Stresslet: (q, nu) with q ~ N(0,1)^3 and nu ~ N(0,1)^3
     normalised to unit length. Stokeslet + stresslet: (f, q, nu), f drawn first. Harmonic
-    field: charges q ~ N(0,1).
+    field and harmonic potential: charges q ~ N(0,1).
     Shape (n, c) or (n_rhs, n, c)."""
     rng = np.random.default_rng(seed)
     shape = (n,) if n_rhs is None else (n_rhs, n)
@@ -51,7 +51,7 @@ def strengths(kernel, n, seed, n_rhs=None):
         nu = rng.standard_normal(shape + (3,))
         nu /= np.linalg.norm(nu, axis=-1, keepdims=True)
         return np.concatenate([f, q, nu], axis=-1)
-    if kernel in ("harmonic_field", 8):
+    if kernel in ("harmonic_field", 8, "harmonic", 16):
         return rng.standard_normal(shape + (1,))
     if kernel in ("stresslet", 4):
         q = rng.standard_normal(shape + (3,))

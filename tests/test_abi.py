@@ -97,18 +97,20 @@ def test_autotune_reproduces_clustered_xi_from_n_rc(key):
 
 @pytest.mark.parametrize("D", [3, 2, 1, 0])
 def test_harmonic_field_takes_the_rotlet_rules(D):
-    """The harmonic field (a first derivative of H like the rotlet) gets the rotlet's
-    parameters and extended-grid options; unknown mask bits are rejected."""
+    """The harmonic field (a first derivative of H like the rotlet) and the harmonic
+    potential get the rotlet's parameters and extended-grid options; unknown mask bits are
+    rejected."""
     res = []
-    for mask in (se.HARMONIC_FIELD, se.ROTLET, se.HARMONIC_FIELD | se.ROTLET):
+    for mask in (se.HARMONIC_FIELD, se.ROTLET, se.HARMONIC_FIELD | se.ROTLET, se.HARMONIC,
+                 se.HARMONIC | se.HARMONIC_FIELD):
         o = se.se_opts_default()
         o.tol_abs = 1e-8
         r = se.se_autotune(D, (1, 1, 1), mask, 1.0, 20000, 0.0, opts=o)
         res.append((r["xi"], r["rc"], tuple(r["M"]), r["P"], tuple(r["opts"].Mext), r["opts"].s0,
                     r["opts"].s_star, r["opts"].kbar_star))
-    assert res[0] == res[1] == res[2]
+    assert res[0] == res[1] == res[2] == res[3] == res[4]
     with pytest.raises(se.SeError) as e:
-        se.se_autotune(D, (1, 1, 1), 16, 1.0, 20000, 1e-6)
+        se.se_autotune(D, (1, 1, 1), 32, 1.0, 20000, 1e-6)
     assert e.value.code == -1
 
 

@@ -59,7 +59,8 @@ CASES = [(3, (1.0, 1.0, 1.0), (32, 32, 32)), (2, (1.0, 1.0, 0.5), (32, 32, 16)),
 
 
 @pytest.mark.parametrize("case", range(len(CASES)))
-@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet", "stresslet", "stokeslet+stresslet", "harmonic_field"])
+@pytest.mark.parametrize("kernel", ["stokeslet", "rotlet", "stresslet", "stokeslet+stresslet", "harmonic_field",
+                                    "harmonic"])
 @pytest.mark.parametrize("prec,bar", [("fp64", 1e-13), ("fp32", 2e-6)])
 def test_blocks_equal_per_target_path(case, kernel, prec, bar):
     D, box, M = CASES[case]
