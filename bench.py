@@ -218,7 +218,7 @@ def make_plan(cfg, item, prec, stream, flags=0):
     import paper_2210_01255_gb300 as se_
     t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
     # the gridding choice of the command line; the real-space path the selection chose
-    o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES))
+    o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES | se_.FLAG_SPLIT_POLY))
     if REAL_PATH == "blocks":
         o.flags |= se_.FLAG_REAL_BLOCKS
     elif REAL_PATH == "target":
@@ -802,7 +802,10 @@ def main():
                                      "autotune": cfg.get("autotune", "rules"),
                                      "timed_ms": [it["tune"].get("ms") for it in items[:4]],
                                      "real_space_path": ["dense blocks" if it["tune"]["opts"].flags & se.FLAG_REAL_BLOCKS
-                                                         else "per target" for it in items[:4]]},
+                                                         else "per target" for it in items[:4]],
+                                     "gridding_tile": ["4x4x%d" % it["tune"]["opts"].tile if it["tune"]["opts"].tile
+                                                       else "default (4x4x4 for 7-12 components, else 4x4x8)"
+                                                       for it in items[:4]]},
                        "targets_per_step": targets_per_step, "l2": "flushed between steps (256 MB write)",
                        "gridding": "tcgen05" if args.gridding == "tc" else "cuda cores",
                        "parallelism": "replicas" if world > 1 else "single"},

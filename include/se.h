@@ -101,6 +101,11 @@ typedef struct {
   int P_margin;      /* se_autotune: window points added to the estimate of Eq.
                         (approximation-estimate) by the error-pollution rule, Eq.
                         (error-pollution-fix); -1 = the paper's (4, or 2 for D = 0)          */
+  int tile;          /* gridding tile depth TZ along direction 2 (CUDA-core gridding works on
+                        tiles of 4 x 4 x TZ grid points, one warp each): 0 = by the number of
+                        components per launch (4 for 9-12, 8 for fewer), 4 or 8 forced (a
+                        launch of 10-12 components always takes 4); se_autotune_timed
+                        chooses it by timing. Same grid to rounding.                     */
 } se_opts;
 
 /* se_opts.flags: with SE_FLAG_TC_GRIDDING, FP32 gridding (Alg. 1, gridding step) with window
@@ -131,6 +136,18 @@ enum { SE_FLAG_REAL_BLOCKS = 4 };
  * grid only gets finer (h smaller), so the tolerance rules still hold. Without the flag the
  * sizes are the paper's multiples of f_M. */
 enum { SE_FLAG_FFT_SIZES = 8 };
+/* se_opts.flags: for D = 0, the precomputed truncated biharmonic kernel (stokeslet,
+ * stresslet; Sec. 3.5) is split as (B_R - p) + p with p(r) = c0 + c1 r^2 + c2 r^4 the least-
+ * squares fit of B_R over the 2M' box of offsets (FP64, at plan creation). The Fourier-space
+ * step uses B_R - p; the potential of p is added exactly from FP64 moment sums of the sources
+ * (the operators of the stokeslet and stresslet turn p into polynomials of degree 2 and 1 in
+ * x - y; the Hasimoto screening leaves p unchanged up to a constant that they annihilate).
+ * The potential is the same to the truncation error of the method, but the large values of
+ * the truncated biharmonic at small wavenumbers, which multiply the FP32 rounding of the
+ * transforms, shrink: in FP32 the rounding of the free-space Fourier part approaches that of
+ * the triply periodic one. Rotlet and harmonic kernels are unaffected.
+ * se_autotune_timed sets it for D = 0 FP32 stokeslet / stresslet evaluations. */
+enum { SE_FLAG_SPLIT_POLY = 16 };
 
 /* Fill *opts with the defaults above. */
 se_status se_opts_default(se_opts* opts);
@@ -187,7 +204,10 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * memory, or its grid is unsupported. The real-space path is chosen the same way: both the
  * per-target and the dense-block path (SE_FLAG_REAL_BLOCKS) are timed at the first candidate,
  * the faster is used along the walk, both are timed again at the chosen r_c, and the choice is
- * returned in io_opts->flags (the other flags are kept as given). FP32 trials also bound the
+ * returned in io_opts->flags (the other flags are kept as given; for D = 0 FP32 stokeslet and
+ * stresslet evaluations SE_FLAG_SPLIT_POLY is added). Last, the gridding tile depth
+ * (io_opts->tile = 4 and 8, CUDA-core gridding) is timed at the chosen parameters and the
+ * fastest of the two and the caller's own value is returned in io_opts->tile. FP32 trials also bound the
  * rounding: each candidate evaluates once more with the linear part of the strengths scaled
  * by 1.3 (f, the stresslet's q, the charges), and the relative rms of u(1.3 f)/1.3 - u(f) over
  * a fixed sample of 2048 targets estimates its rounding. A candidate whose estimate exceeds

@@ -697,6 +697,7 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
   se_opts_default(&o);
   if (opts) o = *opts;
   if (o.prec != SE_FP64 && o.prec != SE_FP32) return SE_ERR_ARG;
+  if (o.tile != 0 && o.tile != 4 && o.tile != 8) return SE_ERR_ARG;
 
   se_plan_t* p = new (std::nothrow) se_plan_t();
   if (!p) return SE_ERR_NOMEM;
@@ -1199,6 +1200,8 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       }
     }
     SE_CUDA(cudaGetLastError());
+    // the polynomial taken out of the free-space biharmonic (SE_FLAG_SPLIT_POLY), added back
+    SE_TRY(poly_correction<T>(p, kernel, src, strengths, N, n_rhs, star ? src : tgt, NT, u));
     stage.mark();  // 6: gather
   } else {
     for (int i = 0; i < 6; ++i) stage.mark();
@@ -1451,6 +1454,10 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
     return timed_trial(D, box, kernel_mask, Q, n_src, src, strengths, n_rhs, tol_rel, window, *io,
                        nrc0 * f * f * f, mem_cap, u, fs, u2, e0, e1, c);
   };
+  // FP32 free-space stokeslet / stresslet: the truncated biharmonic with its fitted polynomial
+  // taken out (SE_FLAG_SPLIT_POLY), which keeps the transforms' rounding from being amplified
+  if (D == 0 && io->prec == SE_FP32 && (kernel_mask & (SE_STOKESLET | SE_STRESSLET)))
+    io->flags |= SE_FLAG_SPLIT_POLY;
   // the real-space path (per-target k_real, or the dense-block path) is a choice too: both
   // are timed at f = 1, the faster is kept for the walk over r_c and both are timed again at
   // the chosen r_c
@@ -1528,6 +1535,21 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   if (st == SE_OK && best.f != 1.0) {  // both real-space paths at the chosen r_c
     TimedCand c;
     if (run_both(best.f, &c) == SE_OK && ok(c) && c.ms < best.ms) best = c;
+  }
+  // the gridding tile depth (4 x 4 x TZ tiles, TZ = 4 or 8) at the chosen parameters, unless
+  // the gridding runs on the tensor cores
+  if (st == SE_OK && !(io->prec == SE_FP32 && (io->flags & SE_FLAG_TC_GRIDDING))) {
+    se_opts keep = *io;
+    TimedCand pick = best;  // the caller's tile (0: the per-launch default) as timed above
+    for (int tz : {4, 8}) {
+      *io = keep;
+      io->flags = best.o.flags;
+      io->tile = tz;
+      TimedCand c;
+      if (run(best.f, &c) == SE_OK && ok(c) && c.ms < pick.ms) pick = c;
+    }
+    *io = keep;
+    best = pick;
   }
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);

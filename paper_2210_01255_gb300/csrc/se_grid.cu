@@ -1,8 +1,9 @@
 // libse gridding step, Eq. (SE-gridding-disc): H(x_j) = sum_n f_n w(x_j - x_n) on the uniform
 // grid, with the separable window w = w0 w0 w0 (Sec. 3.3) of support P grid points per direction.
 //
-// Output-driven, one warp per tile of 4 x 4 x TZ grid points (TZ = 4 for 9-12 components, 8
-// for fewer), no atomics for all but the densest tiles:
+// Output-driven, one warp per tile of 4 x 4 x TZ grid points (by default TZ = 4 for 9-12
+// components, 8 for fewer; se_opts.tile forces either where the register block fits), no
+// atomics for all but the densest tiles:
 //   candidates  points are sorted by bins of 4^3 cells (z fastest), so the bins of one (x, y)
 //               bin column that can reach the tile are one contiguous run of points; the runs are
 //               set up one per lane and laid out as a flat list by a warp scan; each lane tests
@@ -402,11 +403,24 @@ se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const
     a.c0 = c0;
     a.C = Cg;
     SE_CUDA(cudaMemsetAsync(a.qcount, 0, sizeof(int), st));
+    // tile depth: the plan's choice, else 4 for 7-12 components and 8 for fewer; 10-12
+    // components always take 4 (a 2 x 2 x 12 register block with its compensation and chunk
+    // partials would not fit the register file)
+    const int tz = Cg > 9 ? 4 : (p->opts.tile ? p->opts.tile : (Cg > 6 ? 4 : 8));
     if (Cg > 9) launch_grid<T, 4, 1, 12>(st, a, w, sf, grid, &p->launches);
-    else if (Cg > 6) launch_grid<T, 4, 1, 9>(st, a, w, sf, grid, &p->launches);
-    else if (Cg > 3) launch_grid<T, 8, 2, 6>(st, a, w, sf, grid, &p->launches);
-    else if (Cg > 1) launch_grid<T, 8, 2, 3>(st, a, w, sf, grid, &p->launches);
-    else launch_grid<T, 8, 2, 1>(st, a, w, sf, grid, &p->launches);
+    else if (Cg > 6) {
+      if (tz == 4) launch_grid<T, 4, 1, 9>(st, a, w, sf, grid, &p->launches);
+      else launch_grid<T, 8, 2, 9>(st, a, w, sf, grid, &p->launches);
+    } else if (Cg > 3) {
+      if (tz == 4) launch_grid<T, 4, 1, 6>(st, a, w, sf, grid, &p->launches);
+      else launch_grid<T, 8, 2, 6>(st, a, w, sf, grid, &p->launches);
+    } else if (Cg > 1) {
+      if (tz == 4) launch_grid<T, 4, 1, 3>(st, a, w, sf, grid, &p->launches);
+      else launch_grid<T, 8, 2, 3>(st, a, w, sf, grid, &p->launches);
+    } else {
+      if (tz == 4) launch_grid<T, 4, 1, 1>(st, a, w, sf, grid, &p->launches);
+      else launch_grid<T, 8, 2, 1>(st, a, w, sf, grid, &p->launches);
+    }
     SE_CUDA(cudaGetLastError());
   }
   return SE_OK;

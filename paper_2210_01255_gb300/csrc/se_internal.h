@@ -128,6 +128,8 @@ struct se_plan_t {
   se::DevBuf ftab[3][3];   // [class][direction] free-direction factors
   se::DevBuf mod0[4];      // k^P = 0 modified-kernel tables
   se::DevBuf atr[2];       // D = 0 precomputed kernels: 0 harmonic, 1 biharmonic
+  double poly_c[3] = {0, 0, 0};  // SE_FLAG_SPLIT_POLY: c0 + c1 r^2 + c2 r^4 taken out of B_R
+  bool poly_on = false;
 
   se::Timers timers;
   float times_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -179,6 +181,9 @@ template <typename T>
 se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rhs, int nt, T* u);
 template <typename T>
 se_status harmonic_constant(se_plan_t* p, const T* q, int n, int n_rhs, int nt, T* u);
+template <typename T>
+se_status poly_correction(se_plan_t* p, int kernel, const double* x, const T* f, int n, int n_rhs, const double* t,
+                          int nt, T* u);
 double pot_mag(int kernel, double L, double Q, double xi);
 double lambda_table(int kernel, int D);
 void upsampling_rule(int D, const double* box, double h, const int* Mext, double lg, double* s_star,

@@ -54,6 +54,12 @@ def test_plan_argument_validation_without_gpu():
         with pytest.raises(se.SeError) as e:
             se.se_plan_create(*args)
         assert e.value.code == -1
+    o = se.se_opts_default()
+    assert o.tile == 0
+    o.tile = 6                                                     # tile depth: 0, 4 or 8
+    with pytest.raises(se.SeError) as e:
+        se.se_plan_create(3, (1, 1, 1), 10.0, 0.3, (32, 32, 32), 8, 2, o)
+    assert e.value.code == -1
 
 
 # Table 6 of the paper (uniform system): xi from the neighbour count of Table 5 at N = 1e5,

@@ -79,3 +79,30 @@ def test_fp32_grid_keeps_fp32_accuracy_on_a_dense_cluster():
     g64 = gpu_grid(x, f, "stokeslet", M, P, "fp64")
     g32 = gpu_grid(x, f, "stokeslet", M, P, "fp32")
     assert np.abs(g32 - g64).max() <= 1e-6 * np.abs(g64).max()
+
+
+@pytest.mark.parametrize("prec,bar", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("kernel,n_rhs", [("harmonic_field", 1), ("stokeslet", 1), ("stresslet", 1),
+                                          ("stokeslet+stresslet", 1), ("stokeslet", 4)])
+def test_tile_depths_give_the_same_grid(kernel, n_rhs, prec, bar):
+    """se_opts.tile = 4 and 8 (4 x 4 x TZ tiles) against the default choice, for 1, 3, 6, 9 and
+    12 components per launch (12: always TZ = 4), on clustered points with split tiles."""
+    M, P = 34, 8
+    x = np.concatenate([tight_cluster(20000, seed=8), W.uniform_points(4000, (1, 1, 1), seed=9)])
+    f = W.strengths(kernel, x.shape[0], seed=10, n_rhs=None if n_rhs == 1 else n_rhs)
+    grids = []
+    for tile in (0, 4, 8):
+        o = se.se_opts_default()
+        o.kernel_mask = se.KERNELS[kernel]
+        o.tile = tile
+        plan = se.Plan(3, (1, 1, 1), 8.0, 0.3, (M, M, M), P, "pkb", prec, opts=o)
+        plan.evaluate(kernel, torch.tensor(x, device="cuda"), torch.tensor(f, dtype=plan.dtype, device="cuda"),
+                      parts=se.PART_FOURIER)
+        plan.sync()
+        C = (1 if kernel == "harmonic_field" else 3 if kernel == "stokeslet" else 6 if kernel == "stresslet" else 9)
+        g = np.zeros((C * n_rhs, M, M, M), dtype=np.float32 if prec == "fp32" else np.float64)
+        se.se_debug_grid(plan.handle, g)
+        grids.append(g.astype(np.float64))
+    scale = np.abs(grids[0]).max()
+    assert np.abs(grids[1] - grids[0]).max() <= bar * scale
+    assert np.abs(grids[2] - grids[0]).max() <= bar * scale
