@@ -197,6 +197,8 @@ def tuned(cfg, item, prec, stream, flags=0):
             t0 = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o0)
             o.n_rc = 4.0 / 3.0 * math.pi * t0["rc"] ** 3 * item["N"] / float(np.prod(cfg["box"])) * NRC_SCALE ** 3
             t = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
+            if cfg["D"] == 0 and prec == "fp32" and se.KERNELS[k] & (se.STOKESLET | se.STRESSLET):
+                t["opts"].flags |= se.FLAG_SPLIT_POLY   # as the timed selection does
         elif cfg.get("autotune") == "timed":
             o.flags |= flags
             t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
