@@ -199,9 +199,10 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * ladder f = 0.8^k around 1 (starting from io_opts->n_rc, or from the uniform rule when it is
  * 0), se_autotune gives each candidate's parameters, and a plan of each candidate evaluates
  * the caller's own sources and strengths (star form) once untimed and twice timed with CUDA
- * events; the walk continues in the improving direction until two candidates are more than
- * 10 % slower than the best, a candidate's grids would use more than half of the free device
- * memory, or its grid is unsupported. The real-space path is chosen the same way: both the
+ * events; the first step decides the direction (towards the faster), and the walk continues
+ * until two candidates in a row are invalid (FP32 rounding, below) or more than 10 % slower
+ * than the best, a candidate's grids would use more than half of the free device memory, or
+ * its grid is unsupported. The real-space path is chosen the same way: both the
  * per-target and the dense-block path (SE_FLAG_REAL_BLOCKS) are timed at the first candidate,
  * the faster is used along the walk, both are timed again at the chosen r_c, and the choice is
  * returned in io_opts->flags (the other flags are kept as given; for D = 0 FP32 stokeslet and
@@ -211,7 +212,8 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * rounding: each candidate evaluates once more with the linear part of the strengths scaled
  * by 1.3 (f, the stresslet's q, the charges), and the relative rms of u(1.3 f)/1.3 - u(f) over
  * a fixed sample of 2048 targets estimates its rounding. A candidate whose estimate exceeds
- * 3.5 tol_rel is not chosen (the FP32 rounding of the free-space transforms grows with xi,
+ * 3.5 tol_rel is not chosen (the estimate varies between repeated trials by about 2x, so it
+ * decides eligibility, not the direction of the walk) (the FP32 rounding of the free-space transforms grows with xi,
  * so large grids can cost more accuracy than the truncation rules allow); if no candidate
  * passes, SE_ERR_UNSUPPORTED. Temporary device memory: one output array (FP32: two, and one
  * copy of the strengths) and the trial plans (one at a time).
@@ -342,6 +344,35 @@ se_status se_batch_create(se_batch_h* out, int n_cfg, const se_plan_h* plans, co
                           const void* const* strengths, const int* n_rhs, void* const* u);
 se_status se_batch_launch(se_batch_h batch);
 void se_batch_destroy(se_batch_h batch);
+
+/*
+ * Many independent configurations on ONE plan, each stage one launch over all of them
+ * (batching of Sec. 5's independent systems; the plan's box, xi, r_c, M, P and window serve
+ * every configuration, so pick parameters that meet the tolerance for each, e.g. from the
+ * largest N and the smallest source quantity Q).
+ *   n_cfg        number of configurations (>= 1).
+ *   n_src        HOST long long [n_cfg]: points of each configuration (>= 0, total < 2^31).
+ *   src          device double [sum n_src][3]: the configurations' points one after the other.
+ *   strengths    device, per configuration a [n_rhs][n_src[c]][c_k] block (c_k as se_eval),
+ *                the blocks one after the other.
+ *   u            device, per configuration a [n_rhs][n_src[c]][3] block ([...][1] for
+ *                SE_HARMONIC), the blocks one after the other, overwritten.
+ * Star form (targets = sources of each configuration); a configuration's points interact only
+ * with each other. Sorting keys, grid components and outputs are offset per configuration:
+ * one gridding launch covers the tiles of all configurations, the transforms and the scaling
+ * run over all configurations' components at once, one gathering and one real-space launch
+ * cover all targets; the corrections run per configuration. Consecutive configurations are
+ * taken together as far as the buffers allow (the adaptive FFT's class buffers of D = 2, 1
+ * are indexed with 32-bit offsets, and a group's buffers are held to half the free device
+ * memory): a larger group runs as a few such evaluations in sequence. The offsets are copied
+ * to the device when they change (so a first call with given n_src comes before any stream
+ * capture of a call with the same n_src). Tensor-core gridding is not used for a group.
+ * se_get_info reports the kernels of all sub-groups and the stage times of the last one.
+ * Asynchronous on the plan's stream. Errors: SE_ERR_ARG (bad argument), SE_ERR_UNSUPPORTED (a
+ * key count beyond 2^31), otherwise as se_eval.
+ */
+se_status se_eval_group(se_plan_h plan, int kernel_mask, int n_cfg, const long long* n_src, const double* src,
+                        const void* strengths, int n_rhs, void* u);
 
 /*
  * The same entry points under the names of the problem statement:

@@ -93,6 +93,8 @@ SIGNATURES = {
     "se_eval_batch": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, _I3, ctypes.POINTER(ctypes.c_longlong),
                                      ctypes.POINTER(_P), ctypes.POINTER(_P), _I3, ctypes.POINTER(_P)]),
     "se_batch_destroy": (None, [_P]),
+    "se_eval_group": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _P, _P,
+                                     ctypes.c_int, _P]),
     "se_real_noalloc": (ctypes.c_int, [ctypes.c_int, _D3, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_longlong, _P, _P, _P, _P]),
 }
@@ -266,6 +268,18 @@ def se_eval_batch(plans, kernel_masks, srcs, strengths, n_rhs, us):
                               arr(ctypes.c_void_p, [f.data_ptr() for f in strengths]),
                               arr(ctypes.c_int, [int(r) for r in n_rhs]),
                               arr(ctypes.c_void_p, [u.data_ptr() for u in us])), "se_eval_batch")
+
+
+def se_eval_group(plan, kernel_mask, n_src, src, strengths, n_rhs, u):
+    """Several independent configurations on one plan in one evaluation (star form). n_src:
+    the configurations' point counts; src (sum n_src, 3), strengths (per configuration an
+    [n_rhs][N_c][c] block, concatenated) and u (per configuration an [n_rhs][N_c][out] block,
+    concatenated): contiguous torch device tensors (or raw device addresses)."""
+    n = len(n_src)
+    ptr = lambda t: ctypes.c_void_p(t if isinstance(t, int) else t.data_ptr())
+    check(lib().se_eval_group(plan, int(KERNELS.get(kernel_mask, kernel_mask)), n,
+                              (ctypes.c_longlong * n)(*[int(v) for v in n_src]), ptr(src), ptr(strengths),
+                              int(n_rhs), ptr(u)), "se_eval_group")
 
 
 def se_batch_launch(batch):

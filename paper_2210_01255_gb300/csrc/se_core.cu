@@ -48,6 +48,7 @@ struct BinGeom {
   GridGeom g;
   int bs;
   int nb[3];
+  GroupDev gr;  // a group evaluation: keys per configuration
 };
 
 __global__ void k_tile_keys(BinGeom bg, const double* __restrict__ x, int n, int* __restrict__ key,
@@ -67,6 +68,7 @@ __global__ void k_tile_keys(BinGeom bg, const double* __restrict__ x, int n, int
     c[d] = cc / bg.bs;
   }
   int k = (c[0] * bg.nb[1] + c[1]) * bg.nb[2] + c[2];
+  if (bg.gr.ncfg > 1) k += group_of(bg.gr, i) * (bg.nb[0] * bg.nb[1] * bg.nb[2]);
   key[i] = k;
   rank[i] = atomicAdd(&count[k], 1);
 }
@@ -83,6 +85,7 @@ __global__ void k_cell_keys(CellGeom g, const double* __restrict__ x, int n, int
     c[d] = min(max(cc, 0), g.nc[d] - 1);
   }
   int k = (c[0] * g.nc[1] + c[1]) * g.nc[2] + c[2];
+  if (g.gr.ncfg > 1) k += group_of(g.gr, i) * (g.nc[0] * g.nc[1] * g.nc[2]);
   key[i] = k;
   rank[i] = atomicAdd(&count[k], 1);
 }
@@ -315,13 +318,21 @@ __global__ void k_scatter_tile(GridGeom g, WinArgs<T> w, const int* __restrict__
                                const int* __restrict__ rank, const int* __restrict__ start, int n,
                                const double* __restrict__ x, int kernel, const T* __restrict__ f, int n_rhs,
                                int* __restrict__ perm, int* __restrict__ base, T* __restrict__ wts,
-                               T* __restrict__ sf, int* status) {
+                               T* __restrict__ sf, int* status, GroupDev gr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int s = start[key[i]] + rank[i];
   perm[s] = i;
   put_weights(g, w, x, i, s, base, wts, status);
-  if (f) put_spread_strengths(kernel, f, n, n_rhs, i, s, sf);
+  if (f) {
+    if (gr.ncfg > 1) {  // the strengths of point i in its configuration's [n_rhs][N_c][c] block
+      const int c = group_of(gr, i), b = gr.off[c];
+      put_spread_strengths(kernel, f + (size_t)b * n_rhs * kernel_comps(kernel), gr.off[c + 1] - b, n_rhs, i - b,
+                           s, sf);
+    } else {
+      put_spread_strengths(kernel, f, n, n_rhs, i, s, sf);
+    }
+  }
 }
 
 // ============================================== scaling step, Eq. (SE-scaling-disc), D = 3
@@ -435,8 +446,11 @@ template <typename T, int NCMAX>
 __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restrict__ perm,
                                                 const int* __restrict__ base, const T* __restrict__ wts,
                                                 const T* __restrict__ F, int nt, int NC, int no, T scale,
-                                                T* __restrict__ u, long long cst, long long xst) {
-  // F: component c at F + c cst, grid point (x, y, z) at x xst + y n2 + z
+                                                T* __restrict__ u, long long cst, long long xst, GroupDev gr,
+                                                int c0, int ncper) {
+  // F: component c at F + c cst, grid point (x, y, z) at x xst + y n2 + z; this launch gathers
+  // components c0 .. c0 + NC - 1 of the ncper outputs of each target (of its configuration's
+  // block of a group)
   __shared__ T s_w[8][3 * MAX_P];
   __shared__ long long s_xo[8][MAX_P];  // wrapped direction-0 plane offsets of the P taps
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -459,6 +473,8 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
   const T* w1 = s_w[warp] + P;
   const T* w2 = s_w[warp] + 2 * P;
   const long long* xo = s_xo[warp];
+  F += (size_t)((size_t)group_of(gr, s) * ncper + c0) * G;  // sorted targets of a configuration
+                                                            // are contiguous
   // FP32: each lane sums one P-term row along direction 0 in plain FP32 and adds the row sum
   // to its accumulator with Kahan compensation (err[]); the lanes' totals then meet in a
   // shuffle tree. FP64 accumulates directly.
@@ -510,7 +526,7 @@ __global__ void __launch_bounds__(256) k_gather(GridGeom g, const int* __restric
     const int i = perm ? perm[s] : s;
 #pragma unroll
     for (int k = 0; k < NCMAX; ++k)
-      if (k < NC) u[((size_t)(k / no) * nt + i) * no + k % no] = scale * acc[k];
+      if (k < NC) u[out_index(gr, ncper / no, no, nt, i, (c0 + k) / no, (c0 + k) % no)] = scale * acc[k];
   }
 }
 
@@ -548,8 +564,30 @@ __global__ void k_scatter_cell(CellGeom g, const int* __restrict__ key, const in
   }
   if (f) {
     const int nc = kernel_comps(kernel);
+    const T* fb = f;
+    int nl = n, il = i;
+    if (g.gr.ncfg > 1) {  // point i's configuration block [n_rhs][N_c][nc] of a group
+      const int c = group_of(g.gr, i), b = g.gr.off[c];
+      fb = f + (size_t)b * n_rhs * nc;
+      nl = g.gr.off[c + 1] - b;
+      il = i - b;
+    }
     for (int r = 0; r < n_rhs; ++r)
-      for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = f[((size_t)r * n + i) * nc + c];
+      for (int c = 0; c < nc; ++c) fs[((size_t)s * n_rhs + r) * nc + c] = fb[((size_t)r * nl + il) * nc + c];
+  }
+}
+
+// cell (of the cell geometry g) of each sorted target s: point perm[s] of x, wrapped as the
+// cell sort wraps it
+__global__ void k_cell_of(CellGeom g, const double* __restrict__ x, const int* __restrict__ perm, int n,
+                          int* __restrict__ cell3, int* status) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  const int i = perm[s];
+  for (int d = 0; d < 3; ++d) {
+    const double w = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
+    const int cc = (int)floor(w * g.inv_cs[d]);
+    cell3[3 * s + d] = min(max(cc, 0), g.nc[d] - 1);
   }
 }
 
@@ -948,18 +986,19 @@ bool use_tc_gridding(const se_plan_t* p) {
 
 template <typename T>
 se_status spread_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C,
-                        T* grid, long long cst, long long xst) {
-  if (sizeof(T) == 4 && use_tc_gridding(p))
+                        T* grid, long long cst, long long xst, int ncfg) {
+  // (a group of configurations always grids on the CUDA cores)
+  if (sizeof(T) == 4 && use_tc_gridding(p) && ncfg == 1)
     return spread_tc_launch(p, bin_start, base, (const float*)w, (const float*)sf, C, (float*)grid, cst, xst);
-  return grid_launch<T>(p, bin_start, base, w, sf, C, grid, cst, xst);
+  return grid_launch<T>(p, bin_start, base, w, sf, C, grid, cst, xst, ncfg);
 }
 
 template <typename T, int NC>
 void gather_launch(se_plan_t* p, const int* perm, const int* base, const T* w, const T* F, int nt, int NCr,
-                   int no, T scale, T* u, long long cst, long long xst) {
+                   int no, T scale, T* u, long long cst, long long xst, const GroupDev& gr, int c0, int ncper) {
   ++p->launches;
   k_gather<T, NC><<<grid1d(nt, 8), 256, 0, p->stream>>>(p->geom, perm, base, w, F, nt, NCr, no, scale, u, cst,
-                                                        xst);
+                                                        xst, gr, c0, ncper);
 }
 
 // u += v elementwise (join of the real-space part computed on the side stream)
@@ -971,14 +1010,20 @@ __global__ void k_axpy1(size_t n, const T* __restrict__ v, T* __restrict__ u) {
 
 template <typename T>
 se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const double* src,
-                    const T* strengths, int n_rhs, long long n_tgt, const double* tgt, T* u) {
+                    const T* strengths, int n_rhs, long long n_tgt, const double* tgt, T* u,
+                    GroupDev gr = GroupDev(), const int* hoff = nullptr) {
+  // gr, hoff (device and host point offsets): a group of gr.ncfg configurations in the star
+  // form (se_eval_group), each with its own grid components and outputs
   const bool star = (tgt == nullptr);
   const int N = (int)n_src;
   const int NT = star ? N : (int)n_tgt;
   const int cin = kernel_comps(kernel);
-  const int C = cin * n_rhs;    // spread components
+  const int C = cin * n_rhs;    // spread components (per point)
   const int NO = out_comps(kernel);
-  const int NC = NO * n_rhs;    // output components
+  const int NC = NO * n_rhs;    // output components (per point)
+  const int ncfg = gr.ncfg;
+  const int Ca = C * ncfg, NCa = NC * ncfg;  // grid components of all configurations
+  if (ncfg > 1 && (!star || !hoff)) return SE_ERR_UNSUPPORTED;
   if (C > MAX_COMP || n_rhs > 16) return SE_ERR_UNSUPPORTED;
   const GridGeom& g = p->geom;
   cudaStream_t st = p->stream;
@@ -1021,7 +1066,9 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       cg.L[d] = p->L[d];
       cg.inv_cs[d] = 1.0 / cs;
     }
-    const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2];
+    cg.gr = gr;
+    if ((long long)cg.nc[0] * cg.nc[1] * cg.nc[2] * ncfg > 0x7fffffffLL) return SE_ERR_UNSUPPORTED;
+    const int ncell = cg.nc[0] * cg.nc[1] * cg.nc[2] * ncfg;  // cells of all configurations
     int *sperm, *cstart;
     typedef typename Vec4<T>::type V4;
     void *xs, *fs, *xsl;
@@ -1081,9 +1128,47 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       SE_TRY(real_seg_setup(ra));
       if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
       if (blocks) {
+        // the targets of the blocks that are not dense (sparse regions) are summed one warp per
+        // target, as without the flag; cells of r_c/8 would give them hundreds of tiny column
+        // segments each, so they get a second cell list of cells >= r_c/2 (the sources sorted
+        // once more, the cell of each sorted target in that list)
+        CellGeom cc = cg;
+        for (int d = 0; d < 3; ++d) {
+          int nc = (int)std::floor(2.0 * p->L[d] / p->rc);
+          nc = std::max(1, std::min(nc, 128));
+          cc.nc[d] = nc;
+          const double cs = p->L[d] / nc;
+          cc.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
+          cc.inv_cs[d] = 1.0 / cs;
+        }
+        if ((long long)cc.nc[0] * cc.nc[1] * cc.nc[2] * ncfg > 0x7fffffffLL) return SE_ERR_UNSUPPORTED;
+        const int nccell = cc.nc[0] * cc.nc[1] * cc.nc[2] * ncfg;
+        int *cperm, *cstart2;
+        void *xsc, *xslc, *fsc, *tcc;
+        SE_TRY(buf(p, "rs.xsc", sizeof(V4) * (size_t)std::max(N, 1), &xsc));
+        SE_TRY(buf(p, "rs.xslc", sizeof(V4) * (size_t)std::max(N, 1), &xslc));
+        SE_TRY(buf(p, "rs.fsc", sizeof(T) * C * (size_t)std::max(N, 1), &fsc));
+        SE_TRY(buf(p, "rs.tcellc", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcc));
+        SE_TRY(counting_sort(p, rs, "ccell", N, nccell, cell_keyfun, src, &cc, &cperm, &cstart2,
+                             [&](const int* key, const int* rank, const int* start, int* perm) {
+                               k_scatter_cell<T><<<grid1d(N, 256), 256, 0, rs>>>(
+                                   cc, key, rank, start, N, src, kernel, strengths, n_rhs, perm, (V4*)xsc,
+                                   (V4*)xslc, (int*)nullptr, (T*)fsc, p->d_status);
+                             }));
+        ++p->launches;
+        k_cell_of<<<grid1d(NT, 256), 256, 0, rs>>>(cc, star ? src : tgt, tperm, NT, (int*)tcc, p->d_status);
+        RealArgs<T> rsp = ra;
+        rsp.cg = cc;
+        rsp.xs = (V4*)xsc;
+        rsp.xsl = (V4*)xslc;
+        rsp.fs = (T*)fsc;
+        rsp.cstart = cstart2;
+        rsp.tcell = (int*)tcc;
+        for (int d = 0; d < 3; ++d) rsp.cs[d] = (T)(p->L[d] / cc.nc[d]);
+        SE_TRY(real_seg_setup(rsp));
         void* work;
         SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 2), &work));
-        SE_TRY(real_launch_blocks<T>(rs, ra, (int*)work, 0.5 * p->rc, &p->launches));
+        SE_TRY(real_launch_blocks<T>(rs, ra, rsp, (int*)work, 0.5 * p->rc, &p->launches));
       } else {
         p->launches += real_launch<T>(rs, ra);
       }
@@ -1097,9 +1182,11 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   if (parts & SE_PART_FOURIER) {
     BinGeom bg;
     bg.g = g;
-    bg.bs = use_tc_gridding(p) ? TS : 4;
+    bg.bs = (use_tc_gridding(p) && ncfg == 1) ? TS : 4;
     for (int d = 0; d < 3; ++d) bg.nb[d] = cdiv(g.m[d], bg.bs);
-    const int ntiles = bg.nb[0] * bg.nb[1] * bg.nb[2];
+    bg.gr = gr;
+    if ((long long)bg.nb[0] * bg.nb[1] * bg.nb[2] * ncfg > 0x7fffffffLL) return SE_ERR_UNSUPPORTED;
+    const int ntiles = bg.nb[0] * bg.nb[1] * bg.nb[2] * ncfg;  // bins of all configurations
     int *perm, *tstart;
     void *base, *wts, *sf;
     SE_TRY(buf(p, "base", sizeof(int) * 3 * (size_t)std::max(N, 1), &base));
@@ -1118,49 +1205,49 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
                            k_scatter_tile<T><<<grid1d(N, 128), 128, 0, st>>>(g, wa, key, rank, start, N, src,
                                                                             kernel, strengths, n_rhs, pm,
                                                                             (int*)base, (T*)wts, (T*)sf,
-                                                                            p->d_status);
+                                                                            p->d_status, gr);
                          }));
     stage.mark();  // 1: bin + weights
     const size_t G = (size_t)g.cs;
     const size_t H = (size_t)g.n[0] * g.n[1] * (g.n[2] / 2 + 1);
     void *grid, *spec = nullptr, *ugrid;
-    SE_TRY(buf(p, "grid", sizeof(T) * C * G, &grid));
+    SE_TRY(buf(p, "grid", sizeof(T) * Ca * G, &grid));
     // the scaling step writes NC components in place over C (the harmonic field: C < NC)
-    if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * std::max(C, NC) * H, &spec));
-    SE_TRY(buf(p, "ugrid", sizeof(T) * NC * G, &ugrid));
-    if (p->D == 0 && (p->zeroed_grid != grid || p->zeroed_grid_C != C)) {
+    if (p->D == 3) SE_TRY(buf(p, "spec", sizeof(T) * 2 * std::max(Ca, NCa) * H, &spec));
+    SE_TRY(buf(p, "ugrid", sizeof(T) * NCa * G, &ugrid));
+    if (p->D == 0 && (p->zeroed_grid != grid || p->zeroed_grid_C != Ca)) {
       // D = 0: the grid [C][M'0][2M'1][2M'2] is zero beyond M' along directions 1 and 2; the
       // gridding writes only the first M' (every point there), so the padding is set once
       // per buffer and layout
-      SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * C * G, st));
+      SE_CUDA(cudaMemsetAsync(grid, 0, sizeof(T) * Ca * G, st));
       p->zeroed_grid = grid;
-      p->zeroed_grid_C = C;
+      p->zeroed_grid_C = Ca;
     }
     // grid layouts: component-major [C][n0][n1][n2] (D = 0: [C][m0][n1][n2]); for D = 1
     // direction-0-major [n0][C][n1][n2], so that the transforms along the periodic direction
     // take every component in one call
     const long long n12 = (long long)g.n[1] * g.n[2];
     const bool xmaj = p->D == 1;
-    const long long gcst = xmaj ? n12 : g.cs, gxst = xmaj ? (long long)C * n12 : n12;
-    const long long ucst = xmaj ? n12 : g.cs, uxst = xmaj ? (long long)NC * n12 : n12;
-    SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid, gcst, gxst));
+    const long long gcst = xmaj ? n12 : g.cs, gxst = xmaj ? (long long)Ca * n12 : n12;
+    const long long ucst = xmaj ? n12 : g.cs, uxst = xmaj ? (long long)NCa * n12 : n12;
+    SE_TRY(spread_launch<T>(p, tstart, (int*)base, (T*)wts, (T*)sf, C, (T*)grid, gcst, gxst, ncfg));
     SE_CUDA(cudaGetLastError());
-    p->last_grid_comps = C;
+    p->last_grid_comps = Ca;
     stage.mark();  // 2: spread
     if (p->D < 3) {
       // adaptive FFT (D = 2, 1) or padded FFT with the precomputed kernel (D = 0)
       // the forward transforms (3) and the scaling (4) are marked inside fourier_free
-      SE_TRY(fourier_free<T>(p, kernel, n_rhs, (T*)grid, C, (T*)ugrid, NC));
+      SE_TRY(fourier_free<T>(p, kernel, n_rhs * ncfg, (T*)grid, Ca, (T*)ugrid, NCa));
       stage.idx = 5;
       stage.mark();  // 5: inverse transforms
     } else {
     cufftHandle hf, hi;
-    SE_TRY(get_fft(p, true, C, &hf));
-    SE_TRY(get_fft(p, false, NC, &hi));
+    SE_TRY(get_fft(p, true, Ca, &hf));
+    SE_TRY(get_fft(p, false, NCa, &hi));
     SE_TRY(fft_exec<T>(hf, true, (T*)grid, (T*)spec));
     stage.mark();  // 3: fft
     ScaleTables<T> tb{(const T*)p->gtab[0].p, (const T*)p->gtab[1].p, (const T*)p->gtab[2].p, nullptr};
-    SE_TRY(launch_scale3p<T>(p, kernel, n_rhs, (T*)spec, tb));
+    SE_TRY(launch_scale3p<T>(p, kernel, n_rhs * ncfg, (T*)spec, tb));
     p->scale_modes = (long long)H;
     stage.mark();  // 4: scale
     SE_TRY(fft_exec<T>(hi, false, (T*)ugrid, (T*)spec));
@@ -1178,7 +1265,7 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
                            [&](const int* key, const int* rank, const int* start, int* pm) {
                              k_scatter_tile<T><<<grid1d(NT, 128), 128, 0, st>>>(
                                  g, wa, key, rank, start, NT, tgt, kernel, (const T*)nullptr, n_rhs, pm,
-                                 (int*)base2, (T*)wts2, (T*)nullptr, p->d_status);
+                                 (int*)base2, (T*)wts2, (T*)nullptr, p->d_status, GroupDev());
                            }));
       tperm = perm2;
       tbase = (int*)base2;
@@ -1191,17 +1278,25 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       // (outputs of one RHS are contiguous per target: a group of 6 components starts at
       // u + c0 NT whether a RHS has 3 outputs or 1)
       if (NC <= 3) {
-        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, NO, scale, u, ucst, uxst);
+        gather_launch<T, 3>(p, tperm, tbase, tw, (T*)ugrid, NT, NC, NO, scale, u, ucst, uxst, gr, 0, NC);
       } else {
-        const size_t GG = (size_t)ucst;
         for (int c0 = 0; c0 < NC; c0 += 6)
-          gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid + (size_t)c0 * GG, NT, std::min(6, NC - c0), NO,
-                              scale, u + (size_t)c0 * NT, ucst, uxst);
+          gather_launch<T, 6>(p, tperm, tbase, tw, (T*)ugrid, NT, std::min(6, NC - c0), NO, scale, u, ucst, uxst,
+                              gr, c0, NC);
       }
     }
     SE_CUDA(cudaGetLastError());
     // the polynomial taken out of the free-space biharmonic (SE_FLAG_SPLIT_POLY), added back
-    SE_TRY(poly_correction<T>(p, kernel, src, strengths, N, n_rhs, star ? src : tgt, NT, u));
+    // (per configuration of a group: its sources, strengths and output block)
+    if (ncfg == 1) {
+      SE_TRY(poly_correction<T>(p, kernel, src, strengths, N, n_rhs, star ? src : tgt, NT, u));
+    } else {
+      for (int c = 0; c < ncfg; ++c) {
+        const int b = hoff[c], nc = hoff[c + 1] - b;
+        SE_TRY(poly_correction<T>(p, kernel, src + 3 * (size_t)b, strengths + (size_t)b * C, nc, n_rhs,
+                                  src + 3 * (size_t)b, nc, u + (size_t)b * NC));
+      }
+    }
     stage.mark();  // 6: gather
   } else {
     for (int i = 0; i < 6; ++i) stage.mark();
@@ -1216,24 +1311,36 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
   }
   stage.mark();  // 7: real (join)
 
-  // ---------------- corrections (self term lives in the real-space pair loop)
-  if ((parts & SE_PART_CORR) && p->D == 3 && (kernel & SE_STRESSLET) && N > 0 && NT > 0) {
-    void* sums;
-    SE_TRY(buf(p, "k0sums", sizeof(double) * 4 * n_rhs, &sums));
-    SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * n_rhs, st));
-    ++p->launches;
-    k_k0_sums<T><<<std::min(grid1d(N, 256), 152), 256, 0, st>>>(g, src, strengths, N, n_rhs, cin, cin - 6,
-                                                                (double*)sums, p->d_status);
-    const double vol = p->L[0] * p->L[1] * p->L[2];
-    ++p->launches;
-    k_k0_apply<T><<<grid1d(NT, 256), 256, 0, st>>>(g, star ? src : tgt, NT, n_rhs, (double*)sums,
-                                                  -8.0 * M_PI / vol, u, p->d_status);
-    SE_CUDA(cudaGetLastError());
+  // ---------------- corrections (self term lives in the real-space pair loop), per
+  // configuration of a group (its sources, strengths and output block)
+  auto corrections = [&](const double* xs_, const T* f_, int n_, const double* t_, int nt_, T* u_) -> se_status {
+    if ((parts & SE_PART_CORR) && p->D == 3 && (kernel & SE_STRESSLET) && n_ > 0 && nt_ > 0) {
+      void* sums;
+      SE_TRY(buf(p, "k0sums", sizeof(double) * 4 * n_rhs, &sums));
+      SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * 4 * n_rhs, st));
+      ++p->launches;
+      k_k0_sums<T><<<std::min(grid1d(n_, 256), 152), 256, 0, st>>>(g, xs_, f_, n_, n_rhs, cin, cin - 6,
+                                                                   (double*)sums, p->d_status);
+      const double vol = p->L[0] * p->L[1] * p->L[2];
+      ++p->launches;
+      k_k0_apply<T><<<grid1d(nt_, 256), 256, 0, st>>>(g, t_, nt_, n_rhs, (double*)sums, -8.0 * M_PI / vol, u_,
+                                                     p->d_status);
+      SE_CUDA(cudaGetLastError());
+    }
+    if ((parts & SE_PART_CORR) && (kernel & SE_STOKESLET))
+      SE_TRY(gauge_correction<T>(p, f_, cin, n_, n_rhs, nt_, u_));
+    if ((parts & SE_PART_CORR) && kernel == SE_HARMONIC) SE_TRY(harmonic_constant<T>(p, f_, n_, n_rhs, nt_, u_));
+    return SE_OK;
+  };
+  if (ncfg == 1) {
+    SE_TRY(corrections(src, strengths, N, star ? src : tgt, NT, u));
+  } else {
+    for (int c = 0; c < ncfg; ++c) {
+      const int b = hoff[c], nc = hoff[c + 1] - b;
+      SE_TRY(corrections(src + 3 * (size_t)b, strengths + (size_t)b * C, nc, src + 3 * (size_t)b, nc,
+                         u + (size_t)b * NC));
+    }
   }
-  if ((parts & SE_PART_CORR) && (kernel & SE_STOKESLET))
-    SE_TRY(gauge_correction<T>(p, strengths, cin, N, n_rhs, NT, u));
-  if ((parts & SE_PART_CORR) && kernel == SE_HARMONIC)
-    SE_TRY(harmonic_constant<T>(p, strengths, N, n_rhs, NT, u));
   stage.mark();  // 8: corrections
   p->timed_pending = p->timers.on;
   p->real_timed = p->timers.on && (parts & SE_PART_REAL) && NT > 0;
@@ -1258,6 +1365,81 @@ extern "C" se_status se_eval_parts(se_plan_h p, int kernel, int parts, long long
                             (float*)u);
   return eval_impl<double>(p, kernel, parts, n_src, src, (const double*)strengths, n_rhs, n_tgt, tgt,
                            (double*)u);
+}
+
+// A group of independent configurations on one plan: consecutive configurations form
+// sub-groups whose buffers keep 32-bit class offsets (D = 2, 1) and fit in half the free
+// device memory; each sub-group is one evaluation (every stage one launch over its
+// configurations). Each sub-group's point offsets go to the device once per change (plan
+// buffers "group.off.<k>"), so a repeated call uploads nothing.
+extern "C" se_status se_eval_group(se_plan_h p, int kernel, int n_cfg, const long long* n_src, const double* src,
+                                   const void* strengths, int n_rhs, void* u) {
+  if (!p || !n_src || !u || n_cfg < 1 || n_rhs < 1) return SE_ERR_ARG;
+  if (kernel != SE_STOKESLET && kernel != SE_ROTLET && kernel != SE_STRESSLET && kernel != SE_KERNEL_ST &&
+      kernel != SE_HARMONIC_FIELD && kernel != SE_HARMONIC)
+    return SE_ERR_ARG;
+  std::vector<long long> off((size_t)n_cfg + 1, 0);
+  for (int c = 0; c < n_cfg; ++c) {
+    if (n_src[c] < 0) return SE_ERR_ARG;
+    off[c + 1] = off[c] + n_src[c];
+    if (off[c + 1] > 0x7fffffffLL) return SE_ERR_ARG;
+  }
+  if (off[n_cfg] > 0 && (!src || !strengths)) return SE_ERR_ARG;
+  if (cudaSetDevice(p->device) != cudaSuccess) return SE_ERR_CUDA;
+  if (n_cfg == 1) return se_eval(p, kernel, off[1], src, strengths, n_rhs, 0, nullptr, u);
+  // sub-group size
+  const int cin = kernel_comps(kernel), no = out_comps(kernel);
+  const long long C = (long long)cin * n_rhs, NC = (long long)no * n_rhs, CS = std::max(C, NC);
+  const size_t es = p->prec == SE_FP32 ? 4 : 8;
+  const long long cls = free_class_elems(p);
+  const double G = (double)p->geom.n[0] * p->geom.n[1] * p->geom.n[2];
+  // bytes of one configuration's grids, spectra and class buffers (spectra counted as complex
+  // copies of the grid, a bound for every D)
+  const double per_cfg = (double)es * ((double)(C + NC) * G + 2.0 * CS * G + 2.0 * CS * (double)cls);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return SE_ERR_CUDA;
+  long long gmax = n_cfg;
+  if (cls > 0) gmax = std::min(gmax, 0x7fffffffLL / (CS * cls));
+  gmax = std::min(gmax, std::max(1LL, (long long)(0.5 * (double)free_b / per_cfg)));
+  if (gmax < 1) return SE_ERR_UNSUPPORTED;
+  const char* fbase = (const char*)strengths;
+  char* ubase = (char*)u;
+  int launches = 0;  // over all sub-groups (se_get_info)
+  for (int c0 = 0, k = 0; c0 < n_cfg; c0 += (int)gmax, ++k) {
+    const int nc = (int)std::min<long long>(gmax, n_cfg - c0);
+    std::vector<int> so((size_t)nc + 1);
+    for (int c = 0; c <= nc; ++c) so[c] = (int)(off[c0 + c] - off[c0]);
+    const long long b = off[c0], ns = so[nc];
+    const double* s_src = src ? src + 3 * b : nullptr;
+    const void* s_f = fbase ? fbase + es * (size_t)(b * C) : nullptr;
+    void* s_u = ubase + es * (size_t)(b * NC);
+    if (nc == 1) {
+      SE_TRY(se_eval(p, kernel, ns, s_src, s_f, n_rhs, 0, nullptr, s_u));
+      launches += p->launches;
+      continue;
+    }
+    const std::string name = "group.off." + std::to_string(k);
+    void* d_off;
+    const void* before = p->bufs->count(name) ? (*p->bufs)[name].p : nullptr;
+    SE_TRY(buf(p, name.c_str(), sizeof(int) * so.size(), &d_off));
+    if ((size_t)k >= p->group_off.size()) p->group_off.resize((size_t)k + 1);
+    if (d_off != before || p->group_off[(size_t)k] != so) {
+      SE_CUDA(cudaMemcpyAsync(d_off, so.data(), sizeof(int) * so.size(), cudaMemcpyHostToDevice, p->stream));
+      p->group_off[(size_t)k] = so;
+    }
+    GroupDev gr;
+    gr.ncfg = nc;
+    gr.off = (const int*)d_off;
+    if (p->prec == SE_FP32)
+      SE_TRY(eval_impl<float>(p, kernel, SE_PART_ALL, ns, s_src, (const float*)s_f, n_rhs, 0, nullptr, (float*)s_u,
+                              gr, so.data()));
+    else
+      SE_TRY(eval_impl<double>(p, kernel, SE_PART_ALL, ns, s_src, (const double*)s_f, n_rhs, 0, nullptr,
+                               (double*)s_u, gr, so.data()));
+    launches += p->launches;
+  }
+  p->launches = launches;
+  return SE_OK;
 }
 
 extern "C" se_status se_eval(se_plan_h p, int kernel, long long n_src, const double* src,
@@ -1485,8 +1667,11 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   // does not change with the strengths' mantissas, such as the rounded kernel tables, is not
   // in it), so twice the estimate is held to 7 tol_rel of the 10 tol_rel that the rules of
   // Sec. 4.6 allow (their truncation error at tol_rel <= 1e-7 measures far below tol_rel). The
-  // rounding grows with xi (smaller r_c): an invalid candidate ends a walk towards smaller r_c
-  // and is passed over on a walk towards larger r_c.
+  // estimate is itself noisy (one sample of a spatially correlated error: repeated trials of
+  // one candidate read 2.4e-7 .. 6.3e-7 on the clustered 0P workload), so it only decides
+  // whether a candidate may be chosen: the direction of the walk is decided by time, and a
+  // walk ends after two candidates in a row that are invalid or more than 10 % slower than
+  // the best.
   auto ok = [&](const TimedCand& c) { return io->prec != SE_FP32 || 2.0 * c.round_est <= 7.0 * tol_rel; };
   bool have = false;
   if (st == SE_OK) {
@@ -1498,18 +1683,17 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
         best = c1;
         have = true;
       }
-      // the first step down decides the direction: down if it is valid and faster
+      // the first step down decides the direction: down if it is faster
       se_status s2 = run(step, &c2);
       if (s2 != SE_OK && s2 != SE_ERR_NOMEM && s2 != SE_ERR_UNSUPPORTED) st = s2;
-      bool down = false;
+      const bool down = s2 == SE_OK && c2.ms < c1.ms;
       if (s2 == SE_OK && ok(c2) && (!have || c2.ms < best.ms)) {
         best = c2;
         have = true;
-        down = true;
       }
       double f = down ? step * step : 1.0 / step;
-      int worse = 0;
-      for (int k = 0; k < 14 && st == SE_OK && worse < 2; ++k, f = down ? f * step : f / step) {
+      int miss = 0;
+      for (int k = 0; k < 14 && st == SE_OK && miss < 2; ++k, f = down ? f * step : f / step) {
         TimedCand c;
         se_status s = run(f, &c);
         if (s == SE_ERR_NOMEM || s == SE_ERR_UNSUPPORTED) break;
@@ -1517,16 +1701,12 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
           st = s;
           break;
         }
-        if (!ok(c)) {
-          if (down) break;
-          continue;
-        }
-        if (!have || c.ms < best.ms) {
+        if (ok(c) && (!have || c.ms < best.ms)) {
           best = c;
           have = true;
-          worse = 0;
-        } else if (c.ms > 1.1 * best.ms) {
-          ++worse;
+          miss = 0;
+        } else if (!ok(c) || c.ms > 1.1 * best.ms) {
+          ++miss;
         }
       }
       if (st == SE_OK && !have) st = SE_ERR_UNSUPPORTED;  // no candidate keeps the rounding in bounds

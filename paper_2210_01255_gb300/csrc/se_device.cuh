@@ -153,7 +153,17 @@ struct CellGeom {
   int periodic[3];
   double L[3];
   double inv_cs[3];
+  GroupDev gr;  // configurations of a group evaluation: cell keys and cell starts per configuration
 };
+
+// index of output q of RHS r of original target i in u: [n_rhs][nt][no], per configuration of a
+// group ([n_rhs][N_c][no] blocks one after the other)
+__device__ inline size_t out_index(const GroupDev& gr, int n_rhs, int no, int nt, int i, int r, int q) {
+  if (gr.ncfg <= 1) return ((size_t)r * nt + i) * no + q;
+  const int c = group_of(gr, i);
+  const int b = gr.off[c], nl = gr.off[c + 1] - b;
+  return (size_t)b * n_rhs * no + ((size_t)r * nl + (i - b)) * no + q;
+}
 
 // Arguments of the real-space kernels (Eq. real-space-potential-Dp), se_real.cu.
 template <typename T>
@@ -188,8 +198,10 @@ template <typename T>
 int real_launch(cudaStream_t st, const RealArgs<T>& a);
 // the dense-block path: targets grouped in blocks of 32 consecutive (cell-sorted) targets;
 // blocks whose targets lie within a box of side <= thr go to the block kernel, the others'
-// targets to the sparse kernel. work: int scratch of >= ceil(ntgt / 32) + ntgt + 2 entries.
+// targets to the sparse kernel, which runs with `sparse` (the same targets, its own cell list
+// of coarser cells, or `a` itself). work: int scratch of >= ceil(ntgt / 32) + ntgt + 2 entries.
 template <typename T>
-se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, int* work, double thr, int* launches);
+se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, const RealArgs<T>& sparse, int* work, double thr,
+                             int* launches);
 
 }  // namespace se

@@ -1026,6 +1026,21 @@ se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* u
   return SE_OK;
 }
 
+long long free_class_elems(const se_plan_t* p) {
+  const int k = p->kbar_star;
+  if (p->D == 2) {
+    const long long ncolS = (2LL * k + 1) * (k + 1) - 1;
+    return std::max<long long>(p->ncls[0][2], std::max<long long>(ncolS, 1) * p->ncls[1][2]);
+  }
+  if (p->D == 1) {
+    const int H0 = p->geom.m[0] / 2 + 1;
+    const long long kst = std::max(0, std::min(k, H0 - 2));
+    return std::max<long long>((long long)p->ncls[0][1] * p->ncls[0][2],
+                               std::max<long long>(kst, 1) * p->ncls[1][1] * p->ncls[1][2]);
+  }
+  return 0;
+}
+
 // Gauge constants of the 0P and 1P stokeslet (Eqs. 0p-stokeslet-extra-contribution and
 // 1p-stokeslet-extra-contribution): 0P adds (2/R) sum f; 1P subtracts
 // diag(4 ln R + 4, 2 ln R + 1, 2 ln R + 1) sum f / L_0.

@@ -70,6 +70,9 @@ struct GridArgs {
   int2* queue;              // overflow items: (tile, slab)
   int* qcount;
   int qcap;
+  int ncfg;                 // configurations of a group evaluation (1 otherwise): tile t of
+                            // configuration c is item c ntiles + t, its bins are offset by
+                            // c nbins and its components by c Ctot
 };
 
 // (bin, grid shift) pairs along direction d that can hold points reaching [o, o + E) (x, y), or
@@ -124,6 +127,7 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
   const GridGeom& g = a.g;
   const int P = g.P;
   const int ntiles = a.nt[0] * a.nt[1] * a.nt[2];
+  const int nbins = a.nb[0] * a.nb[1] * a.nb[2];
   // thread block of the tile: xy entries 2 ga, 2 ga + 1 (x = ga / 2, y = 2 (ga % 2) + {0, 1}),
   // z = gz RZ .. gz RZ + RZ - 1
   const int ga = lane & 7, gz = lane >> 3;
@@ -141,9 +145,11 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
     } else {
       tile = blockIdx.x * NW + warp;
       slab = 0;
-      if (tile >= ntiles) return;
+      if (tile >= ntiles * a.ncfg) return;
     }
-    const int t2 = tile % a.nt[2], t1 = (tile / a.nt[2]) % a.nt[1], t0 = tile / (a.nt[2] * a.nt[1]);
+    const int cfg = tile / ntiles, lt = tile - cfg * ntiles;
+    const int* bin_start = a.bin_start + (size_t)cfg * nbins;
+    const int t2 = lt % a.nt[2], t1 = (lt / a.nt[2]) % a.nt[1], t0 = lt / (a.nt[2] * a.nt[1]);
     const int o0 = 4 * t0, o1 = 4 * t1, o2 = TZ * t2;
     __syncwarp();
     if (lane == 0) bin_lists(g, a.nb, 0, o0, 4, sm.xb, sm.xsh, &sm.nx, nullptr, nullptr, false);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
       if (lane < cpr && k < ncol) {
         const int ix = k / ny, iy = k - (k / ny) * ny;
         const int colb = (sm.xb[ix] * a.nb[1] + sm.yb[iy]) * a.nb[2];
-        for (int z = 0; z < nz; ++z) cnt += a.bin_start[colb + sm.zhi[z] + 1] - a.bin_start[colb + sm.zlo[z]];
+        for (int z = 0; z < nz; ++z) cnt += bin_start[colb + sm.zhi[z] + 1] - bin_start[colb + sm.zlo[z]];
       }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) cnt += __shfl_xor_sync(FULL, cnt, off);
@@ -272,7 +278,7 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
         const int ix = k / ny, iy = k - (k / ny) * ny;
         const int colb = (sm.xb[ix] * a.nb[1] + sm.yb[iy]) * a.nb[2];
         for (int z = 0; z < nz; ++z) {
-          const int b = a.bin_start[colb + sm.zlo[z]], e = a.bin_start[colb + sm.zhi[z] + 1];
+          const int b = bin_start[colb + sm.zlo[z]], e = bin_start[colb + sm.zhi[z] + 1];
           const int sl = slot0 + z;
           sm.sbeg[sl] = b;
           sm.slen[sl] = e - b;
@@ -350,7 +356,7 @@ __global__ void __launch_bounds__(32 * GWarps<T, TZ>::v) k_grid(GridArgs a, cons
 #pragma unroll
           for (int c = 0; c < CG; ++c) {
             if (c < a.C) {
-              T* dst = grid + (size_t)(a.c0 + c) * a.cst + off;
+              T* dst = grid + (size_t)((size_t)cfg * a.Ctot + a.c0 + c) * a.cst + off;
               if (atomic) atomicAdd(dst, acc[i][z][c]);
               else *dst = acc[i][z][c];
             }
@@ -368,7 +374,7 @@ void launch_grid(cudaStream_t st, GridArgs a, const T* w, const T* sf, T* grid, 
   a.nt[0] = cdiv(a.g.m[0], 4);
   a.nt[1] = cdiv(a.g.m[1], 4);
   a.nt[2] = cdiv(a.g.m[2], TZ);
-  const long long ntiles = (long long)a.nt[0] * a.nt[1] * a.nt[2];
+  const long long ntiles = (long long)a.nt[0] * a.nt[1] * a.nt[2] * a.ncfg;
   k_grid<T, TZ, RZ, CG, false><<<(unsigned)((ntiles + NW - 1) / NW), 32 * NW, 0, st>>>(a, w, sf, grid);
   k_grid<T, TZ, RZ, CG, true><<<152 * 4, 32 * NW, 0, st>>>(a, w, sf, grid);
   *launches += 2;
@@ -380,10 +386,11 @@ void launch_grid(cudaStream_t st, GridArgs a, const T* w, const T* sf, T* grid, 
 // of up to 12 (FP32) components per launch pair.
 template <typename T>
 se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid,
-                      long long cst, long long xst) {
+                      long long cst, long long xst, int ncfg) {
   const GridGeom& g = p->geom;
   GridArgs a;
   a.g = g;
+  a.ncfg = ncfg;
   for (int d = 0; d < 3; ++d) a.nb[d] = cdiv(g.m[d], 4);
   a.bin_start = bin_start;
   a.base = base;
@@ -427,8 +434,8 @@ se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const
 }
 
 template se_status grid_launch<float>(se_plan_t*, const int*, const int*, const float*, const float*, int, float*,
-                                      long long, long long);
+                                      long long, long long, int);
 template se_status grid_launch<double>(se_plan_t*, const int*, const int*, const double*, const double*, int,
-                                       double*, long long, long long);
+                                       double*, long long, long long, int);
 
 }  // namespace se

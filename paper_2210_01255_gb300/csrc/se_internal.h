@@ -45,6 +45,27 @@ __host__ __device__ inline int rule_mask(int mask) {
   return (mask & 7) | ((mask & (SE_HARMONIC_FIELD | SE_HARMONIC)) ? SE_ROTLET : 0);
 }
 
+// A group of independent configurations evaluated together on one plan (se_eval_group):
+// configuration c owns the points off[c] .. off[c+1] - 1 of the concatenated inputs, and the
+// same range of every sorted order (the sort keys start with the configuration), its own
+// block of grid components and its own block of outputs. ncfg = 1 with off = nullptr is the
+// ordinary single evaluation.
+struct GroupDev {
+  int ncfg = 1;
+  const int* off = nullptr;  // device [ncfg + 1]
+};
+// configuration of point i (original or sorted index): the largest c with off[c] <= i
+__host__ __device__ inline int group_of(const GroupDev& gr, int i) {
+  if (gr.ncfg <= 1) return 0;
+  int lo = 0, hi = gr.ncfg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (gr.off[mid] <= i) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Geometry of the grid that gridding writes and gathering reads (Sec. 3.2).
 struct GridGeom {
   int m[3];         // extent of the spread grid per direction (M_i periodic, M'_i free)
@@ -130,6 +151,7 @@ struct se_plan_t {
   se::DevBuf atr[2];       // D = 0 precomputed kernels: 0 harmonic, 1 biharmonic
   double poly_c[3] = {0, 0, 0};  // SE_FLAG_SPLIT_POLY: c0 + c1 r^2 + c2 r^4 taken out of B_R
   bool poly_on = false;
+  std::vector<std::vector<int>> group_off;  // se_eval_group: point offsets last uploaded, per sub-group
 
   se::Timers timers;
   float times_ms[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
@@ -170,7 +192,7 @@ se_status launch_scale3p(se_plan_t* p, int kernel, int n_rhs, T* spec, const Sca
 // gridding on the CUDA cores (se_grid.cu): points sorted by 4^3 bins (bin_start)
 template <typename T>
 se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const T* w, const T* sf, int C, T* grid,
-                      long long cst, long long xst);
+                      long long cst, long long xst, int ncfg = 1);
 // FP32 gridding on the tensor cores (se_spread_tc.cu)
 se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
                            int C, float* grid, long long cst, long long xst);
@@ -181,6 +203,8 @@ template <typename T>
 se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rhs, int nt, T* u);
 template <typename T>
 se_status harmonic_constant(se_plan_t* p, const T* q, int n, int n_rhs, int nt, T* u);
+// elements per component of the largest class buffer of the adaptive FFT (D = 2, 1; 0 else)
+long long free_class_elems(const se_plan_t* p);
 template <typename T>
 se_status poly_correction(se_plan_t* p, int kernel, const double* x, const T* f, int n, int n_rhs, const double* t,
                           int nt, T* u);

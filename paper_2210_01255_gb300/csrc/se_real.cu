@@ -317,6 +317,8 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
   xtl.x = xtl.y = xtl.z = xtl.w = T(0);
   if (sizeof(T) == 4) xtl = a.xtl[s];
   const int cx = a.tcell[3 * s], cy = a.tcell[3 * s + 1], cz = a.tcell[3 * s + 2];
+  // a group evaluation: the cells of this target's configuration (sorted by configuration first)
+  const int cfgcell = group_of(a.cg.gr, s) * (a.cg.nc[0] * a.cg.nc[1] * a.cg.nc[2]);
   const int nc = kernel_comps(KERNEL);
   const int C = nc * a.n_rhs;
   T acc[NO * RMAX];
@@ -401,7 +403,7 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
             zend = min(zend, g.nc[2] - 1);
           }
           const T shx = T(imx) * a.Lhi[0], shy = T(imy) * a.Lhi[1];
-          const int colbase = (ux * g.nc[1] + uy) * g.nc[2];
+          const int colbase = cfgcell + (ux * g.nc[1] + uy) * g.nc[2];
           while (zlo <= zend && nseg < maxseg) {
             int imz = 0, w0 = zlo;
             if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_real(RealArgs<T> a) {
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
       for (int qq = 0; qq < NO; ++qq) {
-        T* o = a.u + ((size_t)r * a.ntgt + i) * NO + qq;
+        T* o = a.u + out_index(a.cg.gr, a.n_rhs, NO, a.ntgt, i, r, qq);
         *o = a.overwrite ? acc[NO * r + qq] : *o + acc[NO * r + qq];
       }
   }
@@ -575,6 +577,8 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
   const bool tv = lane < nt;
   const int s = s0 + (tv ? lane : 0);
   const int C = BlkComps<KERNEL, RMAX>::c * a.n_rhs;
+  // a group evaluation: every target of a listed block is in one configuration (k_real_classify)
+  const int cfgcell = group_of(a.cg.gr, s0) * (a.cg.nc[0] * a.cg.nc[1] * a.cg.nc[2]);
   const V4 th = a.xt[s];
   V4 tl;
   tl.x = tl.y = tl.z = tl.w = T(0);
@@ -631,7 +635,7 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
         int imx = 0, imy = 0;
         const int wx = g.periodic[0] ? wrap_cell(ux, g.nc[0], &imx) : ux;
         const int wy = g.periodic[1] ? wrap_cell(uy, g.nc[1], &imy) : uy;
-        const int colbase = (wx * g.nc[1] + wy) * g.nc[2];
+        const int colbase = cfgcell + (wx * g.nc[1] + wy) * g.nc[2];
         while (zlo <= zhi && nseg < maxseg) {
           int imz = 0, w0 = zlo;
           if (g.periodic[2]) w0 = wrap_cell(zlo, g.nc[2], &imz);
@@ -754,7 +758,7 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
     const int i = a.tperm[s];
     for (int r = 0; r < a.n_rhs && r < RMAX; ++r)
       for (int q = 0; q < NO; ++q) {
-        T* o = a.u + ((size_t)r * a.ntgt + i) * NO + q;
+        T* o = a.u + out_index(a.cg.gr, a.n_rhs, NO, a.ntgt, i, r, q);
         *o = a.overwrite ? acc[NO * r + q] : *o + acc[NO * r + q];
       }
   }
@@ -788,6 +792,8 @@ __global__ void k_real_classify(RealArgs<T> a, T thr, int nblk, int* __restrict_
     }
     dense = dense && (hi - lo <= thr);
   }
+  // a block across two configurations of a group goes to k_real
+  if (a.cg.gr.ncfg > 1 && group_of(a.cg.gr, s0) != group_of(a.cg.gr, s0 + nt - 1)) dense = false;
   if (dense) {
     if (lane == 0) blist[atomicAdd(&counts[0], 1)] = warp;
   } else {
@@ -836,10 +842,11 @@ static void launch_blk(cudaStream_t st, const RealArgs<T>& a, const int* blist, 
 }
 
 template <typename T>
-se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, int* work, double thr, int* launches) {
+se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, const RealArgs<T>& sparse, int* work, double thr,
+                             int* launches) {
   if (a.ntgt <= 0) return SE_OK;
   if (a.n_rhs > 4) {  // the block kernel keeps 3 x 3 n_rhs sums per lane: many RHS use k_real
-    *launches += real_launch(st, a);
+    *launches += real_launch(st, sparse);
     return SE_OK;
   }
   const int nblk = (a.ntgt + 31) / 32;
@@ -863,7 +870,7 @@ se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, int* work, double t
   k_real_classify<T><<<grid1d(nblk, 4), 128, 0, st>>>(a, (T)thr, nblk, blist, tlist, counts);
   if (a.n_rhs <= 1) launch_blk<T, 1>(st, ab, blist, counts, nblk);
   else launch_blk<T, 4>(st, ab, blist, counts, nblk);
-  RealArgs<T> b = a;
+  RealArgs<T> b = sparse;  // the targets of the other blocks, on the sparse path's own cell list
   b.tlist = tlist;
   b.tcount = counts + 1;
   real_launch(st, b);
@@ -876,7 +883,9 @@ template se_status real_seg_setup<float>(RealArgs<float>&);
 template se_status real_seg_setup<double>(RealArgs<double>&);
 template int real_launch<float>(cudaStream_t, const RealArgs<float>&);
 template int real_launch<double>(cudaStream_t, const RealArgs<double>&);
-template se_status real_launch_blocks<float>(cudaStream_t, RealArgs<float>, int*, double, int*);
-template se_status real_launch_blocks<double>(cudaStream_t, RealArgs<double>, int*, double, int*);
+template se_status real_launch_blocks<float>(cudaStream_t, RealArgs<float>, const RealArgs<float>&, int*, double,
+                                             int*);
+template se_status real_launch_blocks<double>(cudaStream_t, RealArgs<double>, const RealArgs<double>&, int*, double,
+                                              int*);
 
 }  // namespace se

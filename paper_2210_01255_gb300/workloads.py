@@ -111,6 +111,9 @@ CONFIGS = {
     # the harmonic field (electrostatics: the field of N(0,1) point charges), triply periodic
     "3p_harmonic_field_n100000": dict(D=3, box=(1.0, 1.0, 1.0), N=100000, kernels=("harmonic_field",),
                                       tol=1e-6, prec="fp32", window="pkb", seed=6, n_rhs=1),
+    # the harmonic (electrostatic) potential of the same charges: one output per target
+    "3p_harmonic_n100000": dict(D=3, box=(1.0, 1.0, 1.0), N=100000, kernels=("harmonic",),
+                                tol=1e-6, prec="fp32", window="pkb", seed=6, n_rhs=1),
     # 64 independent singly periodic systems, N log-uniform in [2e3, 5e4], 16 RHS each;
     # P_margin = 0 (P = 8): RMS relative error 5.6e-7 / 4.4e-7 on two systems (P = 12:
     # 5.0e-7 / 4.2e-7)
