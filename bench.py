@@ -516,7 +516,8 @@ def run_group(cfg, items, args, flush, dev, dist):
     the extended grid size M' their own selection gives (7 buckets for the 64 systems of the 1P
     workload), each bucket shares one plan (the parameters of Sec. 4.6 for the bucket's largest
     N and smallest source quantity Q, so that each of its configurations meets the tolerance)
-    and is one se_eval_group call (every stage one launch over the bucket's configurations).
+    and is one se_eval_group call (every stage one launch over the bucket's configurations) on
+    a stream of its own, forked from and joined to the step's stream.
     Timed eagerly (one call per bucket per step) and as one captured CUDA graph of all the
     calls, with the L2 flushed between steps; end to end with pinned host buffers (copies in the
     timed region); outputs compared with the per-configuration evaluations."""
@@ -544,16 +545,20 @@ def run_group(cfg, items, args, flush, dev, dist):
             o = t["opts"]
             o.kernel_mask = se.KERNELS[kernel]
             o.Q = Q
+            bs = torch.cuda.Stream(device=dev)   # buckets run concurrently, forked from gs
             plan = se.Plan(cfg["D"], cfg["box"], t["xi"], t["rc"], t["M"], t["P"], cfg["window"], cfg["prec"],
-                           opts=o, stream=gs)
-            groups.append(dict(items=its, Ns=Ns, plan=plan, params=t,
+                           opts=o, stream=bs)
+            groups.append(dict(items=its, Ns=Ns, plan=plan, params=t, stream=bs,
                                src=torch.cat([it["xdev"] for it in its]).contiguous(),
                                f=torch.cat([it["fdev"].reshape(-1) for it in its]).contiguous(),
                                u=torch.empty(sum(R * n * no for n in Ns), dtype=tdt, device=dev)))
 
         def gstep():
             for g in groups:
+                g["stream"].wait_stream(gs)
                 se.se_eval_group(g["plan"].handle, kernel, g["Ns"], g["src"], g["f"], R, g["u"])
+            for g in groups:
+                gs.wait_stream(g["stream"])
 
         for _ in range(max(3, args.warmup)):
             gstep()
@@ -627,9 +632,9 @@ def run_group(cfg, items, args, flush, dev, dist):
                          "xi": g["params"]["xi"], "M": list(g["params"]["M"]), "P": g["params"]["P"]}
                         for g in groups],
             "max_rel_diff_vs_per_configuration": err,
-            "form": "FP32 group: the %d configurations in %d se_eval_group calls (one per extended-grid "
-                    "bucket, each on one plan with every stage one launch over its configurations), "
-                    "captured as one CUDA graph and replayed" % (len(items), len(groups))}
+            "form": "FP32 group: the %d configurations in %d concurrent se_eval_group calls (one per "
+                    "extended-grid bucket, each on one plan with every stage one launch over its "
+                    "configurations), captured as one CUDA graph and replayed" % (len(items), len(groups))}
 
 
 def main():

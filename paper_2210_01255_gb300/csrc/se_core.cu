@@ -577,20 +577,6 @@ __global__ void k_scatter_cell(CellGeom g, const int* __restrict__ key, const in
   }
 }
 
-// cell (of the cell geometry g) of each sorted target s: point perm[s] of x, wrapped as the
-// cell sort wraps it
-__global__ void k_cell_of(CellGeom g, const double* __restrict__ x, const int* __restrict__ perm, int n,
-                          int* __restrict__ cell3, int* status) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
-  const int i = perm[s];
-  for (int d = 0; d < 3; ++d) {
-    const double w = wrap_coord(x[3 * i + d], g.L[d], g.periodic[d], status);
-    const int cc = (int)floor(w * g.inv_cs[d]);
-    cell3[3 * s + d] = min(max(cc, 0), g.nc[d] - 1);
-  }
-}
-
 // ================================================================ corrections
 //
 // 3P stresslet zero mode, Eq. (k0-stresslet-3p):
@@ -1128,47 +1114,9 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       SE_TRY(real_seg_setup(ra));
       if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
       if (blocks) {
-        // the targets of the blocks that are not dense (sparse regions) are summed one warp per
-        // target, as without the flag; cells of r_c/8 would give them hundreds of tiny column
-        // segments each, so they get a second cell list of cells >= r_c/2 (the sources sorted
-        // once more, the cell of each sorted target in that list)
-        CellGeom cc = cg;
-        for (int d = 0; d < 3; ++d) {
-          int nc = (int)std::floor(2.0 * p->L[d] / p->rc);
-          nc = std::max(1, std::min(nc, 128));
-          cc.nc[d] = nc;
-          const double cs = p->L[d] / nc;
-          cc.range[d] = (int)std::ceil(p->rc / cs - 1e-12);
-          cc.inv_cs[d] = 1.0 / cs;
-        }
-        if ((long long)cc.nc[0] * cc.nc[1] * cc.nc[2] * ncfg > 0x7fffffffLL) return SE_ERR_UNSUPPORTED;
-        const int nccell = cc.nc[0] * cc.nc[1] * cc.nc[2] * ncfg;
-        int *cperm, *cstart2;
-        void *xsc, *xslc, *fsc, *tcc;
-        SE_TRY(buf(p, "rs.xsc", sizeof(V4) * (size_t)std::max(N, 1), &xsc));
-        SE_TRY(buf(p, "rs.xslc", sizeof(V4) * (size_t)std::max(N, 1), &xslc));
-        SE_TRY(buf(p, "rs.fsc", sizeof(T) * C * (size_t)std::max(N, 1), &fsc));
-        SE_TRY(buf(p, "rs.tcellc", sizeof(int) * 3 * (size_t)std::max(NT, 1), &tcc));
-        SE_TRY(counting_sort(p, rs, "ccell", N, nccell, cell_keyfun, src, &cc, &cperm, &cstart2,
-                             [&](const int* key, const int* rank, const int* start, int* perm) {
-                               k_scatter_cell<T><<<grid1d(N, 256), 256, 0, rs>>>(
-                                   cc, key, rank, start, N, src, kernel, strengths, n_rhs, perm, (V4*)xsc,
-                                   (V4*)xslc, (int*)nullptr, (T*)fsc, p->d_status);
-                             }));
-        ++p->launches;
-        k_cell_of<<<grid1d(NT, 256), 256, 0, rs>>>(cc, star ? src : tgt, tperm, NT, (int*)tcc, p->d_status);
-        RealArgs<T> rsp = ra;
-        rsp.cg = cc;
-        rsp.xs = (V4*)xsc;
-        rsp.xsl = (V4*)xslc;
-        rsp.fs = (T*)fsc;
-        rsp.cstart = cstart2;
-        rsp.tcell = (int*)tcc;
-        for (int d = 0; d < 3; ++d) rsp.cs[d] = (T)(p->L[d] / cc.nc[d]);
-        SE_TRY(real_seg_setup(rsp));
         void* work;
         SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 2), &work));
-        SE_TRY(real_launch_blocks<T>(rs, ra, rsp, (int*)work, 0.5 * p->rc, &p->launches));
+        SE_TRY(real_launch_blocks<T>(rs, ra, ra, (int*)work, 0.5 * p->rc, &p->launches));
       } else {
         p->launches += real_launch<T>(rs, ra);
       }

@@ -172,7 +172,8 @@ __device__ __forceinline__ void real_pair(T r0, T r1, T r2, T rr2, T xi, T xi2, 
 // f, the harmonic potential's -2 xi/sqrt(pi) q, nothing for the other kernels) or zeroed
 // (outside r_c). Same arithmetic as real_pair for
 // a pair that counts; with no branch, the terms of two candidates interleave (k_real_blk).
-template <typename T, int KERNEL, int RMAX>
+// QNPRE: the stresslet's q . nu of RHS r is staged at f[STRIDE RMAX + r] (k_real_blk).
+template <typename T, int KERNEL, int RMAX, bool QNPRE = false>
 __device__ __forceinline__ void real_pair_m(T r0, T r1, T r2, T rr2, bool inside, T xi, T xi2, T c2pi,
                                             const T* __restrict__ f, int n_rhs, T* acc) {
   const bool reg = inside && rr2 > T(0);
@@ -238,7 +239,7 @@ __device__ __forceinline__ void real_pair_m(T r0, T r1, T r2, T rr2, bool inside
         const T* nu = q + 3;
         const T rq = r0 * q[0] + r1 * q[1] + r2 * q[2];
         const T rnu = r0 * nu[0] + r1 * nu[1] + r2 * nu[2];
-        const T qn = q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
+        const T qn = QNPRE ? f[STRIDE * RMAX + r] : q[0] * nu[0] + q[1] * nu[1] + q[2] * nu[2];
         const T c3 = Ai * rq * rnu + qn * B;
         const T bq = B * rnu, bn = B * rq;
         acc[3 * r + 0] += c3 * r0 + bq * q[0] + bn * nu[0];
@@ -556,7 +557,8 @@ template <int KERNEL, int RMAX>
 struct BlkComps {
   static constexpr int c = KERNEL == SE_STRESSLET ? 6 : (KERNEL == (SE_STOKESLET | SE_STRESSLET) ? 9
                            : ((KERNEL == SE_HARMONIC_FIELD || KERNEL == SE_HARMONIC) ? 1 : 3));
-  static constexpr int cp = (c * RMAX + 3) & ~3;
+  static constexpr bool t = KERNEL == SE_STRESSLET || KERNEL == (SE_STOKESLET | SE_STRESSLET);
+  static constexpr int cp = (c * RMAX + (t ? RMAX : 0) + 3) & ~3;  // + the staged q . nu per RHS
 };
 
 template <typename T, int KERNEL, int RMAX>
@@ -594,7 +596,7 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
     }
   }
   const T rc = sqrt(a.rc2);
-  const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);  // pre-test on the hi parts, slightly larger
+  const T rcp2 = a.rc2 * T(1.0001) + T(1e-12);  // column trimming, slightly larger than r_c^2
   // unwrapped cells that can hold sources within rc of the box
   int ulo[3], uhi[3];
 #pragma unroll
@@ -702,6 +704,14 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
 #pragma unroll
         for (int c = 0; c < CP; ++c)
           if (c < C) fv[c] = fj[c];
+        if (BlkComps<KERNEL, RMAX>::t) {  // q . nu of each RHS, after the strengths
+          constexpr int ST_ = BlkComps<KERNEL, RMAX>::c, QO = KERNEL == SE_STRESSLET ? 0 : 3;
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) {
+            const T* qv = fv + ST_ * r + QO;
+            fv[ST_ * RMAX + r] = qv[0] * qv[3] + qv[1] * qv[4] + qv[2] * qv[5];
+          }
+        }
       }
     };
     if (total > 0) fetch(0);
@@ -723,22 +733,20 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
       for (int jj = 0; jj < cnt; jj += 2) {
         const V4 sa = sm.pos[jj], sb = sm.pos[jj + 1];
         const V4 la = sm.low[jj], lb = sm.low[jj + 1];
-        T a0 = th.x - sa.x, a1 = th.y - sa.y, a2 = th.z - sa.z;
-        T b0 = th.x - sb.x, b1 = th.y - sb.y, b2 = th.z - sb.z;
-        bool ina = tv && a0 * a0 + a1 * a1 + a2 * a2 < rcp2;
-        bool inb = tv && jj + 1 < cnt && b0 * b0 + b1 * b1 + b2 * b2 < rcp2;
-        if (!__any_sync(FULL, ina || inb)) continue;
-        a0 += tl.x - la.x;
-        a1 += tl.y - la.y;
-        a2 += tl.z - la.z;
-        b0 += tl.x - lb.x;
-        b1 += tl.y - lb.y;
-        b2 += tl.z - lb.z;
+        // exact separations (hi parts and remainders) directly: a pre-test on the hi parts alone
+        // cost more than it saved, since in a dense block almost every candidate is needed
+        const T a0 = (th.x - sa.x) + (tl.x - la.x), a1 = (th.y - sa.y) + (tl.y - la.y),
+                a2 = (th.z - sa.z) + (tl.z - la.z);
+        const T b0 = (th.x - sb.x) + (tl.x - lb.x), b1 = (th.y - sb.y) + (tl.y - lb.y),
+                b2 = (th.z - sb.z) + (tl.z - lb.z);
         const T ra = a0 * a0 + a1 * a1 + a2 * a2, rb = b0 * b0 + b1 * b1 + b2 * b2;
-        ina = ina && ra < a.rc2;
-        inb = inb && rb < a.rc2;
-        real_pair_m<T, KERNEL, RMAX>(a0, a1, a2, ra, ina, xi, xi2, c2pi, sm.str[jj], a.n_rhs, part);
-        real_pair_m<T, KERNEL, RMAX>(b0, b1, b2, rb, inb, xi, xi2, c2pi, sm.str[jj + 1], a.n_rhs, part);
+        const bool ina = tv && ra < a.rc2;
+        const bool inb = tv && jj + 1 < cnt && rb < a.rc2;
+        if (!__any_sync(FULL, ina || inb)) continue;
+        real_pair_m<T, KERNEL, RMAX, BlkComps<KERNEL, RMAX>::t>(a0, a1, a2, ra, ina, xi, xi2, c2pi, sm.str[jj],
+                                                               a.n_rhs, part);
+        real_pair_m<T, KERNEL, RMAX, BlkComps<KERNEL, RMAX>::t>(b0, b1, b2, rb, inb, xi, xi2, c2pi,
+                                                               sm.str[jj + 1], a.n_rhs, part);
       }
       // fold the chunk into the sums (compensated in FP32)
 #pragma unroll
