@@ -110,15 +110,18 @@ __global__ void k_fill_ahat(int n0, int n1, int n2, double h, double R, int biha
   out[2 * i + 1] = 0.0;
 }
 
-// Least-squares fit of the truncated kernel by an even polynomial (SE_FLAG_SPLIT_POLY): over
-// the 2M' box of offsets o (FFT order, r^2 = h^2 |o|^2, t = r^2 / R^2), the sums
-// sums[k] = sum t^k (k = 0..4) and sums[5 + j] = sum A(o) t^j (j = 0..2) of the normal
-// equations, accumulated in FP64 (block partials added atomically).
+// Least-squares fit of the truncated kernel by an even polynomial of degree 6 in r
+// (SE_FLAG_SPLIT_POLY): over the 2M' box of offsets o (FFT order, r^2 = h^2 |o|^2,
+// t = r^2 / R^2), the sums sums[k] = sum t^k (k = 0..6) and sums[7 + j] = sum A(o) t^j
+// (j = 0..3) of the normal equations, accumulated in FP64 (block partials added atomically).
+constexpr int PS_NB = 4;                   // basis 1, t, t^2, t^3
+constexpr int PS_NSUM = 2 * PS_NB - 1 + PS_NB;
 __global__ void k_poly_fit_sums(const double* A, int u0, int u1, int u2, int m0, int m1, int m2, double scale,
                                 double h2R2, double* sums) {
   const int n0 = 2 * m0, n1 = 2 * m1, n2 = 2 * m2;
   const size_t N = (size_t)n0 * n1 * n2;
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  double acc[PS_NSUM];
+  for (int k = 0; k < PS_NSUM; ++k) acc[k] = 0.0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x) {
     const int i2 = (int)(i % n2), i1 = (int)((i / n2) % n1), i0 = (int)(i / ((size_t)n2 * n1));
     const int o0 = i0 < m0 ? i0 : i0 - n0, o1 = i1 < m1 ? i1 : i1 - n1, o2 = i2 < m2 ? i2 : i2 - n2;
@@ -126,21 +129,21 @@ __global__ void k_poly_fit_sums(const double* A, int u0, int u1, int u2, int m0,
     const double v = A[((size_t)s0 * u1 + s1) * u2 + s2] * scale;
     const double t = h2R2 * ((double)o0 * o0 + (double)o1 * o1 + (double)o2 * o2);
     double tk = 1.0;
-    for (int k = 0; k <= 4; ++k) {
+    for (int k = 0; k < 2 * PS_NB - 1; ++k) {
       acc[k] += tk;
-      if (k <= 2) acc[5 + k] += v * tk;
+      if (k < PS_NB) acc[2 * PS_NB - 1 + k] += v * tk;
       tk *= t;
     }
   }
-  __shared__ double red[8][32];
+  __shared__ double red[PS_NSUM][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k = 0; k < 8; ++k) {
+  for (int k = 0; k < PS_NSUM; ++k) {
     double v = acc[k];
     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
     if (lane == 0) red[k][warp] = v;
   }
   __syncthreads();
-  if (threadIdx.x < 8) {
+  if (threadIdx.x < PS_NSUM) {
     double v = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
     atomicAdd(&sums[threadIdx.x], v);
@@ -148,10 +151,11 @@ __global__ void k_poly_fit_sums(const double* A, int u0, int u1, int u2, int m0,
 }
 
 // truncate A_R to the 2M' offsets around the origin (FFT order), normalise the inverse
-// transform, take out the fitted polynomial (SE_FLAG_SPLIT_POLY: pa0 + pa1 r^2 + pa2 r^4, in
-// the units of the normalised samples; zero otherwise) and mollify the biharmonic (Sec. 3.5)
+// transform, take out the fitted polynomial (SE_FLAG_SPLIT_POLY: pa0 + pa1 r^2 + pa2 r^4 +
+// pa3 r^6, in the units of the normalised samples; zero otherwise) and mollify the biharmonic
+// (Sec. 3.5)
 __global__ void k_trunc_moll(const double* A, int u0, int u1, int u2, int m0, int m1, int m2, int biharm,
-                             double scale, double h, double pa0, double pa1, double pa2, double* At) {
+                             double scale, double h, double pa0, double pa1, double pa2, double pa3, double* At) {
   const int n0 = 2 * m0, n1 = 2 * m1, n2 = 2 * m2;
   const size_t N = (size_t)n0 * n1 * n2;
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -162,7 +166,7 @@ __global__ void k_trunc_moll(const double* A, int u0, int u1, int u2, int m0, in
   double v = A[((size_t)s0 * u1 + s1) * u2 + s2] * scale;
   if (biharm) {
     const double r2 = h * h * ((double)o0 * o0 + (double)o1 * o1 + (double)o2 * o2);
-    v -= pa0 + r2 * (pa1 + r2 * pa2);
+    v -= pa0 + r2 * (pa1 + r2 * (pa2 + r2 * pa3));
     // mu = (f(3), f(2), f(1), f(0), 1, ..., 1, f(0), f(1), f(2), f(3)) in natural order
     const double a = 2.0 / 7.0 * sqrt(log(100.0));
     const int nat[3] = {o0 + m0, o1 + m1, o2 + m2};
@@ -558,56 +562,58 @@ static se_status precompute_0p(se_plan_t* p, int biharm, DevBuf* out) {
     cufftDestroy(h1);
     h1ok = false;
     if (cudaMalloc(&at, sizeof(double) * nt) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
-    // SE_FLAG_SPLIT_POLY: fit c0 + c1 r^2 + c2 r^4 to the biharmonic samples (normal equations in
-    // t = r^2 / R^2, solved in FP64 with partial pivoting)
-    double pa[3] = {0, 0, 0};
+    // SE_FLAG_SPLIT_POLY: fit c0 + c1 r^2 + c2 r^4 + c3 r^6 to the biharmonic samples (normal
+    // equations in t = r^2 / R^2, solved in FP64 with partial pivoting)
+    double pa[PS_NB] = {0, 0, 0, 0};
     p->poly_on = false;
     if (biharm && (p->flags & SE_FLAG_SPLIT_POLY)) {
       double* sums = nullptr;
-      if (cudaMalloc(&sums, sizeof(double) * 8) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
-      cudaMemsetAsync(sums, 0, sizeof(double) * 8, p->stream);
+      if (cudaMalloc(&sums, sizeof(double) * PS_NSUM) != cudaSuccess) { st = SE_ERR_NOMEM; break; }
+      cudaMemsetAsync(sums, 0, sizeof(double) * PS_NSUM, p->stream);
       const double R2 = p->R * p->R;
       k_poly_fit_sums<<<std::min(grid1d((long long)nt, 256), 152 * 8), 256, 0, p->stream>>>(
           areal, u[0], u[1], u[2], g.m[0], g.m[1], g.m[2], 1.0 / (double)nu, g.h * g.h / R2, sums);
-      double hs[8];
+      double hs[PS_NSUM];
       const bool ok = cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, p->stream) == cudaSuccess &&
                       cudaStreamSynchronize(p->stream) == cudaSuccess;
       cudaFree(sums);
       if (!ok) { st = SE_ERR_CUDA; break; }
-      double Mx[3][4];
-      for (int a = 0; a < 3; ++a) {
-        for (int b = 0; b < 3; ++b) Mx[a][b] = hs[a + b];
-        Mx[a][3] = hs[5 + a];
+      double Mx[PS_NB][PS_NB + 1];
+      for (int a = 0; a < PS_NB; ++a) {
+        for (int b = 0; b < PS_NB; ++b) Mx[a][b] = hs[a + b];
+        Mx[a][PS_NB] = hs[2 * PS_NB - 1 + a];
       }
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < PS_NB; ++c) {
         int piv = c;
-        for (int a = c + 1; a < 3; ++a)
+        for (int a = c + 1; a < PS_NB; ++a)
           if (std::fabs(Mx[a][c]) > std::fabs(Mx[piv][c])) piv = a;
-        for (int b = 0; b < 4; ++b) std::swap(Mx[c][b], Mx[piv][b]);
+        for (int b = 0; b <= PS_NB; ++b) std::swap(Mx[c][b], Mx[piv][b]);
         if (!(std::fabs(Mx[c][c]) > 0)) { st = SE_ERR_UNSUPPORTED; break; }
-        for (int a = c + 1; a < 3; ++a) {
+        for (int a = c + 1; a < PS_NB; ++a) {
           const double f = Mx[a][c] / Mx[c][c];
-          for (int b = c; b < 4; ++b) Mx[a][b] -= f * Mx[c][b];
+          for (int b = c; b <= PS_NB; ++b) Mx[a][b] -= f * Mx[c][b];
         }
       }
       if (st != SE_OK) break;
-      double b[3];
-      for (int a = 2; a >= 0; --a) {
-        double v = Mx[a][3];
-        for (int c = a + 1; c < 3; ++c) v -= Mx[a][c] * b[c];
+      double b[PS_NB];
+      for (int a = PS_NB - 1; a >= 0; --a) {
+        double v = Mx[a][PS_NB];
+        for (int c = a + 1; c < PS_NB; ++c) v -= Mx[a][c] * b[c];
         b[a] = v / Mx[a][a];
       }
       // from the t basis to r^2 powers, in the units of the samples (h^3 B_R)
-      pa[0] = b[0];
-      pa[1] = b[1] / R2;
-      pa[2] = b[2] / (R2 * R2);
+      double rp = 1.0;
       const double h3 = g.h * g.h * g.h;
-      for (int k = 0; k < 3; ++k) p->poly_c[k] = pa[k] / h3;
+      for (int k = 0; k < PS_NB; ++k) {
+        pa[k] = b[k] / rp;
+        p->poly_c[k] = pa[k] / h3;
+        rp *= R2;
+      }
       p->poly_on = true;
     }
     k_trunc_moll<<<grid1d((long long)nt, 256), 256, 0, p->stream>>>(areal, u[0], u[1], u[2], g.m[0], g.m[1],
                                                                    g.m[2], biharm, 1.0 / (double)nu, g.h, pa[0],
-                                                                   pa[1], pa[2], at);
+                                                                   pa[1], pa[2], pa[3], at);
     cudaStreamSynchronize(p->stream);
     cudaFree(areal);
     areal = nullptr;
@@ -1066,105 +1072,121 @@ se_status gauge_correction(se_plan_t* p, const T* f, int stride, int n, int n_rh
   return SE_OK;
 }
 
-// The potential of the polynomial p = c0 + c1 r^2 + c2 r^4 taken out of the truncated
-// biharmonic (SE_FLAG_SPLIT_POLY), added back exactly. With r = x - y, the stokeslet operator
-// (delta lap - grad grad) maps r^2 to 4 delta and r^4 to 16 r^2 delta - 8 r r^T; the stresslet
-// operator ((delta_jl d_m + delta_mj d_l + delta_lm d_j) lap - 2 d_j d_l d_m) maps r^2 to 0
-// and r^4 to 24 (delta_jl r_m + delta_mj r_l + delta_lm r_j). Summed over the sources these are
-// polynomials in x with FP64 moments of the sources (per RHS, 37 sums):
-//   stokeslet  F0 = sum f, F1_aj = sum y_a f_j, F2 = sum |y|^2 f, G = sum y (y . f)
-//   stresslet  Qn_jm = sum q_j nu_m, a = sum q (y . nu), b = sum nu (y . q), s = sum q . nu,
-//              d = sum y (q . nu).
-constexpr int POLY_NS = 37;
+// The potential of the polynomial p = sum_n c_n r^(2n) (n = 0..3) taken out of the truncated
+// biharmonic (SE_FLAG_SPLIT_POLY), added back exactly. For a source at y, the stokeslet and
+// stresslet operators map r^(2n), r = x - y, to polynomials in r (the constant c0 to zero);
+// expanded in monomials x^a of the target and y^b of the source (tables of se_poly_split.h,
+// generated symbolically), the summed potential is a polynomial of degree <= 4 in x:
+//   u_j(x) = sum_a C_ja x^a,  C_ja = sum_n c_n sum_(b,k) T_n[j][a][b][k] M[b][k],
+//   M[b][k] = sum_sources y^b s_k,  s = f (k = 0..2) or the products q_l nu_m (k = 3 l + m).
+// The Fourier part sees p through the Hasimoto screening: convolving a polynomial with the
+// radial screening function applies its transform at k^2 = -Lap, 1 - Lap^2/(32 xi^4) -
+// Lap^3/(192 xi^6) + ..., so r^2 and r^4 pass unchanged up to constants (annihilated by both
+// operators) and r^6 gains -840/(32 xi^4) r^2, which is added to c1. Three kernels: the
+// moments (one thread per (b, k), points staged with their monomials in shared memory), the
+// coefficients C, and the evaluation at the targets (FP64).
+#define SE_PS_STORAGE static __constant__
+#include "se_poly_split.h"
+
+constexpr int PS_MS = SE_PS_NMONO * 3;     // stokeslet moments
+constexpr int PS_MT = SE_PS_NMONO3 * 9;    // stresslet moments (degree <= 3)
+constexpr int PS_NM = PS_MS + PS_MT;       // per RHS
+constexpr int PS_TP = 64;                  // points per shared-memory tile
+
 template <typename T>
-__global__ void k_poly_moments(const double* __restrict__ x, const T* __restrict__ f, int n, int cin, int soff,
-                               int toff, double* __restrict__ sums) {
+__global__ void __launch_bounds__(320) k_poly_moments(const double* __restrict__ x, const T* __restrict__ f, int n,
+                                                      int cin, int soff, int toff, double* __restrict__ sums) {
+  __shared__ T mono[PS_TP][SE_PS_NMONO];
+  __shared__ T str[PS_TP][12];
   const int r = blockIdx.y;
-  double acc[POLY_NS];
-#pragma unroll
-  for (int k = 0; k < POLY_NS; ++k) acc[k] = 0.0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const double y[3] = {x[3 * i], x[3 * i + 1], x[3 * i + 2]};
-    const T* fi = f + ((size_t)r * n + i) * cin;
-    if (soff >= 0) {
-      const double g[3] = {(double)fi[soff], (double)fi[soff + 1], (double)fi[soff + 2]};
-      const double yy = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
-      const double yg = y[0] * g[0] + y[1] * g[1] + y[2] * g[2];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        acc[j] += g[j];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) acc[3 + 3 * a + j] += y[a] * g[j];
-        acc[12 + j] += yy * g[j];
-        acc[15 + j] += y[j] * yg;
+  const int t = threadIdx.x;
+  // this thread's moment: (b, k) of the stokeslet or of the stresslet part
+  const bool ms = t < PS_MS, mt = t >= PS_MS && t < PS_NM;
+  const int b = ms ? t / 3 : (t - PS_MS) / 9, kk = ms ? t % 3 : 3 + (t - PS_MS) % 9;
+  const bool active = (ms && soff >= 0) || (mt && toff >= 0);
+  double acc = 0.0;
+  for (int base = blockIdx.x * PS_TP; base < n; base += gridDim.x * PS_TP) {
+    __syncthreads();
+    for (int e = t; e < PS_TP * (SE_PS_NMONO + 12); e += blockDim.x) {
+      const int pnt = e / (SE_PS_NMONO + 12), c = e % (SE_PS_NMONO + 12);
+      const int i = base + pnt;
+      T v = T(0);
+      if (i < n) {
+        if (c < SE_PS_NMONO) {
+          const T y0 = (T)x[3 * i], y1 = (T)x[3 * i + 1], y2 = (T)x[3 * i + 2];
+          v = T(1);
+          for (int q = 0; q < se_ps_mono[c][0]; ++q) v *= y0;
+          for (int q = 0; q < se_ps_mono[c][1]; ++q) v *= y1;
+          for (int q = 0; q < se_ps_mono[c][2]; ++q) v *= y2;
+          mono[pnt][c] = v;
+          continue;
+        }
+        const int s = c - SE_PS_NMONO;
+        const T* fi = f + ((size_t)r * n + i) * cin;
+        if (s < 3) v = soff >= 0 ? fi[soff + s] : T(0);
+        else v = toff >= 0 ? fi[toff + (s - 3) / 3] * fi[toff + 3 + (s - 3) % 3] : T(0);
+      } else if (c < SE_PS_NMONO) {
+        mono[pnt][c] = T(0);
+        continue;
       }
+      str[pnt][c - SE_PS_NMONO] = v;
     }
-    if (toff >= 0) {
-      const double q[3] = {(double)fi[toff], (double)fi[toff + 1], (double)fi[toff + 2]};
-      const double v[3] = {(double)fi[toff + 3], (double)fi[toff + 4], (double)fi[toff + 5]};
-      const double yv = y[0] * v[0] + y[1] * v[1] + y[2] * v[2];
-      const double yq = y[0] * q[0] + y[1] * q[1] + y[2] * q[2];
-      const double qv = q[0] * v[0] + q[1] * v[1] + q[2] * v[2];
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-#pragma unroll
-        for (int m = 0; m < 3; ++m) acc[18 + 3 * j + m] += q[j] * v[m];
-        acc[27 + j] += q[j] * yv;
-        acc[30 + j] += v[j] * yq;
-        acc[34 + j] += y[j] * qv;
-      }
-      acc[33] += qv;
+    __syncthreads();
+    if (active) {
+      const int np = min(PS_TP, n - base);
+      T part = T(0);
+      for (int pnt = 0; pnt < np; ++pnt) part += mono[pnt][b] * str[pnt][kk];
+      acc += (double)part;
     }
   }
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < POLY_NS; ++k) {
-    double v = acc[k];
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    if (lane == 0 && v != 0.0) atomicAdd(&sums[r * POLY_NS + k], v);
-  }
+  if (active && acc != 0.0) atomicAdd(&sums[(size_t)r * PS_NM + t], acc);
+}
+
+// C[r][j][a] = sum over the table rows of c_n T M (one thread per (RHS, j, a))
+__global__ void k_poly_coeffs(const double* __restrict__ sums, int n_rhs, int has_s, int has_t, double c1,
+                              double c2, double c3, double* __restrict__ C) {
+  const int id = blockIdx.x * blockDim.x + threadIdx.x;
+  if (id >= n_rhs * 3 * SE_PS_NMONO) return;
+  const int r = id / (3 * SE_PS_NMONO), j = (id / SE_PS_NMONO) % 3, a = id % SE_PS_NMONO;
+  const double cn[4] = {0.0, c1, c2, c3};
+  const double* M = sums + (size_t)r * PS_NM;
+  double v = 0.0;
+  if (has_s)
+    for (int q = 0; q < SE_PS_NS; ++q) {
+      const SePsTerm& e = se_ps_stokeslet[q];
+      if (e.j == j && e.a == a) v += cn[e.n] * e.c * M[e.b * 3 + e.k];
+    }
+  if (has_t)
+    for (int q = 0; q < SE_PS_NT; ++q) {
+      const SePsTerm& e = se_ps_stresslet[q];
+      if (e.j == j && e.a == a) v += cn[e.n] * e.c * M[PS_MS + e.b * 9 + e.k];
+    }
+  C[id] = v;
 }
 
 template <typename T>
-__global__ void k_poly_apply(const double* __restrict__ t, int nt, int n_rhs, const double* __restrict__ sums,
-                             double c1, double c2, int has_s, int has_t, T* __restrict__ u) {
+__global__ void k_poly_apply(const double* __restrict__ t, int nt, int n_rhs, const double* __restrict__ C,
+                             T* __restrict__ u) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nt) return;
-  const double x[3] = {t[3 * i], t[3 * i + 1], t[3 * i + 2]};
-  const double xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-  for (int r = 0; r < n_rhs; ++r) {
-    const double* S = sums + r * POLY_NS;
-    double up[3] = {0, 0, 0};
-    if (has_s) {
-      const double* F0 = S;
-      const double* F1 = S + 3;  // F1[a][j] at 3 a + j
-      const double* F2 = S + 12;
-      const double* G = S + 15;
-      const double xF0 = x[0] * F0[0] + x[1] * F0[1] + x[2] * F0[2];
-      const double tr = F1[0] + F1[4] + F1[8];
-      for (int j = 0; j < 3; ++j) {
-        const double xF1 = x[0] * F1[j] + x[1] * F1[3 + j] + x[2] * F1[6 + j];           // sum_a x_a F1[a][j]
-        const double F1x = x[0] * F1[3 * j] + x[1] * F1[3 * j + 1] + x[2] * F1[3 * j + 2];  // sum_a x_a F1[j][a]
-        const double r2f = xx * F0[j] - 2.0 * xF1 + F2[j];
-        const double rrf = x[j] * xF0 - x[j] * tr - F1x + G[j];
-        up[j] += 4.0 * c1 * F0[j] + c2 * (16.0 * r2f - 8.0 * rrf);
-      }
-    }
-    if (has_t) {
-      const double* Qn = S + 18;  // Qn[j][m] at 3 j + m
-      const double* a = S + 27;
-      const double* b = S + 30;
-      const double s = S[33];
-      const double* d = S + 34;
-      for (int j = 0; j < 3; ++j) {
-        double v = 0;
-        for (int m = 0; m < 3; ++m) v += x[m] * (Qn[3 * j + m] + Qn[3 * m + j]);
-        up[j] += 24.0 * c2 * (v - a[j] - b[j] + x[j] * s - d[j]);
-      }
-    }
-    T* o = u + ((size_t)r * nt + i) * 3;
-    for (int j = 0; j < 3; ++j) o[j] += (T)up[j];
+  const double x0 = t[3 * i], x1 = t[3 * i + 1], x2 = t[3 * i + 2];
+  double xm[SE_PS_NMONO];
+#pragma unroll
+  for (int a = 0; a < SE_PS_NMONO; ++a) {
+    double v = 1.0;
+    for (int q = 0; q < se_ps_mono[a][0]; ++q) v *= x0;
+    for (int q = 0; q < se_ps_mono[a][1]; ++q) v *= x1;
+    for (int q = 0; q < se_ps_mono[a][2]; ++q) v *= x2;
+    xm[a] = v;
   }
+  for (int r = 0; r < n_rhs; ++r)
+    for (int j = 0; j < 3; ++j) {
+      const double* c = C + ((size_t)r * 3 + j) * SE_PS_NMONO;
+      double v = 0.0;
+#pragma unroll
+      for (int a = 0; a < SE_PS_NMONO; ++a) v += c[a] * xm[a];
+      u[((size_t)r * nt + i) * 3 + j] += (T)v;
+    }
 }
 
 template <typename T>
@@ -1173,17 +1195,22 @@ se_status poly_correction(se_plan_t* p, int kernel, const double* x, const T* f,
   if (!p->poly_on || p->D != 0 || n <= 0 || nt <= 0) return SE_OK;
   const int has_s = (kernel & SE_STOKESLET) ? 1 : 0, has_t = (kernel & SE_STRESSLET) ? 1 : 0;
   if (!has_s && !has_t) return SE_OK;
-  void* sums;
-  SE_TRY(buf(p, "poly.sums", sizeof(double) * POLY_NS * n_rhs, &sums));
-  SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * POLY_NS * n_rhs, p->stream));
+  void *sums, *coef;
+  SE_TRY(buf(p, "poly.sums", sizeof(double) * PS_NM * n_rhs, &sums));
+  SE_TRY(buf(p, "poly.coef", sizeof(double) * 3 * SE_PS_NMONO * n_rhs, &coef));
+  SE_CUDA(cudaMemsetAsync(sums, 0, sizeof(double) * PS_NM * n_rhs, p->stream));
   const int cin = kernel_comps(kernel);
   const int soff = has_s ? 0 : -1, toff = has_t ? (has_s ? 3 : 0) : -1;
+  const double xi2 = p->xi * p->xi;
+  const double c1 = p->poly_c[1] - 840.0 / 32.0 * p->poly_c[3] / (xi2 * xi2);
   ++p->launches;
-  dim3 gr(std::min(grid1d(n, 256), 152 * 2), n_rhs);
-  k_poly_moments<T><<<gr, 256, 0, p->stream>>>(x, f, n, cin, soff, toff, (double*)sums);
+  dim3 gr(std::min(std::max((n + PS_TP - 1) / PS_TP, 1), 152 * 2), n_rhs);
+  k_poly_moments<T><<<gr, 320, 0, p->stream>>>(x, f, n, cin, soff, toff, (double*)sums);
   ++p->launches;
-  k_poly_apply<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(t, nt, n_rhs, (const double*)sums, p->poly_c[1],
-                                                          p->poly_c[2], has_s, has_t, u);
+  k_poly_coeffs<<<grid1d(3LL * SE_PS_NMONO * n_rhs, 128), 128, 0, p->stream>>>(
+      (const double*)sums, n_rhs, has_s, has_t, c1, p->poly_c[2], p->poly_c[3], (double*)coef);
+  ++p->launches;
+  k_poly_apply<T><<<grid1d(nt, 256), 256, 0, p->stream>>>(t, nt, n_rhs, (const double*)coef, u);
   SE_CUDA(cudaGetLastError());
   return SE_OK;
 }

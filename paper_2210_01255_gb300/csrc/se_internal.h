@@ -149,7 +149,7 @@ struct se_plan_t {
   se::DevBuf ftab[3][3];   // [class][direction] free-direction factors
   se::DevBuf mod0[4];      // k^P = 0 modified-kernel tables
   se::DevBuf atr[2];       // D = 0 precomputed kernels: 0 harmonic, 1 biharmonic
-  double poly_c[3] = {0, 0, 0};  // SE_FLAG_SPLIT_POLY: c0 + c1 r^2 + c2 r^4 taken out of B_R
+  double poly_c[4] = {0, 0, 0, 0};  // SE_FLAG_SPLIT_POLY: c0 + c1 r^2 + c2 r^4 + c3 r^6 taken out of B_R
   bool poly_on = false;
   std::vector<std::vector<int>> group_off;  // se_eval_group: point offsets last uploaded, per sub-group
 

@@ -1,6 +1,7 @@
 """SE_FLAG_SPLIT_POLY: the free-space truncated biharmonic with a fitted polynomial
-c0 + c1 r^2 + c2 r^4 taken out before its transform, the polynomial's potential added back from
-FP64 moment sums of the sources. Through the C ABI:
+c0 + c1 r^2 + c2 r^4 + c3 r^6 taken out before its transform, the polynomial's potential (as
+the Hasimoto screening passes it on) added back from moment sums of the sources. Through the C
+ABI:
   * FP64: the whole potential against the exact direct sums (1e-10) for the stokeslet, the
     stresslet and both fused, several RHS and explicit targets; and against the same plan
     without the flag (the two differ by the method's truncation error only);
