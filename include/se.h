@@ -137,11 +137,12 @@ enum { SE_FLAG_REAL_BLOCKS = 4 };
  * sizes are the paper's multiples of f_M. */
 enum { SE_FLAG_FFT_SIZES = 8 };
 /* se_opts.flags: for D = 0, the precomputed truncated biharmonic kernel (stokeslet,
- * stresslet; Sec. 3.5) is split as (B_R - p) + p with p(r) = c0 + c1 r^2 + c2 r^4 the least-
- * squares fit of B_R over the 2M' box of offsets (FP64, at plan creation). The Fourier-space
- * step uses B_R - p; the potential of p is added exactly from FP64 moment sums of the sources
- * (the operators of the stokeslet and stresslet turn p into polynomials of degree 2 and 1 in
- * x - y; the Hasimoto screening leaves p unchanged up to a constant that they annihilate).
+ * stresslet; Sec. 3.5) is split as (B_R - p) + p with p(r) = c0 + c1 r^2 + c2 r^4 + c3 r^6 the
+ * least-squares fit of B_R over the 2M' box of offsets (FP64, at plan creation). The
+ * Fourier-space step uses B_R - p; the potential of p is added exactly from moment sums of the
+ * sources (the operators of the stokeslet and stresslet turn p into polynomials of degree 4
+ * and 3 in x - y; the Hasimoto screening changes p only by constants, which they annihilate,
+ * and by a multiple of r^2 for the r^6 term, which is included).
  * The potential is the same to the truncation error of the method, but the large values of
  * the truncated biharmonic at small wavenumbers, which multiply the FP32 rounding of the
  * transforms, shrink: in FP32 the rounding of the free-space Fourier part approaches that of

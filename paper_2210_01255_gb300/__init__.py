@@ -19,8 +19,8 @@ PART_REAL, PART_FOURIER, PART_CORR, PART_ALL = 1, 2, 4, 7
 FLAG_TC_GRIDDING = 1  # se_opts.flags: FP32 gridding (P <= 16) on the tensor cores (tcgen05)
 FLAG_TEST_TIMEOUT = 2  # se_opts.flags, testing aid: the tensor-core gridding's bounded waits give up at once
 FLAG_REAL_BLOCKS = 4  # se_opts.flags: real-space sum with the dense-block path (k_real_blk)
-FLAG_FFT_SIZES = 8
-FLAG_SPLIT_POLY = 16  # se_opts.flags: grid extents rounded up to FFT-friendly (7-smooth) multiples of f_M
+FLAG_FFT_SIZES = 8  # se_opts.flags: grid extents rounded up to FFT-friendly (7-smooth) sizes
+FLAG_SPLIT_POLY = 16  # se_opts.flags: D = 0 biharmonic split into (B_R - p) + p, p of degree 6
 KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
            "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD,
            "harmonic": HARMONIC}

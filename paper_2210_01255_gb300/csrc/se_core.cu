@@ -1115,8 +1115,9 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
       if (p->timers.on) cudaEventRecord(p->timers.ev[10], rs);
       if (blocks) {
         void* work;
-        SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 2), &work));
-        SE_TRY(real_launch_blocks<T>(rs, ra, ra, (int*)work, 0.5 * p->rc, &p->launches));
+        SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 3), &work));
+        // with the Fourier part running concurrently, one CTA per SM is left to its kernels
+        SE_TRY(real_launch_blocks<T>(rs, ra, ra, (int*)work, 0.5 * p->rc, overlap ? 1 : 0, &p->launches));
       } else {
         p->launches += real_launch<T>(rs, ra);
       }

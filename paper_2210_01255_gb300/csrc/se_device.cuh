@@ -199,9 +199,11 @@ int real_launch(cudaStream_t st, const RealArgs<T>& a);
 // the dense-block path: targets grouped in blocks of 32 consecutive (cell-sorted) targets;
 // blocks whose targets lie within a box of side <= thr go to the block kernel, the others'
 // targets to the sparse kernel, which runs with `sparse` (the same targets, its own cell list
-// of coarser cells, or `a` itself). work: int scratch of >= ceil(ntgt / 32) + ntgt + 2 entries.
+// of coarser cells, or `a` itself). work: int scratch of >= ceil(ntgt / 32) + ntgt + 3 entries.
+// leave: CTAs per SM that the persistent block kernel leaves free for kernels running
+// concurrently on another stream.
 template <typename T>
 se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, const RealArgs<T>& sparse, int* work, double thr,
-                             int* launches);
+                             int leave, int* launches);
 
 }  // namespace se

@@ -561,20 +561,17 @@ struct BlkComps {
   static constexpr int cp = (c * RMAX + (t ? RMAX : 0) + 3) & ~3;  // + the staged q . nu per RHS
 };
 
+// one listed block of 32 targets, evaluated by one warp (sm: the warp's own staging area)
 template <typename T, int KERNEL, int RMAX>
-__global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const int* __restrict__ blist,
-                                                            const int* __restrict__ bcount) {
+__device__ __forceinline__ void real_blk_one(const RealArgs<T>& a, int blk,
+                                             BlkSmem<T, BlkComps<KERNEL, RMAX>::cp>& sm) {
   constexpr int CP = BlkComps<KERNEL, RMAX>::cp;
   constexpr int NO = RsOut<KERNEL>::value;
-  __shared__ __align__(16) BlkSmem<T, CP> sm_all[RB_WARPS];
   typedef typename Vec4<T>::type V4;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int bi = blockIdx.x * RB_WARPS + warp;
-  if (bi >= *bcount) return;  // warp-uniform
-  BlkSmem<T, CP>& sm = sm_all[warp];
+  const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
   const CellGeom& g = a.cg;
-  const int s0 = blist[bi] * 32;
+  const int s0 = blk * 32;
   const int nt = min(32, a.ntgt - s0);
   const bool tv = lane < nt;
   const int s = s0 + (tv ? lane : 0);
@@ -772,6 +769,31 @@ __global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const
   }
 }
 
+// The listed blocks, a warp each: with next == nullptr one warp per listed block (grid over
+// all of them); otherwise a grid of a few CTAs per SM whose warps take the next block from the
+// counter *next until the list is done, leaving the rest of each SM to the kernels of the
+// Fourier part running concurrently on the other stream.
+template <typename T, int KERNEL, int RMAX>
+__global__ void __launch_bounds__(32 * RB_WARPS) k_real_blk(RealArgs<T> a, const int* __restrict__ blist,
+                                                            const int* __restrict__ bcount, int* next) {
+  __shared__ __align__(16) BlkSmem<T, BlkComps<KERNEL, RMAX>::cp> sm_all[RB_WARPS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nb = *bcount;
+  if (next == nullptr) {
+    const int bi = blockIdx.x * RB_WARPS + warp;
+    if (bi < nb) real_blk_one<T, KERNEL, RMAX>(a, blist[bi], sm_all[warp]);  // warp-uniform
+    return;
+  }
+  for (;;) {
+    int bi = 0;
+    if (lane == 0) bi = atomicAdd(next, 1);
+    bi = __shfl_sync(0xffffffffu, bi, 0);
+    if (bi >= nb) break;
+    real_blk_one<T, KERNEL, RMAX>(a, blist[bi], sm_all[warp]);
+    __syncwarp();
+  }
+}
+
 // Blocks of 32 consecutive sorted targets: a block whose targets lie in a box of side <= thr
 // (block-relative coordinates) is listed for k_real_blk, the targets of any other block for
 // k_real. One warp per block; the list order depends on the atomics, the results do not
@@ -836,22 +858,36 @@ int real_launch(cudaStream_t st, const RealArgs<T>& a) {
 }
 
 template <typename T, int K, int R>
-static void launch_blk_k(cudaStream_t st, const RealArgs<T>& a, const int* blist, const int* bcount, int nblk) {
-  k_real_blk<T, K, R><<<grid1d(nblk, RB_WARPS), 32 * RB_WARPS, 0, st>>>(a, blist, bcount);
+static void launch_blk_k(cudaStream_t st, const RealArgs<T>& a, const int* blist, const int* bcount, int nblk,
+                         int* next, int leave) {
+  // persistent: as many CTAs per SM as fit, less `leave`, on every SM
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_real_blk<T, K, R>, 32 * RB_WARPS, 0) != cudaSuccess)
+      per_sm = 0;
+    cudaGetLastError();
+  }
+  const int ctas = std::max(1, per_sm - leave) * std::max(sms, 1);
+  if (per_sm <= 0) next = nullptr;
+  k_real_blk<T, K, R><<<next ? ctas : grid1d(nblk, RB_WARPS), 32 * RB_WARPS, 0, st>>>(a, blist, bcount, next);
 }
 template <typename T, int R>
-static void launch_blk(cudaStream_t st, const RealArgs<T>& a, const int* blist, const int* bcount, int nblk) {
-  if (a.kernel == SE_STOKESLET) launch_blk_k<T, SE_STOKESLET, R>(st, a, blist, bcount, nblk);
-  else if (a.kernel == SE_ROTLET) launch_blk_k<T, SE_ROTLET, R>(st, a, blist, bcount, nblk);
-  else if (a.kernel == SE_STRESSLET) launch_blk_k<T, SE_STRESSLET, R>(st, a, blist, bcount, nblk);
-  else if (a.kernel == SE_HARMONIC_FIELD) launch_blk_k<T, SE_HARMONIC_FIELD, R>(st, a, blist, bcount, nblk);
-  else if (a.kernel == SE_HARMONIC) launch_blk_k<T, SE_HARMONIC, R>(st, a, blist, bcount, nblk);
-  else launch_blk_k<T, SE_STOKESLET | SE_STRESSLET, R>(st, a, blist, bcount, nblk);
+static void launch_blk(cudaStream_t st, const RealArgs<T>& a, const int* blist, const int* bcount, int nblk,
+                       int* next, int leave) {
+  if (a.kernel == SE_STOKESLET) launch_blk_k<T, SE_STOKESLET, R>(st, a, blist, bcount, nblk, next, leave);
+  else if (a.kernel == SE_ROTLET) launch_blk_k<T, SE_ROTLET, R>(st, a, blist, bcount, nblk, next, leave);
+  else if (a.kernel == SE_STRESSLET) launch_blk_k<T, SE_STRESSLET, R>(st, a, blist, bcount, nblk, next, leave);
+  else if (a.kernel == SE_HARMONIC_FIELD) launch_blk_k<T, SE_HARMONIC_FIELD, R>(st, a, blist, bcount, nblk, next, leave);
+  else if (a.kernel == SE_HARMONIC) launch_blk_k<T, SE_HARMONIC, R>(st, a, blist, bcount, nblk, next, leave);
+  else launch_blk_k<T, SE_STOKESLET | SE_STRESSLET, R>(st, a, blist, bcount, nblk, next, leave);
 }
 
 template <typename T>
 se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, const RealArgs<T>& sparse, int* work, double thr,
-                             int* launches) {
+                             int leave, int* launches) {
   if (a.ntgt <= 0) return SE_OK;
   if (a.n_rhs > 4) {  // the block kernel keeps 3 x 3 n_rhs sums per lane: many RHS use k_real
     *launches += real_launch(st, sparse);
@@ -871,13 +907,13 @@ se_status real_launch_blocks(cudaStream_t st, RealArgs<T> a, const RealArgs<T>& 
     ab.maxseg = maxseg;
     ab.cols_per_round = std::min(32, RB_SEGCAP / maxseg);
   }
-  int* counts = work;
-  int* blist = work + 2;
+  int* counts = work;  // listed blocks, sparse targets, the persistent grid's next block
+  int* blist = work + 3;
   int* tlist = blist + nblk;
-  SE_CUDA(cudaMemsetAsync(counts, 0, 2 * sizeof(int), st));
+  SE_CUDA(cudaMemsetAsync(counts, 0, 3 * sizeof(int), st));
   k_real_classify<T><<<grid1d(nblk, 4), 128, 0, st>>>(a, (T)thr, nblk, blist, tlist, counts);
-  if (a.n_rhs <= 1) launch_blk<T, 1>(st, ab, blist, counts, nblk);
-  else launch_blk<T, 4>(st, ab, blist, counts, nblk);
+  if (a.n_rhs <= 1) launch_blk<T, 1>(st, ab, blist, counts, nblk, counts + 2, leave);
+  else launch_blk<T, 4>(st, ab, blist, counts, nblk, counts + 2, leave);
   RealArgs<T> b = sparse;  // the targets of the other blocks, on the sparse path's own cell list
   b.tlist = tlist;
   b.tcount = counts + 1;
@@ -892,8 +928,8 @@ template se_status real_seg_setup<double>(RealArgs<double>&);
 template int real_launch<float>(cudaStream_t, const RealArgs<float>&);
 template int real_launch<double>(cudaStream_t, const RealArgs<double>&);
 template se_status real_launch_blocks<float>(cudaStream_t, RealArgs<float>, const RealArgs<float>&, int*, double,
-                                             int*);
+                                             int, int*);
 template se_status real_launch_blocks<double>(cudaStream_t, RealArgs<double>, const RealArgs<double>&, int*, double,
-                                              int*);
+                                              int, int*);
 
 }  // namespace se
