@@ -202,6 +202,8 @@ def tuned(cfg, item, prec, stream, flags=0):
             t = se.se_autotune(cfg["D"], cfg["box"], se.KERNELS[k], Q, item["N"], cfg["tol"] / 10.0, opts=o)
             if cfg["D"] == 0 and prec == "fp32" and se.KERNELS[k] & (se.STOKESLET | se.STRESSLET):
                 t["opts"].flags |= se.FLAG_SPLIT_POLY   # as the timed selection does
+            if cfg["D"] == 0:
+                t["opts"].flags |= se.FLAG_FFT_TIMED    # likewise
         elif cfg.get("autotune") == "timed":
             o.flags |= flags
             t = se.se_autotune_timed(cfg["D"], cfg["box"], k, Q, item["xdev"], item["fdev"], item["R"],
@@ -223,7 +225,8 @@ def make_plan(cfg, item, prec, stream, flags=0):
     import paper_2210_01255_gb300 as se_
     t, o = tuned(cfg, item, "fp32" if cfg["prec"] == "fp32" else "fp64", stream, flags)
     # the gridding choice of the command line; the real-space path the selection chose
-    o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES | se_.FLAG_SPLIT_POLY))
+    o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES | se_.FLAG_SPLIT_POLY |
+                                          se_.FLAG_FFT_TIMED))
     if REAL_PATH == "blocks":
         o.flags |= se_.FLAG_REAL_BLOCKS
     elif REAL_PATH == "target":
@@ -709,6 +712,8 @@ def main():
         info0 = it["plan"].info()
         it["grid_n"] = list(info0.n)
         it["grid_m"] = list(info0.m)
+        if cfg["D"] < 3:
+            it["params"]["Mext"] = list(info0.m)   # the extended grid the plan uses
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     def step():

@@ -149,6 +149,15 @@ enum { SE_FLAG_FFT_SIZES = 8 };
  * the triply periodic one. Rotlet and harmonic kernels are unaffected.
  * se_autotune_timed sets it for D = 0 FP32 stokeslet / stresslet evaluations. */
 enum { SE_FLAG_SPLIT_POLY = 16 };
+/* se_opts.flags: for D = 0, the extended grid sizes M'_i (given in Mext or from Eq.
+ * extended-grid-size) are lower bounds: se_plan_create takes, among the even M'_i up to 25 %
+ * larger whose transform lengths 2 M'_i have no prime factor above 7, the ones whose transforms
+ * run fastest on this GPU, timing the forward and inverse transforms of one component on
+ * scratch memory (cuFFT's speed varies strongly between such lengths: on a GB300 the 0P
+ * transforms of 2 M' = 900 took less time than those of 840, 864 or 896). A larger M' only adds
+ * zero padding, so the tolerance rules still hold. The choice is kept for the process per
+ * (precision, minimum sizes, kernels); se_autotune_timed sets the flag for D = 0. */
+enum { SE_FLAG_FFT_TIMED = 32 };
 
 /* Fill *opts with the defaults above. */
 se_status se_opts_default(se_opts* opts);
@@ -206,8 +215,9 @@ se_status se_autotune(int periodicity, const double box[3], int kernel_mask, dou
  * its grid is unsupported. The real-space path is chosen the same way: both the
  * per-target and the dense-block path (SE_FLAG_REAL_BLOCKS) are timed at the first candidate,
  * the faster is used along the walk, both are timed again at the chosen r_c, and the choice is
- * returned in io_opts->flags (the other flags are kept as given; for D = 0 FP32 stokeslet and
- * stresslet evaluations SE_FLAG_SPLIT_POLY is added). Last, the gridding tile depth
+ * returned in io_opts->flags (the other flags are kept as given; for D = 0 SE_FLAG_FFT_TIMED
+ * is added, and for D = 0 FP32 stokeslet and stresslet evaluations SE_FLAG_SPLIT_POLY). Last,
+ * the gridding tile depth
  * (io_opts->tile = 4 and 8, CUDA-core gridding) is timed at the chosen parameters and the
  * fastest of the two and the caller's own value is returned in io_opts->tile. FP32 trials also bound the
  * rounding: each candidate evaluates once more with the linear part of the strengths scaled

@@ -21,6 +21,7 @@ FLAG_TEST_TIMEOUT = 2  # se_opts.flags, testing aid: the tensor-core gridding's 
 FLAG_REAL_BLOCKS = 4  # se_opts.flags: real-space sum with the dense-block path (k_real_blk)
 FLAG_FFT_SIZES = 8  # se_opts.flags: grid extents rounded up to FFT-friendly (7-smooth) sizes
 FLAG_SPLIT_POLY = 16  # se_opts.flags: D = 0 biharmonic split into (B_R - p) + p, p of degree 6
+FLAG_FFT_TIMED = 32  # se_opts.flags: D = 0 extended grid sizes chosen among FFT-friendly ones by timing
 KERNELS = {"stokeslet": STOKESLET, "rotlet": ROTLET, "stresslet": STRESSLET,
            "stokeslet+stresslet": STOKESLET | STRESSLET, "harmonic_field": HARMONIC_FIELD,
            "harmonic": HARMONIC}

@@ -785,6 +785,24 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
     }
     g.ntile[d] = cdiv(g.m[d], TS);
   }
+  // D = 0, SE_FLAG_FFT_TIMED: the extents above are lower bounds; the transform lengths 2 M'_d
+  // are chosen among FFT-friendly ones by timing the transforms
+  bool timed_ext = false;
+  if (D == 0 && (o.flags & SE_FLAG_FFT_TIMED)) {
+    const int cin = (kmask & SE_STRESSLET) ? ((kmask & SE_STOKESLET) ? 9 : 6) : 3;
+    int best[3];
+    if (fft0_timed_extents(o.prec, p->stream, g.m, cin, 3, best) == SE_OK) {
+      for (int d = 0; d < 3; ++d) {
+        if (best[d] == g.m[d]) continue;
+        timed_ext = true;
+        g.m[d] = best[d];
+        g.n[d] = 2 * best[d];
+        p->dL[d] = best[d] * h - box[d];
+        g.origin[d] = -0.5 * p->dL[d];
+        g.ntile[d] = cdiv(g.m[d], TS);
+      }
+    }
+  }
   g.cs = D == 0 ? (long long)g.m[0] * g.n[1] * g.n[2] : (long long)g.n[0] * g.n[1] * g.n[2];
   if ((double)g.n[0] * g.n[1] * g.n[2] >= 2147483647.0) {  // grid offsets are 32-bit per component
     free_plan(p);
@@ -799,7 +817,8 @@ extern "C" se_status se_plan_create(se_plan_h* out, int D, const double box[3], 
       minLe = std::min(minLe, Le);
     }
     p->R = std::sqrt(R2);
-    p->s0 = o.s0 > 0 ? o.s0 : std::ceil(10.0 * (1.0 + p->R / minLe) - 1e-9) / 10.0;
+    const double s0r = std::ceil(10.0 * (1.0 + p->R / minLe) - 1e-9) / 10.0;
+    p->s0 = o.s0 > 0 ? (timed_ext ? std::max(o.s0, s0r) : o.s0) : s0r;
     if (D > 0) {
       const double Q = o.Q > 0 ? o.Q : 1.0;
       const double Lc = std::cbrt(box[0] * box[1] * box[2]);
@@ -1589,6 +1608,8 @@ extern "C" se_status se_autotune_timed(int D, const double box[3], int kernel_ma
   // taken out (SE_FLAG_SPLIT_POLY), which keeps the transforms' rounding from being amplified
   if (D == 0 && io->prec == SE_FP32 && (kernel_mask & (SE_STOKESLET | SE_STRESSLET)))
     io->flags |= SE_FLAG_SPLIT_POLY;
+  // free space: transform lengths chosen by timing among the FFT-friendly ones
+  if (D == 0) io->flags |= SE_FLAG_FFT_TIMED;
   // the real-space path (per-target k_real, or the dense-block path) is a choice too: both
   // are timed at f = 1, the faster is kept for the walk over r_c and both are timed again at
   // the chosen r_c

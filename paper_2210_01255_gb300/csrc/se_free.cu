@@ -17,6 +17,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <array>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "se_device.cuh"
@@ -767,6 +770,140 @@ template <> struct FT<double> {
 };
 
 }  // namespace
+
+// SE_FLAG_FFT_TIMED (D = 0): among the even extents M'_d >= mmin[d] whose transform lengths
+// 2 M'_d have no prime factor above 7, up to 25 % above the minimum, the ones whose transforms
+// take the least time. A candidate's cost is that of one evaluation's transforms and scaling:
+// cin forward (2-D R2C over directions 1, 2 of the M'_0 planes, 1-D C2C along direction 0)
+// and no inverse transforms, timed on scratch buffers with CUDA events (best of 3), plus the
+// scaling pass estimated from its bytes. Equal minima (a cube) are searched together, others
+// one direction at a time. Results are kept per (precision, minima, cin, no) for the process.
+namespace {
+std::mutex fft0_mu;
+std::map<std::vector<int>, std::array<int, 3>> fft0_cache;
+
+bool smooth7(int v) {
+  for (int q : {2, 3, 5, 7})
+    while (v % q == 0) v /= q;
+  return v == 1;
+}
+
+template <typename T>
+double fft0_cost(const int me[3], int cin, int no, cudaStream_t st) {
+  const int n0 = 2 * me[0], n1 = 2 * me[1], n2 = 2 * me[2], h2 = n2 / 2 + 1, m0 = me[0];
+  if ((double)n0 * n1 * n2 >= 2147483647.0) return -1;
+  const size_t lines = (size_t)n1 * h2, GS = (size_t)m0 * n1 * n2, H = (size_t)n0 * lines;
+  size_t fr = 0, tot = 0;
+  cudaMemGetInfo(&fr, &tot);
+  const size_t need = sizeof(T) * (GS + 4 * H);
+  if (need * 2 > fr) return -1;  // leave room: the plan's own buffers come later
+  T *grid = nullptr, *tmp = nullptr, *spec = nullptr;
+  cufftHandle hA = 0, hB = 0, hAi = 0;
+  bool okA = false, okB = false, okAi = false;
+  double cost = -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+  do {
+    if (cudaMalloc(&grid, sizeof(T) * GS) != cudaSuccess || cudaMalloc(&tmp, sizeof(T) * 2 * H) != cudaSuccess ||
+        cudaMalloc(&spec, sizeof(T) * 2 * H) != cudaSuccess)
+      break;
+    cudaMemsetAsync(grid, 0, sizeof(T) * GS, st);
+    cudaMemsetAsync(tmp, 0, sizeof(T) * 2 * H, st);
+    int nA[2] = {n1, n2}, nB[1] = {n0}, eB[1] = {n0};
+    okA = cufftPlanMany(&hA, 2, nA, nullptr, 1, n1 * n2, nullptr, 1, (int)lines, FT<T>::R2C, m0) == CUFFT_SUCCESS;
+    okB = okA && cufftPlanMany(&hB, 1, nB, eB, (int)lines, 1, eB, (int)lines, 1, FT<T>::C2C, (int)lines) ==
+                     CUFFT_SUCCESS;
+    okAi = okB && cufftPlanMany(&hAi, 2, nA, nullptr, 1, (int)lines, nullptr, 1, n1 * n2, FT<T>::C2R, m0) ==
+                      CUFFT_SUCCESS;
+    if (!okAi) break;
+    cufftSetStream(hA, st);
+    cufftSetStream(hB, st);
+    cufftSetStream(hAi, st);
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    double best_f = 1e30, best_i = 1e30;
+    bool ok = true;
+    for (int rep = 0; rep < 4 && ok; ++rep) {
+      cudaEventRecord(e0, st);
+      ok = FT<T>::r2c(hA, grid, tmp) == CUFFT_SUCCESS && FT<T>::c2c(hB, tmp, spec, CUFFT_FORWARD) == CUFFT_SUCCESS;
+      cudaEventRecord(e1, st);
+      ok = ok && FT<T>::c2c(hB, spec, spec, CUFFT_INVERSE) == CUFFT_SUCCESS && FT<T>::c2r(hAi, spec, grid) == CUFFT_SUCCESS;
+      cudaEventRecord(e2, st);
+      float tf = 0, ti = 0;
+      ok = ok && cudaEventSynchronize(e2) == cudaSuccess && cudaEventElapsedTime(&tf, e0, e1) == cudaSuccess &&
+           cudaEventElapsedTime(&ti, e1, e2) == cudaSuccess;
+      if (ok && rep > 0) {  // the first round warms up
+        best_f = std::min(best_f, (double)tf);
+        best_i = std::min(best_i, (double)ti);
+      }
+    }
+    if (!ok) break;
+    const double scale_ms = (double)(cin + no) * 2 * sizeof(T) * H / 5e12 * 1e3;
+    cost = cin * best_f + no * best_i + scale_ms;
+  } while (0);
+  if (okA) cufftDestroy(hA);
+  if (okB) cufftDestroy(hB);
+  if (okAi) cufftDestroy(hAi);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (e2) cudaEventDestroy(e2);
+  cudaFree(grid);
+  cudaFree(tmp);
+  cudaFree(spec);
+  cudaGetLastError();
+  return cost;
+}
+}  // namespace
+
+se_status fft0_timed_extents(int prec, cudaStream_t st, const int mmin[3], int cin, int no, int out[3]) {
+  std::lock_guard<std::mutex> lk(fft0_mu);
+  const std::vector<int> key = {prec, mmin[0], mmin[1], mmin[2], cin, no};
+  auto it = fft0_cache.find(key);
+  if (it != fft0_cache.end()) {
+    for (int d = 0; d < 3; ++d) out[d] = it->second[d];
+    return SE_OK;
+  }
+  auto cost = [&](const int me[3]) {
+    return prec == SE_FP32 ? fft0_cost<float>(me, cin, no, st) : fft0_cost<double>(me, cin, no, st);
+  };
+  auto cands = [](int lo) {
+    std::vector<int> c;
+    for (int v = lo + (lo & 1); v <= lo + lo / 4 && c.size() < 8; v += 2)
+      if (smooth7(2 * v)) c.push_back(v);
+    if (c.empty()) c.push_back(lo);
+    return c;
+  };
+  int best[3] = {mmin[0], mmin[1], mmin[2]};
+  if (mmin[0] == mmin[1] && mmin[1] == mmin[2]) {
+    double bc = -1;
+    for (int v : cands(mmin[0])) {
+      const int me[3] = {v, v, v};
+      const double c = cost(me);
+      if (c >= 0 && (bc < 0 || c < bc)) {
+        bc = c;
+        best[0] = best[1] = best[2] = v;
+      }
+    }
+  } else {
+    for (int d = 0; d < 3; ++d) {
+      double bc = -1;
+      int bv = best[d];
+      for (int v : cands(mmin[d])) {
+        int me[3] = {best[0], best[1], best[2]};
+        me[d] = v;
+        const double c = cost(me);
+        if (c >= 0 && (bc < 0 || c < bc)) {
+          bc = c;
+          bv = v;
+        }
+      }
+      best[d] = bv;
+    }
+  }
+  fft0_cache[key] = {best[0], best[1], best[2]};
+  for (int d = 0; d < 3; ++d) out[d] = best[d];
+  return SE_OK;
+}
 
 // Steps (ii)-(iv) for D = 2, 1 (adaptive FFT) and D = 0 (padded FFT with the precomputed
 // kernel). grid: C spread components; ugrid: receives the 3 n_rhs inverse-transformed

@@ -197,6 +197,8 @@ se_status grid_launch(se_plan_t* p, const int* bin_start, const int* base, const
 se_status spread_tc_launch(se_plan_t* p, const int* tile_start, const int* base, const float* w, const float* sf,
                            int C, float* grid, long long cst, long long xst);
 se_status free_plan_setup(se_plan_t* p);
+// D = 0, SE_FLAG_FFT_TIMED: extents >= mmin whose transforms take the least time (se_free.cu)
+se_status fft0_timed_extents(int prec, cudaStream_t st, const int mmin[3], int cin, int no, int out[3]);
 template <typename T>
 se_status fourier_free(se_plan_t* p, int kernel, int n_rhs, T* grid, int C, T* ugrid, int NC);
 template <typename T>

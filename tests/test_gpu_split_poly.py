@@ -109,3 +109,27 @@ def test_harmonic_kernels_unaffected(kernel):
     a = ev(plan(kernel, N, 1e-10, f, "fp64", se.FLAG_SPLIT_POLY), kernel, x, f)
     b = ev(plan(kernel, N, 1e-10, f, "fp64", 0), kernel, x, f)
     assert rms_rel(a, b) < 1e-14
+
+
+def test_fft_timed_extents():
+    """SE_FLAG_FFT_TIMED: the extended grid is at least the rule's, FFT-friendly, and the
+    potential matches the direct sums as with the rule's grid."""
+    kernel = "stokeslet+stresslet"
+    N = 1500
+    x = W.clustered_points(N, seed=6100)
+    f = W.strengths(kernel, N, seed=6200)
+    a_plan = plan(kernel, N, 1e-10, f, "fp64", se.FLAG_FFT_SIZES)
+    b_plan = plan(kernel, N, 1e-10, f, "fp64", se.FLAG_FFT_SIZES | se.FLAG_FFT_TIMED)
+    ma, mb = list(a_plan.info().m), list(b_plan.info().m)
+    for d in range(3):
+        assert ma[d] <= mb[d] <= ma[d] + ma[d] // 4 and mb[d] % 2 == 0
+        v = 2 * mb[d]
+        for q in (2, 3, 5, 7):
+            while v % q == 0:
+                v //= q
+        assert v == 1
+    idx = np.arange(0, N, 4)
+    ref = (E.potential(0, [1, 1, 1], "stokeslet", x, f[:, :3], targets=x[idx])
+           + E.potential(0, [1, 1, 1], "stresslet", x, f[:, 3:], targets=x[idx]))
+    for p in (a_plan, b_plan):
+        assert E.rms_rel(ev(p, kernel, x, f)[idx], ref) < 1e-9
