@@ -42,6 +42,7 @@ WORKLOAD = "0p_stokeslet_stresslet_n1000000"   # default (--workload selects ano
 P_MARGIN = None   # --p-margin: overrides the workload's window margin of the selection
 NRC_SCALE = None  # --nrc-scale: the tolerance rules at r_c scaled from the uniform-case rule (no timing)
 REAL_PATH = "auto"  # --real-path: the real-space path (auto: the selection's choice)
+MEXT = None  # --mext: fixed extended grid size M' of the free directions (no timed choice)
 METRIC_FMT = "targets/sec at 1e-6 RMS rel error (FP32 batched vs FP64 plain), %s"
 METRIC = METRIC_FMT % "0P stokeslet+stresslet, N=1e6 clustered"
 METRIC_NAMES = {"3p_stresslet_rotlet_n20000": "3P stresslet+rotlet, N=20000",
@@ -227,6 +228,10 @@ def make_plan(cfg, item, prec, stream, flags=0):
     # the gridding choice of the command line; the real-space path the selection chose
     o.flags = flags | (t["opts"].flags & (se_.FLAG_REAL_BLOCKS | se_.FLAG_FFT_SIZES | se_.FLAG_SPLIT_POLY |
                                           se_.FLAG_FFT_TIMED))
+    if MEXT is not None and cfg["D"] < 3:
+        o.flags &= ~se_.FLAG_FFT_TIMED
+        for d in range(cfg["D"], 3):
+            o.Mext[d] = MEXT
     if REAL_PATH == "blocks":
         o.flags |= se_.FLAG_REAL_BLOCKS
     elif REAL_PATH == "target":
@@ -641,7 +646,7 @@ def run_group(cfg, items, args, flush, dev, dist):
 
 
 def main():
-    global WORKLOAD, METRIC, P_MARGIN, NRC_SCALE, REAL_PATH
+    global WORKLOAD, METRIC, P_MARGIN, NRC_SCALE, REAL_PATH, MEXT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -660,6 +665,10 @@ def main():
                          "by this factor from the uniform-case rule (for profiling a given choice)")
     ap.add_argument("--real-path", choices=["auto", "blocks", "target"], default="auto",
                     help="real-space path: the selection's choice, the dense-block path or per target")
+    ap.add_argument("--mext", type=int, default=None,
+                    help="fixed extended grid size M' of the free directions (even; instead of the plan's "
+                         "timed choice among FFT-friendly sizes), e.g. to profile the timed choice's "
+                         "configuration under a profiler, whose overheads distort the timing")
     ap.add_argument("--n-points", type=int, default=None,
                     help="override N of a single-system workload (a smaller case of the same kind)")
     ap.add_argument("--experiment", choices=["complexity", "time_vs_error", "window"], default=None,
@@ -679,6 +688,7 @@ def main():
     P_MARGIN = args.p_margin
     NRC_SCALE = args.nrc_scale
     REAL_PATH = args.real_path
+    MEXT = args.mext
     if args.n_points is not None and "N" in W_CONFIGS()[WORKLOAD]:
         W_CONFIGS()[WORKLOAD]["N"] = args.n_points
     if args.impl == "reference":

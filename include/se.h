@@ -122,7 +122,7 @@ enum { SE_FLAG_TC_GRIDDING = 1 };
 enum { SE_FLAG_TEST_TIMEOUT = 2 };
 /* se_opts.flags: real-space sum with the dense-block path. Targets are grouped in blocks of 32
  * consecutive cell-sorted targets (cells of side >= r_c / 8); a block whose targets lie in a
- * box of side <= r_c / 2 is
+ * box of side <= r_c is
  * summed by one warp against the candidates of the whole box (staged in shared memory and
  * shared by the 32 targets), the targets of the other blocks one warp per target as without
  * the flag. Pays off where targets have many neighbours (clustered points, large r_c);
