@@ -161,6 +161,9 @@ struct se_plan_t {
   // side stream for the real-space part (forked from and joined to the plan's stream)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // the Fourier chain's stream while the real space runs beside it: the greatest priority
+  cudaStream_t hi = nullptr;
+  cudaEvent_t ev_hi = nullptr;
   int launches = 0;  // kernels launched by the last evaluation
   long long scale_modes = 0;  // k-space modes per component the last scaling step visited
   // D = 0: buffers whose zero padding is in place (pointer and component count at zeroing)
