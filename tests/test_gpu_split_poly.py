@@ -133,3 +133,38 @@ def test_fft_timed_extents():
            + E.potential(0, [1, 1, 1], "stresslet", x, f[:, 3:], targets=x[idx]))
     for p in (a_plan, b_plan):
         assert E.rms_rel(ev(p, kernel, x, f)[idx], ref) < 1e-9
+
+
+def test_fft_timed_extents_non_cubic_box():
+    """SE_FLAG_FFT_TIMED on a box (1, 0.75, 0.5): the directions are searched one at a time;
+    every extent is at least the rule's and FFT-friendly, and the potential meets the direct
+    sums."""
+    kernel = "stokeslet"
+    box = (1.0, 0.75, 0.5)
+    N = 800
+    rng = np.random.default_rng(6300)
+    x = rng.random((N, 3)) * np.array(box)
+    f = W.strengths(kernel, N, seed=6400)
+    Q = W.source_quantity(kernel, f)
+    plans = []
+    for flags in (se.FLAG_FFT_SIZES, se.FLAG_FFT_SIZES | se.FLAG_FFT_TIMED):
+        o = se.se_opts_default()
+        o.flags = flags
+        t = se.se_autotune(0, box, se.KERNELS[kernel], Q, N, 1e-10, opts=o)
+        o = t["opts"]
+        o.kernel_mask = se.KERNELS[kernel]
+        o.Q = Q
+        o.flags = flags
+        plans.append(se.Plan(0, box, t["xi"], t["rc"], t["M"], t["P"], "pkb", "fp64", opts=o))
+    ma, mb = list(plans[0].info().m), list(plans[1].info().m)
+    for d in range(3):
+        assert ma[d] <= mb[d] <= ma[d] + ma[d] // 4 and mb[d] % 2 == 0
+        v = 2 * mb[d]
+        for q in (2, 3, 5, 7):
+            while v % q == 0:
+                v //= q
+        assert v == 1
+    idx = np.arange(0, N, 4)
+    ref = E.potential(0, list(box), kernel, x, f, targets=x[idx])
+    for p in plans:
+        assert E.rms_rel(ev(p, kernel, x, f)[idx], ref) < 1e-9
