@@ -327,10 +327,10 @@ void se_destroy(se_plan_h plan);
  * the process exits); limits n_src <= 65536 and at most 32 cells per direction; larger
  * requests return SE_ERR_CAPACITY before any work. No cudaMalloc, cudaFree or allocating
  * library call is made. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) once for that device: make that first call before any stream
- * capture. Every call shares the one array and keeps its last contents (the counters and
- * the status word are cleared at the start of each call); calls that overlap on the GPU
- * (different streams, or host threads) race on it and must be serialised by the caller.
+ * (cudaGetSymbolAddress) once for that device. Every call shares the one array and keeps its
+ * last contents (the counters and the status word are cleared at the start of each call);
+ * calls that overlap on the GPU (different streams, or host threads) race on it and must be
+ * serialised by the caller.
  */
 se_status se_real_noalloc(int periodicity, const double box[3], double xi, double rc, int kernel,
                           int prec, long long n_src, const double* src, const void* strengths,
