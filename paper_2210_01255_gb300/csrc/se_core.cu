@@ -1155,9 +1155,10 @@ se_status eval_impl(se_plan_t* p, int kernel, int parts, long long n_src, const 
         SE_TRY(buf(p, "rs.blk", sizeof(int) * ((size_t)(NT + 31) / 32 + NT + 3), &work));
         // blocks whose targets lie in a box of side <= r_c go to the block kernel (on the
         // clustered 0P workload r_c / 2, 3 r_c / 4, r_c and 2 r_c gave 65.9, 62.6, 61.7 and
-        // 61.6 ms); with the Fourier part running concurrently, one CTA per SM is left to its
-        // kernels
-        SE_TRY(real_launch_blocks<T>(rs, ra, ra, (int*)work, p->rc, overlap ? 1 : 0, &p->launches));
+        // 61.6 ms); with the Fourier part running concurrently (on its high-priority stream),
+        // two CTAs per SM are left to its kernels (0, 1, 2, 3, 4 left: 116.4, 115.6, 111.9,
+        // 121.5, 184.1 ms per step)
+        SE_TRY(real_launch_blocks<T>(rs, ra, ra, (int*)work, p->rc, overlap ? 2 : 0, &p->launches));
       } else {
         p->launches += real_launch<T>(rs, ra);
       }
