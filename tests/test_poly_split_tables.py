@@ -11,12 +11,14 @@ import os
 import re
 
 import numpy as np
+import pytest
 
 HDR = os.path.join(os.path.dirname(__file__), "..", "paper_2210_01255_gb300", "csrc", "se_poly_split.h")
 
 
 def _tables():
-    txt = open(HDR).read()
+    with open(HDR) as fh:
+        txt = fh.read()
     mono = np.array([[int(v) for v in m] for m in re.findall(r"\{(-?\d+), (-?\d+), (-?\d+)\}",
                                                               txt.split("se_ps_mono")[1].split(";")[0])])
 
@@ -74,3 +76,34 @@ def test_tables_reproduce_direct_sums():
                 vt[j] += c * xm[a] * Mt[b, k]
         assert np.allclose(vs, us, rtol=1e-12, atol=1e-12 * (np.abs(us).max() + 1.0)), (n, vs, us)
         assert np.allclose(vt, ut, rtol=1e-12, atol=1e-12 * (np.abs(ut).max() + 1.0)), (n, vt, ut)
+
+
+def _screened_power(n, r, xi):
+    """(gamma * |.|^(2n))(x) at |x| = r by quadrature, gamma the Hasimoto screening function
+    xi^3 / pi^(3/2) exp(-xi^2 s^2) (5/2 - xi^2 s^2), whose transform is
+    (1 + k^2/4xi^2) exp(-k^2/4xi^2): the angular integral of (r^2 + s^2 - 2 r s mu)^n over
+    mu in [-1, 1] exactly (polynomial), the radial one numerically."""
+    from numpy.polynomial import polynomial as Pn
+    from scipy.integrate import quad
+
+    def radial(s):
+        # coefficients in mu of (r^2 + s^2 - 2 r s mu)^n, integrated over [-1, 1]
+        c = Pn.polypow([r * r + s * s, -2 * r * s], n)
+        ci = Pn.polyint(c)
+        ang = Pn.polyval(1.0, ci) - Pn.polyval(-1.0, ci)
+        g = xi ** 3 / np.pi ** 1.5 * np.exp(-xi * xi * s * s) * (2.5 - xi * xi * s * s)
+        return 2 * np.pi * g * s * s * ang
+
+    return quad(radial, 0, 12 / xi, epsabs=0, epsrel=1e-11, limit=200)[0]
+
+
+@pytest.mark.parametrize("n,extra", [(1, 0.0), (2, 0.0), (3, -840.0 / 32.0)])
+def test_screening_of_the_split_powers(n, extra):
+    """The Fourier part sees r^(2n) through the Hasimoto screening: r^2 and r^4 come out
+    unchanged up to a constant, r^6 gains -840/(32 xi^4) r^2 (plus a constant): the
+    screened power minus r^(2n) + 840/(32 xi^4) r^2 is the same at every r."""
+    xi = 3.0
+    rs = [0.1, 0.35, 0.8, 1.3]
+    d = [_screened_power(n, r, xi) - r ** (2 * n) - extra / xi ** 4 * r * r for r in rs]
+    scale = max(abs(_screened_power(n, r, xi)) for r in rs)
+    assert max(d) - min(d) < 1e-9 * scale, d
